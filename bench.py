@@ -1,0 +1,336 @@
+"""Benchmark: Gcell-updates/s of block-relaxation sweeps on a 256^3 grid (one GB300 per rank).
+
+Headline workload: 256^3 interior cells, a = (1,1,1), x-line block Jacobi (omega = 0.8),
+FP32, b = h^2 f and u0 from seeded U[-1,1] draws; one step = 50 sweeps.  With N ranks
+(torchrun) every rank sweeps its own replica (no data-path collective: the grids are
+independent), so `value` is N x cells x sweeps / (max-over-ranks time).
+
+Also reported on the same JSON line:
+  roofline     -- the sweep kernel's algorithmic HBM bytes (u read, b read, u' written:
+                  3 words per cell) per launch / average launch time, against the measured
+                  HBM copy bandwidth;
+  e2e          -- the same metric through the host-buffer C-ABI entry point, with the H2D
+                  copies of u and b and the D2H copy of u inside the timed region;
+  cpu_baseline -- the FP64 CPU oracle on the host cores on a bounded slab of the grid;
+  clocks       -- nvidia-smi samples taken during the timed region;
+  variants     -- other method / dtype / coefficient combinations of the 256^3 workload.
+
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only), on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "Gcell-updates/s per sweep & % HBM roofline; FP64 vs mixed at equal residual"
+UNIT = "Gcell-updates/s"
+N = 256
+SWEEPS_PER_STEP = 50
+COEFFS = (1.0, 1.0, 1.0)
+L2_BYTES = 129e6
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _inputs(dtype_str):
+    """Seeded synthetic u0 and b = h^2 f of the 256^3 workload, on the current CUDA device."""
+    import torch
+
+    from brs_inputs import initial_guess, rhs
+
+    td = torch.float64 if dtype_str == "f64" else torch.float32
+    u0 = torch.from_numpy(initial_guess((N, N, N))).to(td)
+    b = torch.from_numpy(rhs((N, N, N))).to(td)
+    return u0, b
+
+
+def _time_sweeps(ctx, u, b, steps, warmup, sweeps, stream, barrier=None):
+    import torch
+
+    for _ in range(warmup):
+        ctx.sweep(u, b, sweeps, stream=stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.sweep(u, b, sweeps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return e0.elapsed_time(e1)  # ms
+
+
+def _cpu_baseline(budget_s: float = 12.0):
+    """FP64 oracle x-line Jacobi on a 256 x 256 x 8 slab of the workload (bounded sample)."""
+    import oracle
+    from brs_inputs import initial_guess, rhs
+
+    oracle.build()
+    nz = 8
+    u = initial_guess((N, N, N))[:nz].copy()
+    b = rhs((N, N, N))[:nz].copy()
+    oracle.sweep(u, b, COEFFS, block="line", method="jacobi", omega=0.8)  # warm
+    t0 = time.perf_counter()
+    sweeps = 0
+    while True:
+        u = oracle.sweep(u, b, COEFFS, block="line", method="jacobi", omega=0.8)
+        sweeps += 1
+        if time.perf_counter() - t0 >= budget_s or sweeps >= 400:
+            break
+    dt = time.perf_counter() - t0
+    cells = N * N * nz
+    return {"value": cells * sweeps / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle x-line block Jacobi, {sweeps} sweeps of a 256x256x{nz} slab "
+                      f"(same cells/line and coefficients as the 256^3 workload), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from brs_inputs import initial_guess, rhs
+
+    oracle.build()
+    nz = 4  # bounded slab per step: 256 x 256 x 4 cells
+    u = initial_guess((N, N, N))[:nz].copy()
+    b = rhs((N, N, N))[:nz].copy()
+    for _ in range(args.warmup):
+        u = oracle.sweep(u, b, COEFFS, block="line", method="jacobi", omega=0.8)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = oracle.sweep(u, b, COEFFS, block="line", method="jacobi", omega=0.8)
+    dt = time.perf_counter() - t0
+    cells = N * N * nz
+    val = cells * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "grid256_iso: 256^3 x-line block Jacobi a=(1,1,1) omega=0.8; "
+                                   "reference step = one FP64 oracle sweep of a 256x256x4 slab",
+                       "nx": N, "ny": N, "nz": N},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "one x-line Jacobi sweep of a 256x256x4 slab per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _traffic_record():
+    """Per-launch DRAM bytes of the headline kernel from the committed ncu summary, if current."""
+    import hashlib
+
+    rec = ROOT / "profiles" / "line_tma_f32_256cubed.traffic.json"
+    if not rec.exists():
+        return None
+    d = json.loads(rec.read_text())
+    src = ROOT / "paper_1208_1975_gb300" / "csrc" / "line_impl.cuh"
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    return d.get("dram_bytes_per_launch") if d.get("source_sha") == h else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_1208_1975_gb300 as brs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    barrier = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+    if rank == 0:
+        brs.build()
+    if barrier:
+        barrier()
+    brs.lib()
+
+    stream = torch.cuda.current_stream()
+    cells = N * N * N
+    u0, b_h = _inputs("f32")
+    u = u0.cuda()
+    b = b_h.cuda()
+    ctx = brs.Context(N, N, N, COEFFS, block="line", method="jacobi", dtype="f32")
+    cfg = brs.lib()  # noqa: F841  (library loaded)
+
+    sampler = ClockSampler(local)
+    ms = _time_sweeps(ctx, u, b, args.steps, args.warmup, SWEEPS_PER_STEP, stream, barrier)
+    clocks = sampler.stop()
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sweeps_total = args.steps * SWEEPS_PER_STEP
+    value = ws * cells * sweeps_total / (ms / 1e3) / 1e9
+    launch_s = ms / 1e3 / sweeps_total  # one kernel launch per sweep, back to back
+    alg_bytes = 3 * 4 * cells
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic_record(),
+                "kernel": "line_tma_kernel<float,8,32,Jacobi>",
+                "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # end to end through the host-buffer entry point (pinned host arrays)
+    uh = u0.pin_memory()
+    bh = b_h.pin_memory()
+    e2e_steps = max(3, min(args.steps, 40))
+    for _ in range(2):
+        ctx.sweep_host(uh, bh, SWEEPS_PER_STEP, stream=stream)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.sweep_host(uh, bh, SWEEPS_PER_STEP, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * cells * SWEEPS_PER_STEP * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 4 * cells, "d2h_bytes_per_step": 4 * cells,
+           "steps": e2e_steps, "timer": "host wall clock around synchronising calls"}
+    ctx.close()
+
+    variants = []
+    if not args.no_variants:
+        for (blk, meth, dt, a) in [("line", "gs", "f32", COEFFS),
+                                   ("line", "jacobi", "f32", (1.0, 1.0, 0.01)),
+                                   ("line", "jacobi", "f64", COEFFS),
+                                   ("line", "gs", "f64", COEFFS)]:
+            try:
+                uv0, bv = _inputs(dt)
+                uv, bv = uv0.cuda(), bv.cuda()
+                with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt) as vc:
+                    vsteps = 6
+                    vms = _time_sweeps(vc, uv, bv, vsteps, 2, SWEEPS_PER_STEP, stream, barrier)
+                es = 8 if dt == "f64" else 4
+                rate = cells * SWEEPS_PER_STEP * vsteps / (vms / 1e3) / 1e9
+                variants.append({"block": blk, "method": meth, "dtype": dt, "coeffs": a,
+                                 "value": rate, "unit": UNIT,
+                                 "hbm_frac": rate * 3 * es / peak})
+                del uv, bv
+            except Exception as exc:  # report, do not hide
+                variants.append({"block": blk, "method": meth, "dtype": dt, "coeffs": a,
+                                 "error": str(exc)})
+
+    if rank != 0:
+        return 0
+    cpu = None if args.no_cpu else _cpu_baseline()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grid256_iso: 256^3 x-line block Jacobi, a=(1,1,1), omega=0.8, "
+                                   "FP32, b=h^2 f, f,u0 ~ U[-1,1] seeded",
+                       "nx": N, "ny": N, "nz": N, "sweeps_per_step": SWEEPS_PER_STEP,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2: u, b and the Jacobi buffer are 192 MB "
+                             "per sweep vs the 129 MB L2"},
+            "gpu_launches": sweeps_total, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "variants": variants}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,142 @@
+/*
+ * brsmooth -- block-relaxation sweeps for 3D constant-coefficient 7-point stencils on one
+ * NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * Problem (Sec. 1.1, Eq. stencil3d7, with per-axis coefficients):
+ *   (A u)_ijk = 2(ax+ay+az) u_ijk - ax(u_{i-1,j,k}+u_{i+1,j,k})
+ *               - ay(u_{i,j-1,k}+u_{i,j+1,k}) - az(u_{i,j,k-1}+u_{i,j,k+1}) = b_ijk
+ * on an nx*ny*nz grid of interior unknowns with Dirichlet values at the ghost indices
+ * -1 and n of each axis.  The library treats those values as zero; a caller with
+ * non-zero boundary data adds a_d * g to b on the adjacent cells (b = h^2 f + boundary).
+ *
+ * One sweep (Sec. 2, Eq. blockiteration2):  u <- u + omega * M^{-1} (b - A u)
+ * with M the block diagonal of A for full x-line blocks (M_line = tridiag(-ax,
+ * 2(ax+ay+az), -ax), one block per (j,k)) or full xy-plane blocks (M_plane = ax Tx (x) I
+ * + ay I (x) Ty + 2 az I, one block per k).  Every block is solved exactly.  Updates are
+ * damped block Jacobi (Sec. 2, Alg. 2: new values into a second buffer, then swap) or
+ * chaotic block Gauss-Seidel (Sec. 2, Alg. 1: in place, blocks processed concurrently
+ * with no ordering; a block may read its neighbours' old or new values).
+ *
+ * Memory layout of every grid array: interior cells only, x fastest,
+ *   idx = i + nx*(j + ny*k), dtype as selected (double or float), contiguous.
+ * Arrays passed to the *_sweep / *_residual calls are DEVICE pointers (e.g. from
+ * cudaMalloc or a torch CUDA tensor) aligned to 16 bytes, owned by the caller.
+ * `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ * All work is enqueued on `stream` and returns before it completes, unless stated.
+ *
+ * Errors: every call returns 0 (BRS_OK) or a negative code; nothing aborts, exits or
+ * throws.  Device-side faults detected by the kernels (a bounded wait that ran out)
+ * set a sticky status read by brsmooth_last_error() and returned by the next call
+ * on the same context.
+ */
+#ifndef BRSMOOTH_H
+#define BRSMOOTH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define BRS_OK 0
+#define BRS_ERR_ARG (-1)         /* bad dims, coefficient, pointer, alignment or count */
+#define BRS_ERR_UNSUPPORTED (-2) /* valid request this build does not implement */
+#define BRS_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define BRS_ERR_NOMEM (-4)       /* device or host allocation failed */
+#define BRS_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out */
+#define BRS_ERR_BOUNDS (-6)      /* a device-side index check failed */
+
+/* Block shape: full x-lines or full xy-planes (Sec. 2, block partition of A). */
+#define BRS_XLINE 0
+#define BRS_XYPLANE 1
+
+/* Update scheme between blocks. */
+#define BRS_JACOBI 0     /* damped block Jacobi, paper default omega = 0.8 (Sec. 2.1) */
+#define BRS_CHAOTIC_GS 1 /* chaotic block Gauss-Seidel, paper default omega = 1.0 (Sec. 2.1) */
+
+/* Arithmetic type of u, b and the sweep. */
+#define BRS_F64 0
+#define BRS_F32 1
+
+/* Plane-solve arithmetic (xy-plane blocks only). */
+#define BRS_PLANE_AUTO 0   /* F64: FP64 SIMT;  F32: 3xTF32 tensor cores */
+#define BRS_PLANE_SIMT 1   /* CUDA-core FMA in the context dtype */
+#define BRS_PLANE_TF32 2   /* one TF32 tensor-core pass per contraction (F32 only) */
+#define BRS_PLANE_3XTF32 3 /* split-TF32: hi*hi + hi*lo + lo*hi (F32 only) */
+
+typedef struct brs_ctx brs_ctx; /* opaque; owned by the library */
+
+typedef struct brs_params {
+    int nx, ny, nz;     /* interior cells per axis, each >= 1 */
+    double ax, ay, az;  /* stencil coefficients, each > 0 and finite */
+    int block;          /* BRS_XLINE or BRS_XYPLANE */
+    int method;         /* BRS_JACOBI or BRS_CHAOTIC_GS */
+    int dtype;          /* BRS_F64 or BRS_F32 */
+    double omega;       /* relaxation weight in (0, 2); <= 0 selects the paper default */
+    int plane_math;     /* BRS_PLANE_* (ignored for x-line blocks) */
+} brs_params;
+
+/*
+ * Create a context for one grid shape, coefficient set and method (Sec. 2: the block
+ * factorisation is computed once, before the sweeps, and reused; Sec. 4.3).
+ * Host-side: validates `p`, factors the block (FP64, rounded to dtype) and allocates the
+ * device tables and, for block Jacobi, one grid-sized scratch buffer (the second vector
+ * of Alg. 2).  Uses the current CUDA device.  On success *out owns those resources until
+ * brsmooth_destroy.  Errors: BRS_ERR_ARG (null pointer, dims < 1, non-positive or
+ * non-finite coefficient, omega >= 2, unknown enum), BRS_ERR_UNSUPPORTED
+ * (e.g. TF32 plane math with BRS_F64, or a grid beyond the implemented maxima:
+ * x-lines nx <= 1024; xy-planes nx, ny <= 1024), BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ */
+int brsmooth_create(const brs_params* p, brs_ctx** out);
+
+/*
+ * Run `nsweeps` sweeps (Sec. 2, Alg. 1 / Alg. 2) of the context's method on device
+ * grid `u` (in/out) with right-hand side `b` (read only), both nx*ny*nz elements of the
+ * context dtype.  Block Jacobi ping-pongs between `u` and the context scratch buffer;
+ * the final iterate is always left in `u`.  nsweeps == 0 is a no-op.
+ * Errors: BRS_ERR_ARG (null ctx/u/b, nsweeps < 0, pointer not 16-byte aligned,
+ * u == b), BRS_ERR_CUDA (launch failure), or a sticky device status.
+ * Not thread-safe per context; distinct contexts may be used from distinct threads.
+ */
+int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream);
+
+/*
+ * Residual r = b - A u (Sec. 2, the r^k of Eq. blockiteration2) and its 2-norm.
+ * `r` (device, nullable) receives the residual in the context dtype.  `norm2` (host,
+ * nullable) receives ||r||_2 accumulated in FP64 in a fixed order (deterministic);
+ * when it is non-NULL the call synchronises `stream` before returning.
+ * Errors: BRS_ERR_ARG (null ctx/u/b), BRS_ERR_CUDA.
+ */
+int brsmooth_residual(brs_ctx* c, const void* u, const void* b, void* r, double* norm2,
+                      void* stream);
+
+/*
+ * Same sweeps as brsmooth_sweep, but `u` and `b` are HOST arrays: the call copies b and
+ * u to context-owned device buffers, sweeps, copies u back and synchronises `stream`.
+ * Host arrays may be pageable or pinned (pinned is faster).  The device buffers are
+ * allocated on first use and kept until destroy.
+ * Errors: as brsmooth_sweep, plus BRS_ERR_NOMEM.
+ */
+int brsmooth_sweep_host(brs_ctx* c, void* u_host, const void* b_host, int nsweeps,
+                        void* stream);
+
+/*
+ * Release the context and every device resource it owns.  NULL is accepted (BRS_OK).
+ * Synchronises the device work the context enqueued.
+ */
+int brsmooth_destroy(brs_ctx* c);
+
+/* Sticky device-side status of the context (BRS_OK, BRS_ERR_TIMEOUT, BRS_ERR_BOUNDS);
+ * synchronises the context's last stream.  Reading it clears it. */
+int brsmooth_last_error(brs_ctx* c);
+
+/* Static English text for a status code; never NULL. */
+const char* brsmooth_strerror(int code);
+
+/* Number of cell updates one sweep performs (nx*ny*nz summed over patches). */
+long long brsmooth_cells(const brs_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRSMOOTH_H */

@@ -1,0 +1,228 @@
+"""brsmooth: block-relaxation sweeps for 3D constant-coefficient 7-point stencils on GB300.
+
+Thin Python binding over the C ABI in ``include/brsmooth.h`` (argument marshalling only:
+every step of a sweep runs in the CUDA library ``_build/libbrsmooth.so``).  Functions
+carry the C names; :class:`Context` wraps one ``brs_ctx``.  Grid arrays are torch CUDA
+tensors of shape (nz, ny, nx) (x fastest), float64 or float32, contiguous.
+
+The library is required: if it has not been built (``build()``) or cannot be loaded,
+every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_build" / "libbrsmooth.so"
+
+BRS_OK = 0
+BRS_ERR_ARG = -1
+BRS_ERR_UNSUPPORTED = -2
+BRS_ERR_CUDA = -3
+BRS_ERR_NOMEM = -4
+BRS_ERR_TIMEOUT = -5
+BRS_ERR_BOUNDS = -6
+
+BRS_XLINE, BRS_XYPLANE = 0, 1
+BRS_JACOBI, BRS_CHAOTIC_GS = 0, 1
+BRS_F64, BRS_F32 = 0, 1
+BRS_PLANE_AUTO, BRS_PLANE_SIMT, BRS_PLANE_TF32, BRS_PLANE_3XTF32 = 0, 1, 2, 3
+
+BLOCKS = {"line": BRS_XLINE, "plane": BRS_XYPLANE}
+METHODS = {"jacobi": BRS_JACOBI, "gs": BRS_CHAOTIC_GS, "chaotic_gs": BRS_CHAOTIC_GS}
+DTYPES = {"f64": BRS_F64, "f32": BRS_F32}
+PLANE_MATH = {"auto": BRS_PLANE_AUTO, "simt": BRS_PLANE_SIMT, "tf32": BRS_PLANE_TF32,
+              "3xtf32": BRS_PLANE_3XTF32}
+
+
+class BrsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {brsmooth_strerror(code)} ({code})")
+
+
+class brs_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("ax", ctypes.c_double), ("ay", ctypes.c_double), ("az", ctypes.c_double),
+                ("block", ctypes.c_int), ("method", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("omega", ctypes.c_double), ("plane_math", ctypes.c_int)]
+
+
+_lib = None
+
+
+def build(verbose: bool = False) -> Path:
+    """Compile the CUDA library for sm_103a (nvcc; works without a GPU)."""
+    from . import builder as _b
+
+    return _b.build(verbose=verbose)
+
+
+def lib():
+    """The loaded CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_1208_1975_gb300.build())")
+    L = ctypes.CDLL(str(LIB_PATH))
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.brsmooth_create.argtypes = [ctypes.POINTER(brs_params), ctypes.POINTER(P)]
+    L.brsmooth_sweep.argtypes = [P, P, P, I, P]
+    L.brsmooth_residual.argtypes = [P, P, P, P, ctypes.POINTER(D), P]
+    L.brsmooth_sweep_host.argtypes = [P, P, P, I, P]
+    L.brsmooth_destroy.argtypes = [P]
+    L.brsmooth_last_error.argtypes = [P]
+    L.brsmooth_strerror.argtypes = [I]
+    L.brsmooth_strerror.restype = ctypes.c_char_p
+    L.brsmooth_cells.argtypes = [P]
+    L.brsmooth_cells.restype = ctypes.c_longlong
+    for name in ("brsmooth_create", "brsmooth_sweep", "brsmooth_residual", "brsmooth_sweep_host",
+                 "brsmooth_destroy", "brsmooth_last_error"):
+        getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != BRS_OK:
+        raise BrsError(rc, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t, dtype_code: int, cells: int, name: str):
+    """Device pointer of a contiguous CUDA tensor of the context dtype and size."""
+    import torch
+
+    want = torch.float64 if dtype_code == BRS_F64 else torch.float32
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != want or not t.is_contiguous() or t.numel() != cells:
+        raise ValueError(f"{name}: need a contiguous {want} tensor with {cells} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ C-named functions
+
+def brsmooth_strerror(code: int) -> str:
+    return lib().brsmooth_strerror(int(code)).decode()
+
+
+def brsmooth_create(p: brs_params):
+    h = ctypes.c_void_p()
+    rc = lib().brsmooth_create(ctypes.byref(p), ctypes.byref(h))
+    return rc, h
+
+
+def brsmooth_sweep(ctx, u_ptr, b_ptr, nsweeps: int, stream) -> int:
+    return lib().brsmooth_sweep(ctx, u_ptr, b_ptr, int(nsweeps), ctypes.c_void_p(stream))
+
+
+def brsmooth_residual(ctx, u_ptr, b_ptr, r_ptr, want_norm: bool, stream):
+    nrm = ctypes.c_double(0.0)
+    rc = lib().brsmooth_residual(ctx, u_ptr, b_ptr, r_ptr, ctypes.byref(nrm) if want_norm else None,
+                                 ctypes.c_void_p(stream))
+    return rc, nrm.value
+
+
+def brsmooth_sweep_host(ctx, u_host_ptr, b_host_ptr, nsweeps: int, stream) -> int:
+    return lib().brsmooth_sweep_host(ctx, u_host_ptr, b_host_ptr, int(nsweeps), ctypes.c_void_p(stream))
+
+
+def brsmooth_destroy(ctx) -> int:
+    return lib().brsmooth_destroy(ctx)
+
+
+def brsmooth_last_error(ctx) -> int:
+    return lib().brsmooth_last_error(ctx)
+
+
+def brsmooth_cells(ctx) -> int:
+    return int(lib().brsmooth_cells(ctx))
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class Context:
+    """One brs_ctx: a grid shape, coefficients, block shape, method and dtype."""
+
+    def __init__(self, nx: int, ny: int, nz: int, a=(1.0, 1.0, 1.0), *, block: str = "line",
+                 method: str = "jacobi", dtype: str = "f64", omega: float = 0.0,
+                 plane_math: str = "auto"):
+        self.shape = (nz, ny, nx)
+        self.dtype_code = DTYPES[dtype]
+        self.p = brs_params(nx, ny, nz, float(a[0]), float(a[1]), float(a[2]), BLOCKS[block],
+                            METHODS[method], self.dtype_code, float(omega), PLANE_MATH[plane_math])
+        rc, h = brsmooth_create(self.p)
+        _check(rc, "brsmooth_create")
+        self.h = h
+        self.cells = nx * ny * nz
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            brsmooth_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sweep(self, u, b, nsweeps: int = 1, stream=None):
+        """nsweeps sweeps on CUDA tensors u (in/out) and b; enqueued on `stream`."""
+        rc = brsmooth_sweep(self.h, _dptr(u, self.dtype_code, self.cells, "u"),
+                            _dptr(b, self.dtype_code, self.cells, "b"), nsweeps, _stream_handle(stream))
+        _check(rc, "brsmooth_sweep")
+        return u
+
+    def residual(self, u, b, r=None, norm: bool = True, stream=None):
+        """r = b - A u into `r` (optional) and ||r||_2 (FP64; synchronises when norm=True)."""
+        rp = _dptr(r, self.dtype_code, self.cells, "r") if r is not None else None
+        rc, nrm = brsmooth_residual(self.h, _dptr(u, self.dtype_code, self.cells, "u"),
+                                    _dptr(b, self.dtype_code, self.cells, "b"), rp, norm,
+                                    _stream_handle(stream))
+        _check(rc, "brsmooth_residual")
+        return nrm if norm else None
+
+    def sweep_host(self, u_host, b_host, nsweeps: int = 1, stream=None):
+        """Sweeps on host arrays (numpy or CPU tensors, contiguous, context dtype), in place on u."""
+        import numpy as np
+
+        def hptr(x, name):
+            if hasattr(x, "data_ptr"):
+                if x.is_cuda or not x.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous CPU tensor")
+                return ctypes.c_void_p(x.data_ptr()), x.numel(), str(x.dtype)
+            if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]):
+                raise ValueError(f"{name} must be a C-contiguous numpy array")
+            return ctypes.c_void_p(x.ctypes.data), x.size, str(x.dtype)
+
+        up, un, ud = hptr(u_host, "u")
+        bp, bn, bd = hptr(b_host, "b")
+        want = "float64" if self.dtype_code == BRS_F64 else "float32"
+        if un != self.cells or bn != self.cells or want not in ud or want not in bd:
+            raise ValueError(f"host arrays need {self.cells} {want} elements")
+        rc = brsmooth_sweep_host(self.h, up, bp, nsweeps, _stream_handle(stream))
+        _check(rc, "brsmooth_sweep_host")
+        return u_host
+
+    def last_error(self) -> int:
+        return brsmooth_last_error(self.h)
+
+
+def cell_updates(dims, sweeps: int) -> int:
+    """Cell updates of `sweeps` sweeps over patches `dims` [(nx, ny, nz), ...] (the rate's numerator)."""
+    return int(sum(int(a) * int(b) * int(c) for a, b, c in dims)) * int(sweeps)

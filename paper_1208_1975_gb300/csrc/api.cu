@@ -1,0 +1,328 @@
+// C ABI of brsmooth (declared in include/brsmooth.h): context lifetime, argument checks,
+// sweep dispatch, residual, host-buffer path and status reporting.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "brs_internal.cuh"
+#include "plane.cuh"
+
+int brs_cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return BRS_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return BRS_ERR_NOMEM;
+    return BRS_ERR_CUDA;
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode;
+}
+
+bool aligned16(const void* p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+bool finite_pos(double v)
+{
+    return std::isfinite(v) && v > 0.0;
+}
+
+// Device status word is host-mapped pinned memory: kernels set it on a device-side
+// failure and every later call on the context can read it without synchronising.
+int poll_status(brs_ctx* c)
+{
+    if (c->sticky == BRS_OK && c->dev_status) {
+        volatile int* hs = reinterpret_cast<volatile int*>(c->dev_status);
+        if (*hs != 0)
+            c->sticky = *hs;
+    }
+    return c->sticky;
+}
+
+int validate(const brs_params* p)
+{
+    if (!p)
+        return BRS_ERR_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1)
+        return BRS_ERR_ARG;
+    if (!finite_pos(p->ax) || !finite_pos(p->ay) || !finite_pos(p->az))
+        return BRS_ERR_ARG;
+    if (p->block != BRS_XLINE && p->block != BRS_XYPLANE)
+        return BRS_ERR_ARG;
+    if (p->method != BRS_JACOBI && p->method != BRS_CHAOTIC_GS)
+        return BRS_ERR_ARG;
+    if (p->dtype != BRS_F64 && p->dtype != BRS_F32)
+        return BRS_ERR_ARG;
+    if (!std::isfinite(p->omega) || p->omega >= 2.0)
+        return BRS_ERR_ARG;
+    if (p->plane_math < BRS_PLANE_AUTO || p->plane_math > BRS_PLANE_3XTF32)
+        return BRS_ERR_ARG;
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (n > (1ll << 40))
+        return BRS_ERR_UNSUPPORTED;
+    return BRS_OK;
+}
+
+void free_ctx(brs_ctx* c)
+{
+    if (!c)
+        return;
+    line_teardown(c);
+    plane_teardown(c);
+    if (c->scratch)
+        cudaFree(c->scratch);
+    if (c->partials)
+        cudaFree(c->partials);
+    if (c->host_u_dev)
+        cudaFree(c->host_u_dev);
+    if (c->host_b_dev)
+        cudaFree(c->host_b_dev);
+    if (c->dev_status)
+        cudaFreeHost(c->dev_status);
+    delete c;
+}
+
+}  // namespace
+
+const CUtensorMap* brs_tmap(brs_ctx* c, const void* ptr, int rows, int* rc)
+{
+    for (auto& t : c->tmaps)
+        if (t.ptr == ptr && t.rows == rows)
+            return &t.map;
+    auto enc = encoder();
+    if (!enc) {
+        *rc = BRS_ERR_CUDA;
+        return nullptr;
+    }
+    const brs_params& p = c->p;
+    TmapEntry ent{};
+    ent.ptr = ptr;
+    ent.rows = rows;
+    cuuint64_t gdim[3] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz};
+    cuuint64_t gstride[2] = {(cuuint64_t)p.nx * c->esize, (cuuint64_t)p.nx * p.ny * c->esize};
+    cuuint32_t box[3] = {(cuuint32_t)c->lcfg.bx, (cuuint32_t)rows, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = enc(&ent.map,
+                     p.dtype == BRS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     3, const_cast<void*>(ptr), gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *rc = BRS_ERR_CUDA;
+        return nullptr;
+    }
+    if (c->tmaps.size() >= 16)
+        c->tmaps.erase(c->tmaps.begin());
+    c->tmaps.push_back(ent);
+    return &c->tmaps.back().map;
+}
+
+extern "C" {
+
+const char* brsmooth_strerror(int code)
+{
+    switch (code) {
+    case BRS_OK: return "success";
+    case BRS_ERR_ARG: return "invalid argument";
+    case BRS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case BRS_ERR_CUDA: return "CUDA runtime error";
+    case BRS_ERR_NOMEM: return "out of memory";
+    case BRS_ERR_TIMEOUT: return "device-side wait timed out";
+    case BRS_ERR_BOUNDS: return "device-side bounds check failed";
+    default: return "unknown status code";
+    }
+}
+
+int brsmooth_create(const brs_params* p, brs_ctx** out)
+{
+    if (!out)
+        return BRS_ERR_ARG;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc != BRS_OK)
+        return rc;
+    brs_ctx* c = new (std::nothrow) brs_ctx();
+    if (!c)
+        return BRS_ERR_NOMEM;
+    c->p = *p;
+    c->omega = p->omega > 0.0 ? p->omega : (p->method == BRS_JACOBI ? 0.8 : 1.0);
+    c->esize = p->dtype == BRS_F64 ? 8 : 4;
+    c->cells = (long long)p->nx * p->ny * p->nz;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return brs_cuda_status(e);
+    }
+    e = cudaHostAlloc((void**)&c->dev_status, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return brs_cuda_status(e);
+    }
+    *c->dev_status = 0;
+    if (p->block == BRS_XLINE)
+        rc = line_setup(c);
+    else
+        rc = plane_setup(c);
+    if (rc == BRS_OK)
+        rc = residual_setup(c);
+    if (rc == BRS_OK && p->method == BRS_JACOBI) {
+        e = cudaMalloc(&c->scratch, (size_t)c->cells * c->esize);
+        rc = brs_cuda_status(e);
+    }
+    if (rc != BRS_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    // the status word's device alias (same address under unified addressing)
+    int* dptr = nullptr;
+    e = cudaHostGetDevicePointer((void**)&dptr, c->dev_status, 0);
+    if (e != cudaSuccess || dptr != c->dev_status) {
+        free_ctx(c);
+        return e != cudaSuccess ? brs_cuda_status(e) : BRS_ERR_UNSUPPORTED;
+    }
+    *out = c;
+    return BRS_OK;
+}
+
+static int sweep_one(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s)
+{
+    if (c->p.block == BRS_XLINE)
+        return line_sweep_launch(c, uin, uout, b, s);
+    return plane_sweep_launch(c, uin, uout, b, s);
+}
+
+int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream)
+{
+    if (!c || !u || !b || nsweeps < 0)
+        return BRS_ERR_ARG;
+    if (!aligned16(u) || !aligned16(b) || u == b)
+        return BRS_ERR_ARG;
+    int rc = poll_status(c);
+    if (rc != BRS_OK)
+        return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    c->last_stream = s;
+    if (c->p.method == BRS_CHAOTIC_GS) {
+        for (int k = 0; k < nsweeps && rc == BRS_OK; ++k)
+            rc = sweep_one(c, u, u, b, s);
+        return rc;
+    }
+    // block Jacobi: v = u + omega M^{-1}(b - A u) into the second vector, then swap (Alg. 2)
+    void* cur = u;
+    void* nxt = c->scratch;
+    for (int k = 0; k < nsweeps && rc == BRS_OK; ++k) {
+        rc = sweep_one(c, cur, nxt, b, s);
+        void* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (rc == BRS_OK && cur != u)
+        rc = brs_cuda_status(
+            cudaMemcpyAsync(u, cur, (size_t)c->cells * c->esize, cudaMemcpyDeviceToDevice, s));
+    return rc;
+}
+
+int brsmooth_residual(brs_ctx* c, const void* u, const void* b, void* r, double* norm2,
+                      void* stream)
+{
+    if (!c || !u || !b)
+        return BRS_ERR_ARG;
+    int rc = poll_status(c);
+    if (rc != BRS_OK)
+        return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    c->last_stream = s;
+    rc = residual_launch(c, u, b, r, norm2 != nullptr, s);
+    if (rc != BRS_OK || !norm2)
+        return rc;
+    double h = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    *norm2 = std::sqrt(h);
+    return BRS_OK;
+}
+
+int brsmooth_sweep_host(brs_ctx* c, void* u_host, const void* b_host, int nsweeps, void* stream)
+{
+    if (!c || !u_host || !b_host || nsweeps < 0)
+        return BRS_ERR_ARG;
+    const size_t bytes = (size_t)c->cells * c->esize;
+    cudaError_t e = cudaSuccess;
+    if (!c->host_u_dev)
+        e = cudaMalloc(&c->host_u_dev, bytes);
+    if (e == cudaSuccess && !c->host_b_dev)
+        e = cudaMalloc(&c->host_b_dev, bytes);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(c->host_b_dev, b_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->host_u_dev, u_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    int rc = brsmooth_sweep(c, c->host_u_dev, c->host_b_dev, nsweeps, stream);
+    if (rc != BRS_OK)
+        return rc;
+    e = cudaMemcpyAsync(u_host, c->host_u_dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    return poll_status(c);
+}
+
+int brsmooth_destroy(brs_ctx* c)
+{
+    if (!c)
+        return BRS_OK;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+    return BRS_OK;
+}
+
+int brsmooth_last_error(brs_ctx* c)
+{
+    if (!c)
+        return BRS_ERR_ARG;
+    if (c->last_stream)
+        cudaStreamSynchronize(c->last_stream);
+    else
+        cudaDeviceSynchronize();
+    int rc = poll_status(c);
+    c->sticky = BRS_OK;
+    if (c->dev_status)
+        *reinterpret_cast<volatile int*>(c->dev_status) = 0;
+    return rc;
+}
+
+long long brsmooth_cells(const brs_ctx* c)
+{
+    return c ? c->cells : 0;
+}
+
+}  // extern "C"

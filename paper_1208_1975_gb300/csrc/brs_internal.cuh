@@ -1,0 +1,170 @@
+// Internal declarations shared by the brsmooth CUDA translation units.
+// Target: sm_103a (GB300).  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "brsmooth.h"
+
+// --------------------------------------------------------------------------------------
+// Launch configuration of the x-line sweep kernels.
+// A "line group" of G lanes owns one x-line; lane l holds the E consecutive cells
+// [l*E, l*E+E).  A CTA holds JT groups (lines j0..j0+JT-1 of one k) and marches in +z.
+struct LineCfg {
+    int E = 0, G = 0;   // elements per lane, lanes per line (G*E >= nx)
+    int JT = 0;         // lines per CTA tile (y extent of the tile)
+    int NS = 0;         // shared-memory ring stages (TMA path)
+    int pieces = 1;     // TMA boxes per row (nx / pieces <= 256 elements)
+    int bx = 0;         // TMA box width in elements
+    bool tma = false;   // TMA ring path (rows 16-byte aligned) or the plain-load path
+    int grid = 0;       // persistent CTAs (TMA path)
+    size_t smem = 0;    // dynamic shared memory bytes (TMA path)
+};
+
+// Arguments of the line kernels (passed by value).
+struct LineArgs {
+    int nx, ny, nz;
+    int JT, NS, pieces, bx;
+    int nj;               // number of y tiles = ceil(ny / JT)
+    long long total;      // nj * nz plane-steps
+    double ay, az, om1;   // coefficients and 1 - omega
+    int* status;          // device status word (sticky error flag)
+};
+
+struct TmapEntry {
+    const void* ptr;
+    int rows;
+    CUtensorMap map;
+};
+
+struct brs_ctx {
+    brs_params p{};
+    double omega = 0.0;
+    int device = 0;
+    long long cells = 0;
+    size_t esize = 8;       // bytes per element
+    // block Jacobi second vector (Alg. 2) -- grid sized
+    void* scratch = nullptr;
+    // line solve tables (device, context dtype)
+    void* line_tab = nullptr;
+    LineCfg lcfg;
+    // residual reduction
+    double* partials = nullptr;
+    int npartials = 0;
+    double* norm_dev = nullptr;
+    // device status word, host-side sticky copy
+    int* dev_status = nullptr;
+    int sticky = BRS_OK;
+    cudaStream_t last_stream = nullptr;
+    // host-buffer entry point
+    void* host_u_dev = nullptr;
+    void* host_b_dev = nullptr;
+    // tensor-map cache keyed by (pointer, box rows)
+    std::vector<TmapEntry> tmaps;
+    // plane path state (owned by plane.cu)
+    void* plane = nullptr;
+};
+
+// Status helpers -------------------------------------------------------------------------
+int brs_cuda_status(cudaError_t e);
+
+// Line path (line.cu) ----------------------------------------------------------------------
+// Chooses E/G/JT/NS and uploads the factor tables; returns a BRS_* code.
+int line_setup(brs_ctx* c);
+void line_teardown(brs_ctx* c);
+// One sweep from `uin` into `uout` (Jacobi) or in place (GS: uin == uout).
+int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s);
+
+// Residual (residual.cu) -------------------------------------------------------------------
+int residual_setup(brs_ctx* c);
+int residual_launch(brs_ctx* c, const void* u, const void* b, void* r, bool want_norm,
+                    cudaStream_t s);
+
+// Tensor maps (api.cu) ---------------------------------------------------------------------
+// 3D tiled map over a grid array with box (bx, rows, 1); cached per (pointer, rows).
+const CUtensorMap* brs_tmap(brs_ctx* c, const void* ptr, int rows, int* rc);
+
+// --------------------------------------------------------------------------------------
+// Device helpers: PTX wrappers for mbarrier + TMA, bounded waits.
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for `parity` on `bar` for at most `limit_ns`; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (globaltimer_ns() - t0 > limit_ns)
+            return false;
+    }
+}
+
+// 3D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void set_status(int* status, int code)
+{
+    if (status)
+        atomicCAS(status, 0, code);
+}
+
+#endif  // __CUDACC__

@@ -1,0 +1,247 @@
+// Host side of the x-line sweep: factor tables, launch configuration, dispatch.
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "line_impl.cuh"
+
+namespace {
+
+// Lanes per line and cells per lane for a line of nx cells (G*E >= nx, E*esize a whole
+// number of 16-byte vectors).
+bool pick_EG(int nx, int* E, int* G)
+{
+    if (nx <= 16) { *G = 4; *E = 4; }
+    else if (nx <= 32) { *G = 8; *E = 4; }
+    else if (nx <= 64) { *G = 16; *E = 4; }
+    else if (nx <= 128) { *G = 32; *E = 4; }
+    else if (nx <= 256) { *G = 32; *E = 8; }
+    else if (nx <= 384) { *G = 32; *E = 12; }
+    else if (nx <= 512) { *G = 32; *E = 16; }
+    else return false;
+    return true;
+}
+
+int env_int(const char* name, int dflt)
+{
+    const char* v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+// Factor tables of M_line = tridiag(-ax, d, -ax), d = 2(ax+ay+az), computed once in FP64
+// (the constant block is factored once and shared by every line, Sec. 2 / Sec. 4.3).
+template <typename T>
+std::vector<T> line_tables(int nx, double ax, double ay, double az, double omega, int E, int G)
+{
+    const int NP = G * E;
+    int LG = 0;
+    while ((1 << LG) < G) ++LG;
+    const double d = 2.0 * (ax + ay + az);
+    std::vector<double> p(NP, 0.0), c(NP, 0.0), e(NP, 0.0);
+    p[0] = 1.0 / d;
+    for (int i = 1; i < nx; ++i)
+        p[i] = 1.0 / (d - ax * ax * p[i - 1]);
+    for (int i = 1; i < nx; ++i)
+        c[i] = ax * p[i - 1];
+    for (int i = 0; i + 1 < nx; ++i)
+        e[i] = ax * p[i + 1];
+    std::vector<double> Af(G, 1.0), Ab(G, 1.0);
+    for (int l = 0; l < G; ++l)
+        for (int q = 0; q < E; ++q) {
+            Af[l] *= c[l * E + q];
+            Ab[l] *= e[l * E + q];
+        }
+    std::vector<T> tab(3 * NP + 2 * LG * G);
+    for (int i = 0; i < NP; ++i) {
+        tab[i] = (T)c[i];
+        tab[NP + i] = (T)e[i];
+        tab[2 * NP + i] = (T)(i < nx ? omega * p[i] : 0.0);
+    }
+    for (int t = 0; t < LG; ++t)
+        for (int l = 0; l < G; ++l) {
+            double f = 1.0, b = 1.0;
+            for (int m = (l - (1 << t) + 1 > 0 ? l - (1 << t) + 1 : 0); m <= l; ++m)
+                f *= Af[m];
+            for (int m = l; m < G && m < l + (1 << t); ++m)
+                b *= Ab[m];
+            tab[3 * NP + t * G + l] = (T)f;
+            tab[3 * NP + LG * G + t * G + l] = (T)b;
+        }
+    return tab;
+}
+
+template <typename T, int E, int G>
+struct LineKernels {
+    static const void* tma(bool gs)
+    {
+        return gs ? (const void*)brs::line_tma_kernel<T, E, G, true>
+                  : (const void*)brs::line_tma_kernel<T, E, G, false>;
+    }
+    static const void* plain(bool gs)
+    {
+        return gs ? (const void*)brs::line_plain_kernel<T, E, G, true>
+                  : (const void*)brs::line_plain_kernel<T, E, G, false>;
+    }
+};
+
+template <typename T>
+bool kernels_for(int E, int G, bool gs, const void** tma, const void** plain)
+{
+#define BRS_LINE_CASE(EE, GG)                              \
+    if (E == EE && G == GG) {                              \
+        *tma = LineKernels<T, EE, GG>::tma(gs);            \
+        *plain = LineKernels<T, EE, GG>::plain(gs);        \
+        return true;                                       \
+    }
+    BRS_LINE_CASE(4, 4)
+    BRS_LINE_CASE(4, 8)
+    BRS_LINE_CASE(4, 16)
+    BRS_LINE_CASE(4, 32)
+    BRS_LINE_CASE(8, 32)
+    BRS_LINE_CASE(12, 32)
+    BRS_LINE_CASE(16, 32)
+#undef BRS_LINE_CASE
+    return false;
+}
+
+size_t tma_slot_bytes(const LineCfg& L, size_t es)
+{
+    const size_t ubox = ((size_t)(L.JT + 2) * L.bx * es + 127) & ~size_t(127);
+    const size_t bbox = ((size_t)L.JT * L.bx * es + 127) & ~size_t(127);
+    return (size_t)L.pieces * (ubox + bbox);
+}
+
+}  // namespace
+
+int line_setup(brs_ctx* c)
+{
+    const brs_params& p = c->p;
+    LineCfg L;
+    if (!pick_EG(p.nx, &L.E, &L.G))
+        return BRS_ERR_UNSUPPORTED;
+    const size_t es = c->esize;
+    // TMA path: rows 16-byte aligned, whole lane chunks, boxes of <= 256 elements
+    L.pieces = (p.nx + 255) / 256;
+    L.bx = p.nx / L.pieces;
+    L.tma = (p.nx * es) % 16 == 0 && p.nx % L.E == 0 && p.nx % L.pieces == 0 &&
+            (L.bx * es) % 16 == 0 && L.bx % L.E == 0 && L.bx <= 256 &&
+            env_int("BRSMOOTH_LINE_PLAIN", 0) == 0;
+    const int groups_per_warp = 32 / L.G;
+    int jt_default = (c->p.dtype == BRS_F64 && L.E >= 8) ? 4 : 256 / L.G;
+    int jt = env_int("BRSMOOTH_LINE_JT", jt_default);
+    const int ny_round = ((p.ny + groups_per_warp - 1) / groups_per_warp) * groups_per_warp;
+    if (jt > ny_round)
+        jt = ny_round;
+    jt = ((jt + groups_per_warp - 1) / groups_per_warp) * groups_per_warp;
+    if (jt * L.G > 256)
+        jt = 256 / L.G;
+    L.JT = jt;
+    L.NS = env_int("BRSMOOTH_LINE_NS", 4);
+    if (L.NS < 3)
+        L.NS = 3;
+
+    const bool gs = p.method == BRS_CHAOTIC_GS;
+    const void *ktma = nullptr, *kplain = nullptr;
+    bool ok = (p.dtype == BRS_F64) ? kernels_for<double>(L.E, L.G, gs, &ktma, &kplain)
+                                   : kernels_for<float>(L.E, L.G, gs, &ktma, &kplain);
+    if (!ok)
+        return BRS_ERR_UNSUPPORTED;
+    if (L.tma) {
+        L.smem = (size_t)L.NS * tma_slot_bytes(L, es) + (size_t)L.NS * 8;
+        cudaError_t e = cudaFuncSetAttribute(ktma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L.smem);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ktma, L.JT * L.G, L.smem);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        if (occ < 1)
+            return BRS_ERR_UNSUPPORTED;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        const int per_sm = env_int("BRSMOOTH_LINE_CTAS_PER_SM", occ);
+        L.grid = sms * (per_sm < occ ? per_sm : occ);
+        const long long nj = (p.ny + L.JT - 1) / L.JT;
+        const long long total = nj * p.nz;
+        if (L.grid > total)
+            L.grid = (int)total;
+    }
+    c->lcfg = L;
+
+    // factor tables
+    size_t bytes;
+    cudaError_t e;
+    if (p.dtype == BRS_F64) {
+        auto tab = line_tables<double>(p.nx, p.ax, p.ay, p.az, c->omega, L.E, L.G);
+        bytes = tab.size() * sizeof(double);
+        e = cudaMalloc(&c->line_tab, bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->line_tab, tab.data(), bytes, cudaMemcpyHostToDevice);
+    } else {
+        auto tab = line_tables<float>(p.nx, p.ax, p.ay, p.az, c->omega, L.E, L.G);
+        bytes = tab.size() * sizeof(float);
+        e = cudaMalloc(&c->line_tab, bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->line_tab, tab.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    return brs_cuda_status(e);
+}
+
+void line_teardown(brs_ctx* c)
+{
+    if (c->line_tab)
+        cudaFree(c->line_tab);
+    c->line_tab = nullptr;
+}
+
+int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s)
+{
+    const brs_params& p = c->p;
+    const LineCfg& L = c->lcfg;
+    const bool gs = p.method == BRS_CHAOTIC_GS;
+    const void *ktma = nullptr, *kplain = nullptr;
+    if (p.dtype == BRS_F64)
+        kernels_for<double>(L.E, L.G, gs, &ktma, &kplain);
+    else
+        kernels_for<float>(L.E, L.G, gs, &ktma, &kplain);
+    LineArgs a{};
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.nz = p.nz;
+    a.JT = L.JT;
+    a.NS = L.NS;
+    a.pieces = L.pieces;
+    a.bx = L.bx;
+    a.nj = (p.ny + L.JT - 1) / L.JT;
+    a.total = (long long)a.nj * p.nz;
+    a.ay = p.ay;
+    a.az = p.az;
+    a.om1 = 1.0 - c->omega;
+    a.status = c->dev_status;
+    cudaError_t e;
+    if (L.tma) {
+        int rc = BRS_OK;
+        const CUtensorMap* mu = brs_tmap(c, uin, L.JT + 2, &rc);
+        if (rc != BRS_OK)
+            return rc;
+        const CUtensorMap* mb = brs_tmap(c, b, L.JT, &rc);
+        if (rc != BRS_OK)
+            return rc;
+        CUtensorMap tu = *mu, tbm = *mb;
+        void* out = uout;
+        const void* tab = c->line_tab;
+        void* args[] = {&tu, &tbm, &out, (void*)&tab, &a};
+        e = cudaLaunchKernel(ktma, dim3(L.grid), dim3(L.JT * L.G), args, L.smem, s);
+    } else {
+        const int groups = 256 / L.G;
+        const long long nlines = (long long)p.ny * p.nz;
+        const unsigned blocks = (unsigned)((nlines + groups - 1) / groups);
+        const void* in = uin;
+        void* out = uout;
+        const void* tab = c->line_tab;
+        void* args[] = {(void*)&in, &out, (void*)&b, (void*)&tab, &a};
+        e = cudaLaunchKernel(kplain, dim3(blocks), dim3(256), args, 0, s);
+    }
+    return brs_cuda_status(e);
+}

@@ -1,0 +1,260 @@
+"""x-line block sweeps on the GPU against the FP64 oracle (Sec. 2, Alg. 1 / Alg. 2).
+
+Block Jacobi is deterministic: one GPU sweep from a given iterate is compared element by
+element with the oracle's sweep from the same iterate (relative max-norm <= 1e-12 FP64,
+<= 1e-5 FP32).  Chaotic block Gauss-Seidel is not reproducible; it is judged by the
+componentwise Perron bound, a residual bracket and convergence to the exact solution.
+"""
+import numpy as np
+import pytest
+
+from brs_inputs import initial_guess, rhs, sine_mode
+from gpu_common import TOL, rel_max_err, rounded, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+# (nx, ny, nz): TMA-path shapes, ragged y tiles, the plain-load path (rows not 16-byte
+# aligned or nx not a multiple of the lane chunk), degenerate 1-cell axes, widest lines.
+SHAPES = [(32, 32, 32), (24, 13, 7), (33, 17, 9), (48, 20, 11), (1, 1, 1), (4, 1, 1),
+          (1, 5, 3), (130, 5, 5), (100, 7, 5), (256, 9, 6), (384, 5, 4), (512, 3, 3),
+          (16, 16, 40)]
+COEFFS = [(1.0, 1.0, 1.0), (1.0, 1.0, 0.01), (1.0, 0.1, 0.01)]
+
+
+@pytest.fixture(scope="module")
+def brs():
+    import paper_1208_1975_gb300 as brs
+
+    brs.build()
+    return brs
+
+
+def gpu_sweep(brs, u, b, a, *, dt, method="jacobi", omega=0.0, nsweeps=1, block="line"):
+    nz, ny, nx = u.shape
+    with brs.Context(nx, ny, nz, a, block=block, method=method, dtype=dt, omega=omega) as ctx:
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
+        ctx.sweep(ut, bt, nsweeps)
+        out = to_np(ut)
+        assert ctx.last_error() == 0
+    return out
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
+def test_jacobi_one_sweep_parity(brs, orc, dt, shape, a):
+    nx, ny, nz = shape
+    u = rounded(initial_guess((nz, ny, nx)), dt)
+    b = rounded(rhs((nz, ny, nx)), dt)
+    ref = orc.sweep(u, b, a, block="line", method="jacobi", omega=0.8)
+    got = gpu_sweep(brs, u, b, a, dt=dt)
+    assert rel_max_err(got, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("omega", [0.5, 1.0, 1.3])
+def test_jacobi_omega(brs, orc, omega):
+    shape = (3, 8, 40)
+    u, b = initial_guess(shape), rhs(shape)
+    ref = orc.sweep(u, b, (1.0, 0.5, 2.0), block="line", method="jacobi", omega=omega)
+    got = gpu_sweep(brs, u, b, (1.0, 0.5, 2.0), dt="f64", omega=omega)
+    assert rel_max_err(got, ref) <= 1e-12
+
+
+def test_trajectory_32cubed_residual_per_sweep(brs, orc):
+    """32^3, a=(1,1,1), h=1/33, u0=0: 10 line-Jacobi sweeps, iterate and ||r|| per sweep."""
+    n = 32
+    a = (1.0, 1.0, 1.0)
+    b = rhs((n, n, n))
+    u0 = np.zeros_like(b)
+    traj = orc.trajectory(u0, b, a, 10, block="line", method="jacobi", omega=0.8)
+    with brs.Context(n, n, n, a, block="line", method="jacobi", dtype="f64") as ctx:
+        ut, bt = to_dev(u0, "f64"), to_dev(b, "f64")
+        for k in range(10):
+            ctx.sweep(ut, bt, 1)
+            got = to_np(ut)
+            assert rel_max_err(got, traj[k]) <= 1e-12
+            nrm = ctx.residual(ut, bt)
+            ref = orc.residual_norm(traj[k], b, a)
+            assert abs(nrm - ref) <= 1e-12 * ref
+
+
+def test_multi_sweep_odd_and_even_counts(brs, orc):
+    shape = (6, 10, 24)
+    u, b = initial_guess(shape), rhs(shape)
+    a = (1.0, 1.0, 1.0)
+    for ns in (0, 1, 2, 5):
+        ref = u
+        for _ in range(ns):
+            ref = orc.sweep(ref, b, a, block="line", method="jacobi", omega=0.8)
+        got = gpu_sweep(brs, u, b, a, dt="f64", nsweeps=ns)
+        assert rel_max_err(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_jacobi_is_bitwise_deterministic(brs, dt):
+    shape = (20, 30, 64)
+    u, b = initial_guess(shape), rhs(shape)
+    g1 = gpu_sweep(brs, u, b, (1, 1, 1), dt=dt, nsweeps=3)
+    g2 = gpu_sweep(brs, u, b, (1, 1, 1), dt=dt, nsweeps=3)
+    assert np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 9), (1, 1, 1)], ids=str)
+def test_residual_and_norm(brs, orc, dt, shape):
+    import torch
+
+    nx, ny, nz = shape
+    a = (1.0, 0.1, 0.01)
+    u = rounded(initial_guess((nz, ny, nx)), dt)
+    b = rounded(rhs((nz, ny, nx)), dt)
+    ref = orc.residual(u, b, a)
+    with brs.Context(nx, ny, nz, a, dtype=dt) as ctx:
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
+        r = torch.empty_like(ut)
+        nrm = ctx.residual(ut, bt, r)
+    tol = 1e-13 if dt == "f64" else 2e-6
+    scale = np.max(np.abs(b)) + 2 * sum(a) * np.max(np.abs(u))
+    assert np.max(np.abs(to_np(r) - ref)) <= tol * scale
+    assert abs(nrm - np.linalg.norm(ref)) <= (1e-12 if dt == "f64" else 1e-5) * np.linalg.norm(ref)
+
+
+def test_host_buffer_path_matches_device_path(brs):
+    shape = (16, 24, 32)
+    u, b = initial_guess(shape), rhs(shape)
+    dev = gpu_sweep(brs, u, b, (1, 1, 1), dt="f64", nsweeps=3)
+    with brs.Context(32, 24, 16, (1, 1, 1)) as ctx:
+        uh = u.copy()
+        ctx.sweep_host(uh, b, 3)
+    assert np.array_equal(uh, dev)
+
+
+def test_argument_errors(brs):
+    import torch
+
+    with brs.Context(8, 8, 8) as ctx:
+        u = torch.zeros(512, dtype=torch.float64, device="cuda")
+        b = torch.zeros(513, dtype=torch.float64, device="cuda")
+        rc = brs.brsmooth_sweep(ctx.h, u.data_ptr(), u.data_ptr(), 1, 0)
+        assert rc == brs.BRS_ERR_ARG  # u aliases b
+        rc = brs.brsmooth_sweep(ctx.h, u.data_ptr(), b[1:].data_ptr(), 1, 0)
+        assert rc == brs.BRS_ERR_ARG  # misaligned b
+        rc = brs.brsmooth_sweep(ctx.h, u.data_ptr(), b.data_ptr(), -1, 0)
+        assert rc == brs.BRS_ERR_ARG
+        assert brs.brsmooth_sweep(ctx.h, u.data_ptr(), b.data_ptr(), 0, 0) == brs.BRS_OK
+    p = brs.brs_params(2000, 4, 4, 1.0, 1.0, 1.0, 0, 0, 0, 0.0, 0)
+    rc, h = brs.brsmooth_create(p)
+    assert rc == brs.BRS_ERR_UNSUPPORTED and not h.value
+
+
+# ----------------------------------------------------------------- chaotic Gauss-Seidel
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (24, 40, 48), (33, 17, 9)], ids=str)
+def test_chaotic_gs_perron_bound(brs, orc, dt, shape):
+    """b = 0, u0 = positive mode: 0 <= u_k <= g_111^k u0 componentwise for any race outcome.
+
+    A is an M-matrix, so M^{-1} >= 0 and N = M - A >= 0; every read returns an old or a
+    newer (smaller, still non-negative) value, so each update is bounded by the Jacobi
+    update of the old iterate, which maps the positive sine mode to g_111 times itself.
+    """
+    nx, ny, nz = shape
+    a = (1.0, 1.0, 1.0)
+    m = sine_mode(nx, ny, nz, 1, 1, 1)
+    g = orc.mode_factor(nx, ny, nz, a, "line", 1.0)[0, 0, 0]
+    slack = 1e-13 if dt == "f64" else 2e-6
+    with brs.Context(nx, ny, nz, a, block="line", method="gs", dtype=dt) as ctx:
+        ut = to_dev(m, dt)
+        bt = to_dev(np.zeros_like(m), dt)
+        mr = to_np(ut)
+        for k in range(1, 9):
+            ctx.sweep(ut, bt, 1)
+            u = to_np(ut)
+            assert np.all(u >= -slack)
+            assert np.all(u <= g ** k * mr + slack * (1 + k))
+
+
+def test_chaotic_gs_residual_bracket_32cubed(brs, orc):
+    """||r_k|| of chaotic line GS lies between the ordered GS sweeps and Jacobi (omega=1)."""
+    n = 32
+    a = (1.0, 1.0, 1.0)
+    b = rhs((n, n, n))
+    u0 = initial_guess((n, n, n))
+    refs = {}
+    for meth, om in (("jacobi", 1.0), ("gs_lex", 1.0), ("gs_zebra", 1.0), ("gs_reverse", 1.0)):
+        u, norms = u0, []
+        for _ in range(10):
+            u = orc.sweep(u, b, a, block="line", method=meth, omega=om)
+            norms.append(orc.residual_norm(u, b, a))
+        refs[meth] = np.array(norms)
+    lo = np.minimum(np.minimum(refs["gs_lex"], refs["gs_zebra"]), refs["gs_reverse"])
+    with brs.Context(n, n, n, a, block="line", method="gs", dtype="f64") as ctx:
+        ut, bt = to_dev(u0, "f64"), to_dev(b, "f64")
+        for k in range(10):
+            ctx.sweep(ut, bt, 1)
+            r = ctx.residual(ut, bt)
+            assert 0.9 * lo[k] <= r <= 1.1 * refs["jacobi"][k], (k, r, lo[k], refs["jacobi"][k])
+
+
+def test_chaotic_gs_converges_to_exact_solution(brs, orc):
+    n = 32
+    a = (1.0, 1.0, 1.0)
+    b = rhs((n, n, n))
+    ustar = orc.exact_solve(b, a)
+    with brs.Context(n, n, n, a, block="line", method="gs", dtype="f64") as ctx:
+        ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
+        ctx.sweep(ut, bt, 2500)
+        assert ctx.last_error() == 0
+        assert rel_max_err(to_np(ut), ustar) <= 1e-10
+
+
+def test_jacobi_converges_to_exact_solution(brs, orc):
+    n = 32
+    a = (1.0, 1.0, 0.01)
+    b = rhs((n, n, n))
+    ustar = orc.exact_solve(b, a)
+    with brs.Context(n, n, n, a, block="line", method="jacobi", dtype="f64") as ctx:
+        ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
+        ctx.sweep(ut, bt, 2000)
+        assert rel_max_err(to_np(ut), ustar) <= 1e-10
+
+
+# ----------------------------------------------------------------- full-size sampled parity
+
+def _sampled_lines(orc, u, b, a, got, lines, omega=0.8):
+    """Oracle Jacobi for selected lines from a 3x3-line neighbourhood sub-grid."""
+    nz, ny, nx = u.shape
+    worst = 0.0
+    for (j, k) in lines:
+        j0, j1 = max(0, j - 1), min(ny, j + 2)
+        k0, k1 = max(0, k - 1), min(nz, k + 2)
+        sub = orc.sweep(u[k0:k1, j0:j1], b[k0:k1, j0:j1], a, block="line", method="jacobi",
+                        omega=omega)
+        ref = sub[k - k0, j - j0]
+        worst = max(worst, rel_max_err(got[k, j], ref))
+    return worst
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("a", [(1.0, 1.0, 1.0), (1.0, 1.0, 0.01)], ids=["iso", "aniso"])
+def test_full_size_256_sampled_lines(brs, orc, dt, a):
+    """256^3 in the benchmark's launch configuration; ~60 lines checked against the oracle."""
+    import torch
+
+    n = 256
+    rng = np.random.default_rng(7)
+    ut = torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=torch.Generator(
+        device="cuda").manual_seed(2)) * 2 - 1
+    bt = (torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=torch.Generator(
+        device="cuda").manual_seed(1)) * 2 - 1) / (n + 1) ** 2
+    if dt == "f32":
+        ut, bt = ut.float(), bt.float()
+    u, b = to_np(ut), to_np(bt)
+    with brs.Context(n, n, n, a, dtype=dt) as ctx:
+        ctx.sweep(ut, bt, 1)
+        torch.cuda.synchronize()
+        assert ctx.last_error() == 0
+    got = to_np(ut)
+    lines = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (7, 8), (8, 7), (128, 129)]
+    lines += [tuple(x) for x in rng.integers(0, n, size=(50, 2))]
+    assert _sampled_lines(orc, u, b, a, got, lines) <= TOL[dt]
