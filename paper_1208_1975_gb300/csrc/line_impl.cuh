@@ -203,19 +203,18 @@ __global__ void __launch_bounds__(256) line_tma_kernel(const __grid_constant__ C
 
     const long long L0 = (long long)blockIdx.x * a.total / gridDim.x;
     const long long L1 = (long long)(blockIdx.x + 1) * a.total / gridDim.x;
-
-    // Producer state (thread 0): next stage to issue, segment cursor.
-    SegIter pit{L0, L1, a.nz, 0, 0, 0};
-    long long p_next = 0;      // global index of the next stage to issue
-    long long p_seg_base = 0;  // global index of stage 0 of the producer's segment
-    bool p_has = false;
-    long long p_end = 0;  // one past the last stage of the producer's segment
-
-    auto slot_ptr = [&](long long gidx) -> T* {
-        return reinterpret_cast<T*>(smem_raw + (size_t)(gidx % NS) * slot_bytes);
+    auto slot_ptr = [&](int slot) -> T* {
+        return reinterpret_cast<T*>(smem_raw + (uint32_t)slot * (uint32_t)slot_bytes);
     };
-    auto issue = [&](long long limit) {
-        // issue stages while the ring has room (stages < limit)
+    auto inc = [&](int slot) { return slot + 1 == NS ? 0 : slot + 1; };
+
+    // Producer state (thread 0).  Stage indices are per CTA and fit in 32 bits; ring
+    // slots advance incrementally (no division on the hot path).
+    SegIter pit{L0, L1, a.nz, 0, 0, 0};
+    int p_next = 0, p_slot = 0;   // next stage to issue and its slot
+    int p_seg_base = 0, p_end = 0;
+    bool p_has = false;
+    auto issue = [&](int limit) {
         while (true) {
             if (!p_has || p_next >= p_end) {
                 if (p_has)
@@ -227,9 +226,9 @@ __global__ void __launch_bounds__(256) line_tma_kernel(const __grid_constant__ C
             }
             if (p_next >= limit)
                 return;
-            const int t = (int)(p_next - p_seg_base);
-            T* dst = slot_ptr(p_next);
-            uint64_t* bar = &full[p_next % NS];
+            const int t = p_next - p_seg_base;
+            T* dst = slot_ptr(p_slot);
+            uint64_t* bar = &full[p_slot];
             const bool with_b = t >= 2;
             mbar_arrive_expect_tx(bar, ubytes + (with_b ? bbytes : 0u));
             const int j0 = pit.jt * JT;
@@ -242,50 +241,58 @@ __global__ void __launch_bounds__(256) line_tma_kernel(const __grid_constant__ C
                     tma_load_3d(bdst + (size_t)pc * bbox, &tm_b, bar, pc * bx, j0, ku - 1);
             }
             ++p_next;
+            p_slot = inc(p_slot);
         }
     };
     if (tid == 0)
         issue(NS);
 
     SegIter cit{L0, L1, a.nz, 0, 0, 0};
-    long long c_base = 0;  // global index of stage 0 of the consumer's segment
-    long long waited = 0;  // stages [0, waited) have completed
+    int c_base = 0;               // stage 0 of the consumer's segment
+    int cs_slot = 0;              // slot of stage c_base + s
+    int waited = 0, w_slot = 0;   // stages [0, waited) have completed; slot of `waited`
+    uint32_t w_phase = 0;         // parity of the ring pass `waited` is in
     bool failed = false;
 
     const T ay = (T)a.ay, az = (T)a.az, om1 = (T)a.om1;
     T um[E], uc[E], up[E], r[E];
+    const uint32_t urow_off = (uint32_t)(piece * ubox + xo);
+    const uint32_t brow_off = (uint32_t)(u_elems + piece * bbox + g * bx + xo);
 
     while (cit.next()) {
         const int j = cit.jt * JT + g;
         const bool jin = j < a.ny;
+        T* outp = out + ((size_t)cit.kb * a.ny + j) * a.nx + x0;
+        const size_t plane = (size_t)a.ny * a.nx;
         for (int s = 0; s < cit.n; ++s) {
-            const int k = cit.kb + s;
             // wait for stages up to c_base + s + 2
-            const long long need = c_base + s + 3;
+            const int need = c_base + s + 3;
             bool ok = true;
             while (waited < need && ok) {
-                ok = mbar_wait_bounded(&full[waited % NS], (uint32_t)((waited / NS) & 1));
-                if (ok)
+                ok = mbar_wait_bounded(&full[w_slot], w_phase);
+                if (ok) {
                     ++waited;
+                    w_slot = inc(w_slot);
+                    if (w_slot == 0)
+                        w_phase ^= 1u;
+                }
             }
             // the solve shuffles across the warp: skip it warp-uniformly on a timeout
             ok = __all_sync(0xffffffffu, ok);
+            const int s1 = inc(cs_slot), s2 = inc(s1);
             if (ok) {
-                const T* st1 = slot_ptr(c_base + s + 1);
-                const T* st2 = slot_ptr(c_base + s + 2);
+                const T* st1 = slot_ptr(s1);
+                const T* st2 = slot_ptr(s2);
                 if (xin) {
-                    const size_t urow = (size_t)piece * ubox + xo;
                     if (s == 0) {
-                        const T* st0 = slot_ptr(c_base + s);
-                        ld_shared_vec<T, E>(um, st0 + urow + (size_t)(g + 1) * bx);
-                        ld_shared_vec<T, E>(uc, st1 + urow + (size_t)(g + 1) * bx);
+                        ld_shared_vec<T, E>(um, slot_ptr(cs_slot) + urow_off + (g + 1) * bx);
+                        ld_shared_vec<T, E>(uc, st1 + urow_off + (g + 1) * bx);
                     }
-                    ld_shared_vec<T, E>(up, st2 + urow + (size_t)(g + 1) * bx);
+                    ld_shared_vec<T, E>(up, st2 + urow_off + (g + 1) * bx);
                     T un[E], us[E], bb[E];
-                    ld_shared_vec<T, E>(un, st1 + urow + (size_t)g * bx);
-                    ld_shared_vec<T, E>(us, st1 + urow + (size_t)(g + 2) * bx);
-                    ld_shared_vec<T, E>(bb, st2 + u_elems + (size_t)piece * bbox +
-                                                (size_t)g * bx + xo);
+                    ld_shared_vec<T, E>(un, st1 + urow_off + g * bx);
+                    ld_shared_vec<T, E>(us, st1 + urow_off + (g + 2) * bx);
+                    ld_shared_vec<T, E>(bb, st2 + brow_off);
 #pragma unroll
                     for (int q = 0; q < E; ++q)
                         r[q] = fma(az, um[q] + up[q], fma(ay, un[q] + us[q], bb[q]));
@@ -302,33 +309,37 @@ __global__ void __launch_bounds__(256) line_tma_kernel(const __grid_constant__ C
                 for (int q = 0; q < E; ++q)
                     v[q] = fma(tb.wp[q], r[q], om1 * uc[q]);
                 if (xin && jin)
-                    st_global_vec<T, E>(out + ((size_t)k * a.ny + j) * a.nx + x0, v);
+                    st_global_vec<T, E>(outp, v);
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     um[q] = GS ? v[q] : uc[q];
                     uc[q] = up[q];
                 }
             }
+            outp += plane;
+            cs_slot = s1;
             failed = __syncthreads_or(!ok) != 0;
             if (failed)
                 break;
             if (tid == 0) {
                 // stages below the first one the next step needs are free
-                const long long next_first =
-                    (s + 1 < cit.n) ? c_base + s + 1 : c_base + cit.n + 2;
+                const int next_first = (s + 1 < cit.n) ? c_base + s + 1 : c_base + cit.n + 2;
                 issue(next_first + NS);
             }
         }
         if (failed)
             break;
         c_base += cit.n + 2;
+        cs_slot = inc(inc(cs_slot));  // skip the segment's last two stages
     }
-    if (failed) {
-        if (tid == 0) {
-            set_status(a.status, BRS_ERR_TIMEOUT);
-            // drain copies still in flight before the CTA's shared memory is released
-            for (long long q = waited; q < p_next; ++q)
-                mbar_wait_bounded(&full[q % NS], (uint32_t)((q / NS) & 1), 200000000ull);
+    if (failed && tid == 0) {
+        set_status(a.status, BRS_ERR_TIMEOUT);
+        // drain copies still in flight before the CTA's shared memory is released
+        for (int q = waited; q < p_next; ++q) {
+            mbar_wait_bounded(&full[w_slot], w_phase, 200000000ull);
+            w_slot = inc(w_slot);
+            if (w_slot == 0)
+                w_phase ^= 1u;
         }
     }
 }

@@ -203,7 +203,7 @@ def test_chaotic_gs_converges_to_exact_solution(brs, orc):
     ustar = orc.exact_solve(b, a)
     with brs.Context(n, n, n, a, block="line", method="gs", dtype="f64") as ctx:
         ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
-        ctx.sweep(ut, bt, 2500)
+        ctx.sweep(ut, bt, 6000)  # rho ~ 0.9932 when each plane reads old neighbours
         assert ctx.last_error() == 0
         assert rel_max_err(to_np(ut), ustar) <= 1e-10
 
@@ -215,7 +215,7 @@ def test_jacobi_converges_to_exact_solution(brs, orc):
     ustar = orc.exact_solve(b, a)
     with brs.Context(n, n, n, a, block="line", method="jacobi", dtype="f64") as ctx:
         ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
-        ctx.sweep(ut, bt, 2000)
+        ctx.sweep(ut, bt, 6000)  # rho ~ 0.9928 for a = (1, 1, 0.01)
         assert rel_max_err(to_np(ut), ustar) <= 1e-10
 
 
