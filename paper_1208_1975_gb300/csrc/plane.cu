@@ -1,9 +1,317 @@
-// xy-plane block sweeps (Sec. 2 with full-plane blocks).
+// xy-plane block sweeps (Sec. 2 with one block per xy-plane).
+//
+// For plane k the sweep gathers the off-block (z) neighbours into the block right-hand
+// side and solves the plane block exactly:
+//   R_k = b_k + az (u_{k-1} + u_{k+1})
+//   M_plane X = R_k,  M_plane(X) = ax X Tx + ay Ty X + 2 az X   (X indexed [y][x])
+//   new u_k = (1-omega) u_k + omega X
+// M_plane is diagonal in the orthonormal DST-I basis S (S = S^T = S^{-1},
+// S T S = diag(s), s_p = 2 - 2 cos(p pi/(n+1))), so
+//   X = S_y [ (S_y R S_x) ./ L ] S_x,   L[q][p] = ax s_p + ay s_q + 2 az.
+// The basis and 1/L are built once per context on the host in FP64 (the constant block
+// is factored once and reused, Sec. 4.3).
+//
+// The four contractions run as batched "TN" products C = A B^T (both operands K-major,
+// one plane per batch index) chosen so that each pass's output is the next pass's
+// K-major operand:
+//   P1  C1[p][y] = sum_x Sx[p][x] R[y][x]
+//   P2  Q[p][q]  = (sum_y C1[p][y] Sy[q][y]) / L[q][p]
+//   P3  W[y][p]  = sum_q Sy[y][q] Q[p][q]
+//   P4  X[y][x]  = sum_p W[y][p] Sx[x][p]      -> fused Jacobi / GS update of plane k
+// Block Jacobi reads only old planes and writes the second vector.  Chaotic block GS
+// updates in place, even planes first and odd planes second, so odd planes read their
+// neighbours' new values (one admissible outcome of the unordered update of Alg. 1).
+#include <cmath>
+#include <vector>
+
 #include "plane.cuh"
 
-int plane_setup(brs_ctx*) { return BRS_ERR_UNSUPPORTED; }
-void plane_teardown(brs_ctx*) {}
-int plane_sweep_launch(brs_ctx*, const void*, void*, const void*, cudaStream_t)
+namespace {
+
+struct PlaneState {
+    int nx = 0, ny = 0;
+    int math = BRS_PLANE_SIMT;
+    void* sx = nullptr;    // [nx][nx] DST-I (context dtype)
+    void* sy = nullptr;    // [ny][ny]
+    void* ilam = nullptr;  // [nx][ny]: 1 / (ax s_p + ay s_q + 2 az) at [p][q]
+    void* t1 = nullptr;    // grid-sized intermediates
+    void* t2 = nullptr;
+};
+
+PlaneState* ps(brs_ctx* c)
 {
-    return BRS_ERR_UNSUPPORTED;
+    return static_cast<PlaneState*>(c->plane);
+}
+
+// ------------------------------------------------------------------- gather kernel
+// R_k = b_k + az (u_{k-1} + u_{k+1}) for planes k = k0, k0 + kstep, ...; R is packed by
+// batch index (batch i holds plane k0 + i*kstep).
+template <typename T>
+__global__ void plane_gather_kernel(const T* __restrict__ u, const T* __restrict__ b,
+                                    T* __restrict__ R, int nx, int ny, int nz, double az,
+                                    int k0, int kstep, int nbatch)
+{
+    const long long plane = (long long)nx * ny;
+    const long long total = plane * nbatch;
+    const T cz = (T)az;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long bi = t / plane;
+        const long long o = t - bi * plane;
+        const int k = k0 + (int)bi * kstep;
+        const long long g = (long long)k * plane + o;
+        const T s = (k > 0 ? u[g - plane] : T(0)) + (k + 1 < nz ? u[g + plane] : T(0));
+        R[t] = fma(cz, s, b[g]);
+    }
+}
+
+// ------------------------------------------------------------------- SIMT batched GEMM
+// C_b[m][n] = sum_k A_b[m][k] * B_b[n][k]  (both operands K-major), 64x64 tiles,
+// 256 threads, 4x4 outputs per thread.  Batch b uses A + b*strideA (strideA = 0 for a
+// shared basis matrix), likewise B and C.
+enum Epi { EPI_STORE = 0, EPI_SCALE = 1, EPI_UPDATE = 2 };
+
+struct GemmArgs {
+    int M, N, K;
+    long long strideA, strideB, strideC;  // elements per batch
+    const void* scale;                    // EPI_SCALE: [M][N] factors
+    const void* u;                        // EPI_UPDATE: old plane values, [M][N]
+    long long strideU;
+    int k0, kstep;                        // EPI_UPDATE: batch b -> plane k0 + b*kstep
+    double omega;
+};
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) gemm_tn_simt(const T* __restrict__ A,
+                                                    const T* __restrict__ B, T* C, GemmArgs g)
+{
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const int bidx = blockIdx.z;
+    const T* Ab = A + (long long)bidx * g.strideA;
+    const T* Bb = B + (long long)bidx * g.strideB;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            acc[i][j] = T(0);
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        // each thread loads 4 elements of A's and of B's 64x16 tile
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = threadIdx.x + r * 256;
+            const int row = idx / BK, kk = idx % BK;
+            const int gm = m0 + row, gn = n0 + row, gk = k0 + kk;
+            As[kk][row] = (gm < g.M && gk < g.K) ? Ab[(long long)gm * g.K + gk] : T(0);
+            Bs[kk][row] = (gn < g.N && gk < g.K) ? Bb[(long long)gn * g.K + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty + 16 * i];
+                bv[i] = Bs[kk][tx + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    T* Cb = C + (long long)bidx * g.strideC;
+    const T om = (T)g.omega, om1 = (T)(1.0 - g.omega);
+    const T* Ub = nullptr;
+    if (EPI == EPI_UPDATE)
+        Ub = static_cast<const T*>(g.u) + (long long)(g.k0 + bidx * g.kstep) * g.strideU;
+    if (EPI == EPI_UPDATE)
+        Cb = C + (long long)(g.k0 + bidx * g.kstep) * g.strideC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < g.M && n < g.N) {
+                const long long o = (long long)m * g.N + n;
+                T v = acc[i][j];
+                if (EPI == EPI_SCALE)
+                    v *= static_cast<const T*>(g.scale)[o];
+                if (EPI == EPI_UPDATE)
+                    v = fma(om, v, om1 * Ub[o]);
+                Cb[o] = v;
+            }
+        }
+}
+
+template <typename T, int EPI>
+cudaError_t launch_gemm(const T* A, const T* B, T* C, const GemmArgs& g, int batch,
+                        cudaStream_t s)
+{
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
+    gemm_tn_simt<T, EPI><<<grid, 256, 0, s>>>(A, B, C, g);
+    return cudaGetLastError();
+}
+
+// One plane-block solve + update for planes k0, k0+kstep, ... (nbatch of them), reading
+// neighbours from `uin` and writing the updated planes to `uout`.
+template <typename T>
+int plane_pass(brs_ctx* c, const T* uin, T* uout, const T* b, int k0, int kstep, int nbatch,
+               cudaStream_t s)
+{
+    PlaneState* P = ps(c);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const long long plane = (long long)nx * ny;
+    T* R = static_cast<T*>(P->t2);
+    T* T1 = static_cast<T*>(P->t1);
+    T* T2 = static_cast<T*>(P->t2);
+    const T* Sx = static_cast<const T*>(P->sx);
+    const T* Sy = static_cast<const T*>(P->sy);
+    {
+        const long long total = plane * nbatch;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 152 * 16)
+            blocks = 152 * 16;
+        plane_gather_kernel<T><<<blocks, 256, 0, s>>>(uin, b, R, nx, ny, nz, c->p.az, k0, kstep,
+                                                      nbatch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+    }
+    cudaError_t e;
+    GemmArgs g{};
+    // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]
+    g.M = nx; g.N = ny; g.K = nx; g.strideA = 0; g.strideB = plane; g.strideC = plane;
+    e = launch_gemm<T, EPI_STORE>(Sx, R, T1, g, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P2: Q[p][q] = (sum_y C1[p][y] Sy[q][y]) / L[q][p]
+    g = GemmArgs{};
+    g.M = nx; g.N = ny; g.K = ny; g.strideA = plane; g.strideB = 0; g.strideC = plane;
+    g.scale = P->ilam;
+    e = launch_gemm<T, EPI_SCALE>(T1, Sy, T2, g, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P3: W[y][p] = sum_q Sy[y][q] Q[p][q]
+    g = GemmArgs{};
+    g.M = ny; g.N = nx; g.K = ny; g.strideA = 0; g.strideB = plane; g.strideC = plane;
+    e = launch_gemm<T, EPI_STORE>(Sy, T2, T1, g, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P4: X[y][x] = sum_p W[y][p] Sx[x][p], then u_k <- (1-omega) u_k + omega X
+    g = GemmArgs{};
+    g.M = ny; g.N = nx; g.K = nx; g.strideA = plane; g.strideB = 0; g.strideC = plane;
+    g.u = uin; g.strideU = plane; g.k0 = k0; g.kstep = kstep; g.omega = c->omega;
+    e = launch_gemm<T, EPI_UPDATE>(T1, Sx, uout, g, nbatch, s);
+    return brs_cuda_status(e);
+}
+
+// Orthonormal DST-I matrix S[i][j] = sqrt(2/(n+1)) sin((i+1)(j+1) pi/(n+1)).
+std::vector<double> dst1(int n)
+{
+    std::vector<double> S((size_t)n * n);
+    const double sc = std::sqrt(2.0 / (n + 1));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            // reduce the angle index mod 2(n+1) before the sine for accuracy
+            const long long q = ((long long)(i + 1) * (j + 1)) % (2LL * (n + 1));
+            S[(size_t)i * n + j] = sc * std::sin(M_PI * (double)q / (n + 1));
+        }
+    return S;
+}
+
+template <typename T>
+int upload(void** dst, const std::vector<double>& src)
+{
+    std::vector<T> h(src.size());
+    for (size_t i = 0; i < src.size(); ++i)
+        h[i] = (T)src[i];
+    cudaError_t e = cudaMalloc(dst, h.size() * sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return brs_cuda_status(e);
+}
+
+}  // namespace
+
+int plane_setup(brs_ctx* c)
+{
+    const brs_params& p = c->p;
+    if (p.nx > 1024 || p.ny > 1024)
+        return BRS_ERR_UNSUPPORTED;
+    int math = p.plane_math;
+    if (p.dtype == BRS_F64 && (math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32))
+        return BRS_ERR_UNSUPPORTED;
+    if (math == BRS_PLANE_AUTO)
+        math = BRS_PLANE_SIMT;
+    if (math != BRS_PLANE_SIMT)
+        return BRS_ERR_UNSUPPORTED;
+    PlaneState* P = new PlaneState();
+    c->plane = P;
+    P->nx = p.nx;
+    P->ny = p.ny;
+    P->math = math;
+    std::vector<double> sx = dst1(p.nx), sy = dst1(p.ny), il((size_t)p.nx * p.ny);
+    for (int pp = 0; pp < p.nx; ++pp)
+        for (int q = 0; q < p.ny; ++q) {
+            const double spx = 2.0 - 2.0 * std::cos(M_PI * (pp + 1) / (p.nx + 1));
+            const double sqy = 2.0 - 2.0 * std::cos(M_PI * (q + 1) / (p.ny + 1));
+            il[(size_t)pp * p.ny + q] = 1.0 / (p.ax * spx + p.ay * sqy + 2.0 * p.az);
+        }
+    int rc;
+    if (p.dtype == BRS_F64)
+        rc = upload<double>(&P->sx, sx);
+    else
+        rc = upload<float>(&P->sx, sx);
+    if (rc == BRS_OK)
+        rc = p.dtype == BRS_F64 ? upload<double>(&P->sy, sy) : upload<float>(&P->sy, sy);
+    if (rc == BRS_OK)
+        rc = p.dtype == BRS_F64 ? upload<double>(&P->ilam, il) : upload<float>(&P->ilam, il);
+    const size_t bytes = (size_t)c->cells * c->esize;
+    if (rc == BRS_OK)
+        rc = brs_cuda_status(cudaMalloc(&P->t1, bytes));
+    if (rc == BRS_OK)
+        rc = brs_cuda_status(cudaMalloc(&P->t2, bytes));
+    return rc;
+}
+
+void plane_teardown(brs_ctx* c)
+{
+    PlaneState* P = ps(c);
+    if (!P)
+        return;
+    for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2})
+        if (q)
+            cudaFree(q);
+    delete P;
+    c->plane = nullptr;
+}
+
+int plane_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s)
+{
+    const int nz = c->p.nz;
+    const bool gs = c->p.method == BRS_CHAOTIC_GS;
+    auto run = [&](auto tag) -> int {
+        using T = decltype(tag);
+        const T* ui = static_cast<const T*>(uin);
+        T* uo = static_cast<T*>(uout);
+        const T* bb = static_cast<const T*>(b);
+        if (!gs)
+            return plane_pass<T>(c, ui, uo, bb, 0, 1, nz, s);
+        // in place: even planes, then odd planes (which read the new even planes)
+        int rc = plane_pass<T>(c, ui, uo, bb, 0, 2, (nz + 1) / 2, s);
+        if (rc == BRS_OK && nz > 1)
+            rc = plane_pass<T>(c, ui, uo, bb, 1, 2, nz / 2, s);
+        return rc;
+    };
+    if (c->p.dtype == BRS_F64)
+        return run(double{});
+    return run(float{});
 }

@@ -1,0 +1,145 @@
+"""xy-plane block sweeps on the GPU (sine-basis plane solve) against the FP64 oracle.
+
+The oracle solves each plane block with a once-factored banded Cholesky, so the two
+paths share nothing but the definition of the block.  Jacobi: element-wise per-sweep
+parity; chaotic GS: Perron bound, residual bracket and convergence to A^{-1} b.
+"""
+import numpy as np
+import pytest
+
+from brs_inputs import initial_guess, rhs, sine_mode
+from gpu_common import TOL, rel_max_err, rounded, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(16, 16, 8), (32, 24, 5), (33, 17, 4), (1, 1, 3), (64, 64, 4), (5, 70, 3),
+          (1, 9, 2), (100, 3, 3)]
+COEFFS = [(1.0, 1.0, 1.0), (1.0, 1.0, 0.01), (1.0, 0.1, 0.01)]
+
+
+@pytest.fixture(scope="module")
+def brs():
+    import paper_1208_1975_gb300 as brs
+
+    brs.build()
+    return brs
+
+
+def gpu_run(brs, u, b, a, *, dt, method="jacobi", nsweeps=1, math="auto", omega=0.0):
+    nz, ny, nx = u.shape
+    with brs.Context(nx, ny, nz, a, block="plane", method=method, dtype=dt, plane_math=math,
+                     omega=omega) as ctx:
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
+        ctx.sweep(ut, bt, nsweeps)
+        out = to_np(ut)
+        assert ctx.last_error() == 0
+    return out
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
+def test_plane_jacobi_one_sweep_parity(brs, orc, dt, shape, a):
+    nx, ny, nz = shape
+    u = rounded(initial_guess((nz, ny, nx)), dt)
+    b = rounded(rhs((nz, ny, nx)), dt)
+    ref = orc.sweep(u, b, a, block="plane", method="jacobi", omega=0.8)
+    got = gpu_run(brs, u, b, a, dt=dt)
+    assert rel_max_err(got, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("block", ["line", "plane"])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_single_mode_damping_on_gpu(brs, orc, block, dt):
+    """A sine mode is scaled by exactly g = 1 - omega lambda/mu per Jacobi sweep (b = 0)."""
+    nx, ny, nz = 24, 20, 12
+    a = (1.0, 0.1, 0.01)
+    g = orc.mode_factor(nx, ny, nz, a, block, 0.8)
+    for (p, q, r) in [(1, 1, 1), (24, 20, 12), (5, 17, 3)]:
+        m = rounded(sine_mode(nx, ny, nz, p, q, r), dt)
+        with brs.Context(nx, ny, nz, a, block=block, method="jacobi", dtype=dt) as ctx:
+            ut, bt = to_dev(m, dt), to_dev(np.zeros_like(m), dt)
+            ctx.sweep(ut, bt, 1)
+            got = to_np(ut)
+        # measured against the input's magnitude: a strongly damped mode (|g| << 1) is a
+        # small difference of O(|m|) terms, so its rounding scales with |m|, not with g|m|
+        err = np.max(np.abs(got - g[r - 1, q - 1, p - 1] * m)) / np.max(np.abs(m))
+        assert err <= 4 * TOL[dt]
+
+
+def test_plane_trajectory_and_norms(brs, orc):
+    n = 24
+    a = (1.0, 1.0, 0.01)
+    b = rhs((n, n, n))
+    u0 = initial_guess((n, n, n))
+    traj = orc.trajectory(u0, b, a, 6, block="plane", method="jacobi", omega=0.8)
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as ctx:
+        ut, bt = to_dev(u0, "f64"), to_dev(b, "f64")
+        for k in range(6):
+            ctx.sweep(ut, bt, 1)
+            assert rel_max_err(to_np(ut), traj[k]) <= 1e-12
+            ref = orc.residual_norm(traj[k], b, a)
+            assert abs(ctx.residual(ut, bt) - ref) <= 1e-11 * ref
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_plane_gs_perron_bound(brs, orc, dt):
+    nx, ny, nz = 32, 24, 20
+    a = (1.0, 1.0, 1.0)
+    m = sine_mode(nx, ny, nz, 1, 1, 1)
+    g = orc.mode_factor(nx, ny, nz, a, "plane", 1.0)[0, 0, 0]
+    slack = 1e-13 if dt == "f64" else 2e-6
+    with brs.Context(nx, ny, nz, a, block="plane", method="gs", dtype=dt) as ctx:
+        ut, bt = to_dev(m, dt), to_dev(np.zeros_like(m), dt)
+        mr = to_np(ut)
+        for k in range(1, 7):
+            ctx.sweep(ut, bt, 1)
+            u = to_np(ut)
+            assert np.all(u >= -slack * k)
+            assert np.all(u <= g ** k * mr + slack * (1 + k))
+
+
+def test_plane_gs_bracket_and_convergence(brs, orc):
+    n = 16
+    a = (1.0, 1.0, 0.01)
+    b = rhs((n, n, n))
+    u0 = initial_guess((n, n, n))
+    refs = {}
+    for meth in ("jacobi", "gs_lex", "gs_zebra", "gs_reverse"):
+        u, norms = u0, []
+        for _ in range(8):
+            u = orc.sweep(u, b, a, block="plane", method=meth, omega=1.0)
+            norms.append(orc.residual_norm(u, b, a))
+        refs[meth] = np.array(norms)
+    lo = np.minimum(np.minimum(refs["gs_lex"], refs["gs_zebra"]), refs["gs_reverse"])
+    with brs.Context(n, n, n, a, block="plane", method="gs", dtype="f64") as ctx:
+        ut, bt = to_dev(u0, "f64"), to_dev(b, "f64")
+        for k in range(8):
+            ctx.sweep(ut, bt, 1)
+            r = ctx.residual(ut, bt)
+            assert 0.9 * lo[k] <= r <= 1.1 * refs["jacobi"][k]
+        ctx.sweep(ut, bt, 400)
+        assert rel_max_err(to_np(ut), orc.exact_solve(b, a)) <= 1e-10
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_full_size_256_sampled_planes(brs, orc, dt):
+    """256^3 plane Jacobi, launch configuration of the benchmark; three planes vs the oracle."""
+    import torch
+
+    n = 256
+    a = (1.0, 1.0, 0.01)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    ut = torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+    bt = (torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen) * 2 - 1) / (n + 1) ** 2
+    if dt == "f32":
+        ut, bt = ut.float(), bt.float()
+    u, b = to_np(ut), to_np(bt)
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype=dt) as ctx:
+        ctx.sweep(ut, bt, 1)
+        torch.cuda.synchronize()
+    got = to_np(ut)
+    for k in (0, 131, n - 1):
+        k0, k1 = max(0, k - 1), min(n, k + 2)
+        sub = orc.sweep(u[k0:k1], b[k0:k1], a, block="plane", method="jacobi", omega=0.8)
+        assert rel_max_err(got[k], sub[k - k0]) <= TOL[dt]
