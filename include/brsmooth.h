@@ -84,7 +84,7 @@ typedef struct brs_params {
  * brsmooth_destroy.  Errors: BRS_ERR_ARG (null pointer, dims < 1, non-positive or
  * non-finite coefficient, omega >= 2, unknown enum), BRS_ERR_UNSUPPORTED
  * (e.g. TF32 plane math with BRS_F64, or a grid beyond the implemented maxima:
- * x-lines nx <= 1024; xy-planes nx, ny <= 1024), BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ * x-lines nx <= 512; xy-planes nx, ny <= 1024), BRS_ERR_NOMEM, BRS_ERR_CUDA.
  */
 int brsmooth_create(const brs_params* p, brs_ctx** out);
 
@@ -131,6 +131,38 @@ int brsmooth_last_error(brs_ctx* c);
 
 /* Static English text for a status code; never NULL. */
 const char* brsmooth_strerror(int code);
+
+/*
+ * Many independent patches of one refinement level (Sec. 1.1 patches; Sec. 4.2 mixed patch
+ * sizes), swept as one stream of work: every patch uses x-line blocks with the common
+ * coefficients, method, dtype and omega of `common` (its nx/ny/nz are ignored).
+ * `dims` (host) holds npatch triples (nx, ny, nz), each >= 1, nx <= 128.
+ * Packed layout: patch q occupies cells [off_q, off_q + nx*ny*nz) of one array, x fastest
+ * within the patch, off_q = sum of the earlier patches' cell counts (no padding).
+ * Creation runs the built-in autotuner (z-chunk length, warps per CTA, CTAs per SM),
+ * timing candidates on scratch arrays; results are cached per process.
+ * Errors: BRS_ERR_ARG (null, npatch < 1, a dim < 1, bad common params),
+ * BRS_ERR_UNSUPPORTED (xy-plane blocks, nx > 128), BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ */
+int brsmooth_create_batched(int npatch, const int* dims, const brs_params* common,
+                            brs_ctx** out);
+
+/*
+ * `nsweeps` sweeps over every patch of a batched context; u_packed (in/out) and b_packed
+ * are DEVICE arrays in the packed layout, 16-byte aligned.  One persistent launch per
+ * sweep pulls (patch, y-block, z-chunk) work items from an atomic queue, so uneven
+ * patches balance across the GPU.  The sweep sequence of a call is captured into a CUDA
+ * graph on the first call with a given (u, b, nsweeps) and replayed as one graph launch
+ * on `stream` afterwards (the graph is keyed by the pointers: reuse the same buffers).
+ * Block Jacobi ping-pongs with a context buffer and leaves the result in u_packed.
+ * Errors: as brsmooth_sweep; BRS_ERR_ARG if `c` is not a batched context.
+ */
+int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int nsweeps,
+                           void* stream);
+
+/* Launch shape the autotuner chose for a batched context (host outputs). */
+int brsmooth_batched_config(const brs_ctx* c, int* kchunk, int* warps_per_cta, int* ctas,
+                            int* work_items);
 
 /* Number of cell updates one sweep performs (nx*ny*nz summed over patches). */
 long long brsmooth_cells(const brs_ctx* c);

@@ -78,8 +78,13 @@ def lib():
     L.brsmooth_strerror.restype = ctypes.c_char_p
     L.brsmooth_cells.argtypes = [P]
     L.brsmooth_cells.restype = ctypes.c_longlong
+    L.brsmooth_create_batched.argtypes = [I, P, ctypes.POINTER(brs_params), ctypes.POINTER(P)]
+    L.brsmooth_sweep_batched.argtypes = [P, P, P, I, P]
+    IP = ctypes.POINTER(ctypes.c_int)
+    L.brsmooth_batched_config.argtypes = [P, IP, IP, IP, IP]
     for name in ("brsmooth_create", "brsmooth_sweep", "brsmooth_residual", "brsmooth_sweep_host",
-                 "brsmooth_destroy", "brsmooth_last_error"):
+                 "brsmooth_destroy", "brsmooth_last_error", "brsmooth_create_batched",
+                 "brsmooth_sweep_batched", "brsmooth_batched_config"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -151,6 +156,26 @@ def brsmooth_cells(ctx) -> int:
     return int(lib().brsmooth_cells(ctx))
 
 
+def brsmooth_create_batched(dims, p: brs_params):
+    import numpy as np
+
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1))
+    h = ctypes.c_void_p()
+    rc = lib().brsmooth_create_batched(len(d) // 3, ctypes.c_void_p(d.ctypes.data), ctypes.byref(p),
+                                       ctypes.byref(h))
+    return rc, h
+
+
+def brsmooth_sweep_batched(ctx, u_ptr, b_ptr, nsweeps: int, stream) -> int:
+    return lib().brsmooth_sweep_batched(ctx, u_ptr, b_ptr, int(nsweeps), ctypes.c_void_p(stream))
+
+
+def brsmooth_batched_config(ctx):
+    v = [ctypes.c_int() for _ in range(4)]
+    rc = lib().brsmooth_batched_config(ctx, *[ctypes.byref(x) for x in v])
+    return rc, tuple(x.value for x in v)
+
+
 # ------------------------------------------------------------------ convenience wrapper
 
 class Context:
@@ -218,6 +243,58 @@ class Context:
         rc = brsmooth_sweep_host(self.h, up, bp, nsweeps, _stream_handle(stream))
         _check(rc, "brsmooth_sweep_host")
         return u_host
+
+    def last_error(self) -> int:
+        return brsmooth_last_error(self.h)
+
+
+class BatchedContext:
+    """Many patches (x-line blocks, common coefficients/method/dtype) in one packed array."""
+
+    def __init__(self, dims, a=(1.0, 1.0, 1.0), *, method: str = "gs", dtype: str = "f32",
+                 omega: float = 0.0):
+        import numpy as np
+
+        self.dims = np.asarray(dims, dtype=np.int64).reshape(-1, 3)
+        self.dtype_code = DTYPES[dtype]
+        p = brs_params(1, 1, 1, float(a[0]), float(a[1]), float(a[2]), BRS_XLINE, METHODS[method],
+                       self.dtype_code, float(omega), BRS_PLANE_AUTO)
+        rc, h = brsmooth_create_batched(self.dims, p)
+        _check(rc, "brsmooth_create_batched")
+        self.h = h
+        sizes = self.dims.prod(axis=1)
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)])
+        self.cells = int(self.offsets[-1])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            brsmooth_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sweep(self, u, b, nsweeps: int = 1, stream=None):
+        rc = brsmooth_sweep_batched(self.h, _dptr(u, self.dtype_code, self.cells, "u"),
+                                    _dptr(b, self.dtype_code, self.cells, "b"), nsweeps,
+                                    _stream_handle(stream))
+        _check(rc, "brsmooth_sweep_batched")
+        return u
+
+    def config(self):
+        rc, cfg = brsmooth_batched_config(self.h)
+        _check(rc, "brsmooth_batched_config")
+        return dict(zip(("kchunk", "warps_per_cta", "ctas", "work_items"), cfg))
+
+    def patch(self, arr, q):
+        """View of patch q of a packed array as (nz, ny, nx)."""
+        nx, ny, nz = (int(v) for v in self.dims[q])
+        return arr[int(self.offsets[q]):int(self.offsets[q + 1])].reshape(nz, ny, nx)
 
     def last_error(self) -> int:
         return brsmooth_last_error(self.h)

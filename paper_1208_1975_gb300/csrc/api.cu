@@ -9,6 +9,7 @@
 #include <new>
 
 #include "brs_internal.cuh"
+#include "batched.cuh"
 #include "plane.cuh"
 
 int brs_cuda_status(cudaError_t e)
@@ -90,6 +91,7 @@ void free_ctx(brs_ctx* c)
         return;
     line_teardown(c);
     plane_teardown(c);
+    batched_teardown(c);
     if (c->scratch)
         cudaFree(c->scratch);
     if (c->partials)
@@ -224,6 +226,8 @@ int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     c->last_stream = s;
+    if (c->batch)
+        return batched_sweep(c, u, b, nsweeps, s);
     if (c->p.method == BRS_CHAOTIC_GS) {
         for (int k = 0; k < nsweeps && rc == BRS_OK; ++k)
             rc = sweep_one(c, u, u, b, s);
@@ -249,6 +253,8 @@ int brsmooth_residual(brs_ctx* c, const void* u, const void* b, void* r, double*
 {
     if (!c || !u || !b)
         return BRS_ERR_ARG;
+    if (c->batch)
+        return BRS_ERR_UNSUPPORTED;
     int rc = poll_status(c);
     if (rc != BRS_OK)
         return rc;
@@ -318,6 +324,72 @@ int brsmooth_last_error(brs_ctx* c)
     if (c->dev_status)
         *reinterpret_cast<volatile int*>(c->dev_status) = 0;
     return rc;
+}
+
+int brsmooth_create_batched(int npatch, const int* dims, const brs_params* common,
+                            brs_ctx** out)
+{
+    if (!out)
+        return BRS_ERR_ARG;
+    *out = nullptr;
+    if (npatch < 1 || !dims || !common)
+        return BRS_ERR_ARG;
+    brs_params p = *common;
+    p.nx = p.ny = p.nz = 1;
+    int rc = validate(&p);
+    if (rc != BRS_OK)
+        return rc;
+    if (p.block != BRS_XLINE)
+        return BRS_ERR_UNSUPPORTED;
+    long long total = 0;
+    for (int q = 0; q < npatch; ++q) {
+        const int nx = dims[3 * q], ny = dims[3 * q + 1], nz = dims[3 * q + 2];
+        if (nx < 1 || ny < 1 || nz < 1)
+            return BRS_ERR_ARG;
+        if (nx > 128)
+            return BRS_ERR_UNSUPPORTED;
+        total += (long long)nx * ny * nz;
+    }
+    if (total > (1ll << 36))
+        return BRS_ERR_UNSUPPORTED;
+    brs_ctx* c = new (std::nothrow) brs_ctx();
+    if (!c)
+        return BRS_ERR_NOMEM;
+    c->p = p;
+    c->omega = p.omega > 0.0 ? p.omega : (p.method == BRS_JACOBI ? 0.8 : 1.0);
+    c->esize = p.dtype == BRS_F64 ? 8 : 4;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc((void**)&c->dev_status, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return brs_cuda_status(e);
+    }
+    *c->dev_status = 0;
+    rc = batched_setup(c, npatch, dims);
+    if (rc != BRS_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return BRS_OK;
+}
+
+int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int nsweeps,
+                           void* stream)
+{
+    if (!c || !c->batch)
+        return BRS_ERR_ARG;
+    return brsmooth_sweep(c, u_packed, b_packed, nsweeps, stream);
+}
+
+int brsmooth_batched_config(const brs_ctx* c, int* kchunk, int* warps_per_cta, int* ctas,
+                            int* work_items)
+{
+    if (!c || !c->batch || !kchunk || !warps_per_cta || !ctas || !work_items)
+        return BRS_ERR_ARG;
+    batched_describe(c, kchunk, warps_per_cta, ctas, work_items);
+    return BRS_OK;
 }
 
 long long brsmooth_cells(const brs_ctx* c)

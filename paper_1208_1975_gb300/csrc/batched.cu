@@ -1,0 +1,570 @@
+// Batched x-line block sweeps over many independent patches of different sizes
+// (Sec. 1.1 / Sec. 4.2: an AMR level holds many patches; the GPU processes their blocks
+// as one stream of work, with no synchronisation between patches).
+//
+// Work items are (patch, y-block of R lines, z-chunk of KC planes).  A persistent grid
+// of warps pulls items from an atomic counter (load balance across uneven patches);
+// each warp marches its R lines in +z: u(j,k-1), u(j,k), u(j,k+1) stay in registers,
+// the y neighbours inside the warp come by shuffle and only the two halo lines of the
+// y-block are loaded.  Lines are solved exactly with the shared-pivot Thomas scan of the
+// single-grid path (the factor of M_line depends only on nx and the coefficients, so one
+// table per distinct nx is built once).  One launch per sweep; the sweep sequence of a
+// call is captured once into a CUDA graph and replayed as a single graph launch.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "batched.cuh"
+#include "line_impl.cuh"
+
+namespace {
+
+struct PatchDesc {
+    int nx, ny, nz;
+    int cls;          // lanes per line G = 4 << cls (E = 4 cells per lane)
+    long long off;    // element offset of the patch in the packed arrays
+    int item0;        // first work item of the patch
+    int njb;          // y-blocks (R = 32 / G lines each)
+    int nkc;          // z-chunks
+    int tab;          // element offset of the patch's line tables
+    int vec;          // rows and patch start are 16-byte aligned
+};
+
+struct Graph {
+    const void* u;
+    const void* b;
+    int nsweeps;
+    cudaGraphExec_t exec;
+};
+
+struct BatchState {
+    int npatch = 0;
+    std::vector<int> dims;      // 3 * npatch
+    long long total = 0;        // cells
+    int KC = 8;                 // z-chunk
+    int warps = 8;              // warps per CTA
+    int grid = 0;               // persistent CTAs
+    int nitems = 0;
+    PatchDesc* d_desc = nullptr;
+    int* d_item_patch = nullptr;
+    void* d_tab = nullptr;
+    int* d_counters = nullptr;  // one per sweep of a call
+    int ncounters = 0;
+    std::vector<PatchDesc> h_desc;
+    std::vector<int> h_item_patch;
+    cudaStream_t cap = nullptr; // private capture stream
+    std::vector<Graph> graphs;
+};
+
+BatchState* bs(brs_ctx* c)
+{
+    return static_cast<BatchState*>(c->batch);
+}
+
+constexpr int kE = 4;
+
+template <typename T, int G, bool GS>
+__device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc, int KC,
+                                             const T* uin, T* uout, const T* __restrict__ b,
+                                             const T* __restrict__ tab, T ay, T az, T om1)
+{
+    constexpr int R = 32 / G;
+    const int lanew = threadIdx.x & 31;
+    const int g = lanew / G, l = lanew % G;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const int j = jb * R + g;
+    const bool jin = j < ny;
+    const int x0 = l * kE;
+    const bool xin = x0 < nx;
+    const long long plane = (long long)nx * ny;
+    const T* ub = uin + d.off;
+    T* uo = uout + d.off;
+    const T* bb = b + d.off;
+    brs::LineTables<T, kE, G> tb;
+    tb.load(tab + d.tab, l);
+    const int k0 = kc * KC;
+    const int k1 = min(nz, k0 + KC);
+
+    // load E cells of line (jj, kk) of `src`, zero outside the patch
+    auto ld = [&](const T* src, int jj, int kk, T (&v)[kE]) {
+        if (xin && jj >= 0 && jj < ny && kk >= 0 && kk < nz) {
+            const T* p = src + (long long)kk * plane + (long long)jj * nx + x0;
+            if (d.vec) {
+                if (sizeof(T) == 4) {
+                    float4 f = *reinterpret_cast<const float4*>(p);
+                    v[0] = (T)f.x; v[1] = (T)f.y; v[2] = (T)f.z; v[3] = (T)f.w;
+                } else {
+                    const double2* q = reinterpret_cast<const double2*>(p);
+                    double2 f0 = q[0], f1 = q[1];
+                    v[0] = (T)f0.x; v[1] = (T)f0.y; v[2] = (T)f1.x; v[3] = (T)f1.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kE; ++q)
+                    v[q] = (x0 + q < nx) ? p[q] : T(0);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kE; ++q)
+                v[q] = T(0);
+        }
+    };
+
+    T um[kE], uc[kE], up[kE], r[kE], bv[kE], un[kE], us[kE];
+    ld(ub, j, k0 - 1, um);
+    ld(ub, j, k0, uc);
+    for (int k = k0; k < k1; ++k) {
+        ld(ub, j, k + 1, up);
+        ld(bb, j, k, bv);
+        // y neighbours: from the adjacent line group in the warp, halo lines from memory
+        T hn[kE], hs[kE];
+        if (g == 0)
+            ld(ub, j - 1, k, hn);
+        if (g == R - 1)
+            ld(ub, j + 1, k, hs);
+#pragma unroll
+        for (int q = 0; q < kE; ++q) {
+            T a = __shfl_up_sync(0xffffffffu, uc[q], G);
+            T c = __shfl_down_sync(0xffffffffu, uc[q], G);
+            un[q] = (g == 0) ? hn[q] : a;
+            us[q] = (g == R - 1) ? hs[q] : c;
+        }
+#pragma unroll
+        for (int q = 0; q < kE; ++q)
+            r[q] = (xin && jin) ? fma(az, um[q] + up[q], fma(ay, un[q] + us[q], bv[q])) : T(0);
+        brs::line_solve<T, kE, G>(r, tb, l);
+        T v[kE];
+#pragma unroll
+        for (int q = 0; q < kE; ++q)
+            v[q] = fma(tb.wp[q], r[q], om1 * uc[q]);
+        if (xin && jin) {
+            T* p = uo + (long long)k * plane + (long long)j * nx + x0;
+            if (d.vec && sizeof(T) == 4) {
+                *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1],
+                                                            (float)v[2], (float)v[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kE; ++q)
+                    if (x0 + q < nx)
+                        p[q] = v[q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kE; ++q) {
+            um[q] = GS ? ((xin && jin) ? v[q] : T(0)) : uc[q];
+            uc[q] = up[q];
+        }
+    }
+}
+
+template <typename T, bool GS>
+__global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __restrict__ desc,
+                                                           const int* __restrict__ item_patch,
+                                                           int nitems, int* counter, int KC,
+                                                           const T* uin, T* uout,
+                                                           const T* __restrict__ b,
+                                                           const T* __restrict__ tab,
+                                                           double ay, double az, double om1)
+{
+    const int lanew = threadIdx.x & 31;
+    while (true) {
+        int item = 0;
+        if (lanew == 0)
+            item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems)
+            return;
+        const PatchDesc d = desc[item_patch[item]];
+        const int local = item - d.item0;
+        const int jb = local % d.njb, kc = local / d.njb;
+        switch (d.cls) {
+        case 0: batched_item<T, 4, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
+        case 1: batched_item<T, 8, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
+        case 2: batched_item<T, 16, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
+        default: batched_item<T, 32, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
+        }
+    }
+}
+
+const void* kernel_for(int dtype, bool gs)
+{
+    if (dtype == BRS_F64)
+        return gs ? (const void*)batched_line_kernel<double, true>
+                  : (const void*)batched_line_kernel<double, false>;
+    return gs ? (const void*)batched_line_kernel<float, true>
+              : (const void*)batched_line_kernel<float, false>;
+}
+
+// Line tables of one nx for E = 4 and G lanes (same layout and recurrences as the
+// single-grid line path).
+std::vector<double> tables_for(int nx, int G, const brs_params& p, double omega)
+{
+    const int E = kE, NP = G * E;
+    int LG = 0;
+    while ((1 << LG) < G) ++LG;
+    const double d = 2.0 * (p.ax + p.ay + p.az);
+    std::vector<double> pv(NP, 0.0), c(NP, 0.0), e(NP, 0.0);
+    pv[0] = 1.0 / d;
+    for (int i = 1; i < nx; ++i)
+        pv[i] = 1.0 / (d - p.ax * p.ax * pv[i - 1]);
+    for (int i = 1; i < nx; ++i)
+        c[i] = p.ax * pv[i - 1];
+    for (int i = 0; i + 1 < nx; ++i)
+        e[i] = p.ax * pv[i + 1];
+    std::vector<double> Af(G, 1.0), Ab(G, 1.0);
+    for (int l = 0; l < G; ++l)
+        for (int q = 0; q < E; ++q) {
+            Af[l] *= c[l * E + q];
+            Ab[l] *= e[l * E + q];
+        }
+    std::vector<double> tab(3 * NP + 2 * LG * G);
+    for (int i = 0; i < NP; ++i) {
+        tab[i] = c[i];
+        tab[NP + i] = e[i];
+        tab[2 * NP + i] = i < nx ? omega * pv[i] : 0.0;
+    }
+    for (int t = 0; t < LG; ++t)
+        for (int l = 0; l < G; ++l) {
+            double f = 1.0, bb = 1.0;
+            for (int m = std::max(0, l - (1 << t) + 1); m <= l; ++m)
+                f *= Af[m];
+            for (int m = l; m < G && m < l + (1 << t); ++m)
+                bb *= Ab[m];
+            tab[3 * NP + t * G + l] = f;
+            tab[3 * NP + LG * G + t * G + l] = bb;
+        }
+    return tab;
+}
+
+int build_items(brs_ctx* c, int KC)
+{
+    BatchState* B = bs(c);
+    B->h_item_patch.clear();
+    int item = 0;
+    for (int q = 0; q < B->npatch; ++q) {
+        PatchDesc& d = B->h_desc[q];
+        const int G = 4 << d.cls, R = 32 / G;
+        d.njb = (d.ny + R - 1) / R;
+        d.nkc = (d.nz + KC - 1) / KC;
+        d.item0 = item;
+        const int n = d.njb * d.nkc;
+        for (int t = 0; t < n; ++t)
+            B->h_item_patch.push_back(q);
+        item += n;
+    }
+    B->nitems = item;
+    B->KC = KC;
+    if (B->d_desc)
+        cudaFree(B->d_desc);
+    if (B->d_item_patch)
+        cudaFree(B->d_item_patch);
+    B->d_desc = nullptr;
+    B->d_item_patch = nullptr;
+    cudaError_t e = cudaMalloc(&B->d_desc, sizeof(PatchDesc) * B->npatch);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_desc, B->h_desc.data(), sizeof(PatchDesc) * B->npatch,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&B->d_item_patch, sizeof(int) * std::max(1, item));
+    if (e == cudaSuccess && item > 0)
+        e = cudaMemcpy(B->d_item_patch, B->h_item_patch.data(), sizeof(int) * item,
+                       cudaMemcpyHostToDevice);
+    return brs_cuda_status(e);
+}
+
+int ensure_counters(BatchState* B, int n)
+{
+    if (B->ncounters >= n)
+        return BRS_OK;
+    if (B->d_counters)
+        cudaFree(B->d_counters);
+    B->d_counters = nullptr;
+    B->ncounters = 0;
+    cudaError_t e = cudaMalloc(&B->d_counters, sizeof(int) * n);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    B->ncounters = n;
+    return BRS_OK;
+}
+
+int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* counter,
+               cudaStream_t s)
+{
+    BatchState* B = bs(c);
+    const void* k = kernel_for(c->p.dtype, c->p.method == BRS_CHAOTIC_GS);
+    const PatchDesc* desc = B->d_desc;
+    const int* ip = B->d_item_patch;
+    int nitems = B->nitems, KC = B->KC;
+    const void* tab = B->d_tab;
+    double ay = c->p.ay, az = c->p.az, om1 = 1.0 - c->omega;
+    void* args[] = {(void*)&desc, (void*)&ip, &nitems, &counter, &KC, (void*)&uin, &uout,
+                    (void*)&b, (void*)&tab, &ay, &az, &om1};
+    return brs_cuda_status(
+        cudaLaunchKernel(k, dim3(B->grid), dim3(B->warps * 32), args, 0, s));
+}
+
+// Enqueue one call's sweeps (counter reset + one launch per sweep) on stream s.
+int enqueue_sweeps(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s)
+{
+    BatchState* B = bs(c);
+    cudaError_t e = cudaMemsetAsync(B->d_counters, 0, sizeof(int) * nsweeps, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    const bool gs = c->p.method == BRS_CHAOTIC_GS;
+    void* cur = u;
+    void* nxt = gs ? u : c->scratch;
+    int rc = BRS_OK;
+    for (int k = 0; k < nsweeps && rc == BRS_OK; ++k) {
+        rc = launch_one(c, cur, nxt, b, B->d_counters + k, s);
+        if (!gs)
+            std::swap(cur, nxt);
+    }
+    if (rc == BRS_OK && cur != u)
+        rc = brs_cuda_status(cudaMemcpyAsync(u, cur, (size_t)B->total * c->esize,
+                                             cudaMemcpyDeviceToDevice, s));
+    return rc;
+}
+
+int env_int(const char* name, int dflt)
+{
+    const char* v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+void set_shape(brs_ctx* c, int warps, int ctas_per_sm)
+{
+    BatchState* B = bs(c);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    B->warps = warps;
+    B->grid = std::max(1, sms * ctas_per_sm);
+}
+
+// Autotuner: time each candidate (z-chunk, warps per CTA, CTAs per SM) on scratch
+// arrays of the real patch set and keep the fastest.  Results are cached per process
+// keyed by the patch set, dtype and method.
+struct TuneKey {
+    std::vector<int> dims;
+    int dtype, method;
+    bool operator<(const TuneKey& o) const
+    {
+        if (dtype != o.dtype) return dtype < o.dtype;
+        if (method != o.method) return method < o.method;
+        return dims < o.dims;
+    }
+};
+struct TuneVal {
+    int KC, warps, cps;
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
+std::mutex g_tune_mutex;
+
+int autotune(brs_ctx* c)
+{
+    BatchState* B = bs(c);
+    TuneKey key{B->dims, c->p.dtype, c->p.method};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            set_shape(c, it->second.warps, it->second.cps);
+            return build_items(c, it->second.KC);
+        }
+    }
+    const int fixed_kc = env_int("BRSMOOTH_BATCH_KC", 0);
+    std::vector<TuneVal> cands;
+    for (int kc : {4, 8, 16, 32})
+        for (int w : {4, 8, 16})
+            for (int cps : {2, 4, 8}) {
+                if (w * cps > 64)
+                    continue;
+                if (fixed_kc && kc != fixed_kc)
+                    continue;
+                cands.push_back({kc, w, cps});
+            }
+    const size_t bytes = (size_t)B->total * c->esize;
+    void *tu = nullptr, *tb = nullptr;
+    cudaError_t e = cudaMalloc(&tu, bytes);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&tb, bytes);
+    if (e == cudaSuccess)
+        e = cudaMemset(tu, 0, bytes);
+    if (e == cudaSuccess)
+        e = cudaMemset(tb, 0, bytes);
+    int rc = brs_cuda_status(e);
+    if (rc == BRS_OK)
+        rc = ensure_counters(B, 4);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == BRS_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+    }
+    TuneVal best{8, 8, 4};
+    float best_ms = 1e30f;
+    for (const TuneVal& v : cands) {
+        if (rc != BRS_OK)
+            break;
+        set_shape(c, v.warps, v.cps);
+        rc = build_items(c, v.KC);
+        if (rc != BRS_OK)
+            break;
+        rc = enqueue_sweeps(c, tu, tb, 1, nullptr);  // warm
+        cudaEventRecord(e0, nullptr);
+        if (rc == BRS_OK)
+            rc = enqueue_sweeps(c, tu, tb, 3, nullptr);
+        cudaEventRecord(e1, nullptr);
+        if (cudaEventSynchronize(e1) != cudaSuccess && rc == BRS_OK)
+            rc = BRS_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == BRS_OK && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (tu)
+        cudaFree(tu);
+    if (tb)
+        cudaFree(tb);
+    if (rc != BRS_OK)
+        return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    set_shape(c, best.warps, best.cps);
+    return build_items(c, best.KC);
+}
+
+}  // namespace
+
+int batched_setup(brs_ctx* c, int npatch, const int* dims)
+{
+    BatchState* B = new BatchState();
+    c->batch = B;
+    B->npatch = npatch;
+    B->dims.assign(dims, dims + 3 * npatch);
+    std::map<int, int> tab_off;  // nx -> table offset
+    std::vector<double> tabs;
+    long long off = 0;
+    const long long align = 16 / (long long)c->esize;
+    for (int q = 0; q < npatch; ++q) {
+        PatchDesc d{};
+        d.nx = dims[3 * q];
+        d.ny = dims[3 * q + 1];
+        d.nz = dims[3 * q + 2];
+        d.cls = d.nx <= 16 ? 0 : d.nx <= 32 ? 1 : d.nx <= 64 ? 2 : 3;
+        d.off = off;
+        d.vec = (d.nx % 4 == 0) && (off % align == 0) && (d.nx * (long long)c->esize) % 16 == 0;
+        const int G = 4 << d.cls;
+        const int key = d.nx;
+        if (!tab_off.count(key)) {
+            tab_off[key] = (int)tabs.size();
+            auto t = tables_for(d.nx, G, c->p, c->omega);
+            tabs.insert(tabs.end(), t.begin(), t.end());
+        }
+        d.tab = tab_off[key];
+        B->h_desc.push_back(d);
+        off += (long long)d.nx * d.ny * d.nz;
+    }
+    B->total = off;
+    c->cells = off;
+    cudaError_t e;
+    if (c->p.dtype == BRS_F64) {
+        e = cudaMalloc(&B->d_tab, tabs.size() * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_tab, tabs.data(), tabs.size() * sizeof(double),
+                           cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> tf(tabs.begin(), tabs.end());
+        e = cudaMalloc(&B->d_tab, tf.size() * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_tab, tf.data(), tf.size() * sizeof(float),
+                           cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    if (c->p.method == BRS_JACOBI) {
+        e = cudaMalloc(&c->scratch, (size_t)B->total * c->esize);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+    }
+    const int kc = env_int("BRSMOOTH_BATCH_KC", 0);
+    if (env_int("BRSMOOTH_BATCH_NOTUNE", 0)) {
+        set_shape(c, 8, 4);
+        return build_items(c, kc ? kc : 8);
+    }
+    return autotune(c);
+}
+
+void batched_teardown(brs_ctx* c)
+{
+    BatchState* B = bs(c);
+    if (!B)
+        return;
+    for (auto& g : B->graphs)
+        cudaGraphExecDestroy(g.exec);
+    for (void* q : {(void*)B->d_desc, (void*)B->d_item_patch, B->d_tab, (void*)B->d_counters})
+        if (q)
+            cudaFree(q);
+    if (B->cap)
+        cudaStreamDestroy(B->cap);
+    delete B;
+    c->batch = nullptr;
+}
+
+int batched_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s)
+{
+    BatchState* B = bs(c);
+    if (nsweeps == 0)
+        return BRS_OK;
+    int rc = ensure_counters(B, nsweeps);
+    if (rc != BRS_OK)
+        return rc;
+    for (auto& g : B->graphs)
+        if (g.u == u && g.b == b && g.nsweeps == nsweeps)
+            return brs_cuda_status(cudaGraphLaunch(g.exec, s));
+    // capture this call's sweep sequence once on the private stream, replay on `s`
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    rc = enqueue_sweeps(c, u, b, nsweeps, B->cap);
+    e = cudaStreamEndCapture(B->cap, &graph);
+    if (rc != BRS_OK || e != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc != BRS_OK ? rc : brs_cuda_status(e);
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    if (B->graphs.size() >= 8) {
+        cudaGraphExecDestroy(B->graphs.front().exec);
+        B->graphs.erase(B->graphs.begin());
+    }
+    B->graphs.push_back({u, b, nsweeps, exec});
+    return brs_cuda_status(cudaGraphLaunch(exec, s));
+}
+
+void batched_describe(const brs_ctx* c, int* kc, int* warps, int* grid, int* nitems)
+{
+    const BatchState* B = static_cast<const BatchState*>(c->batch);
+    *kc = B->KC;
+    *warps = B->warps;
+    *grid = B->grid;
+    *nitems = B->nitems;
+}

@@ -67,6 +67,8 @@ struct brs_ctx {
     std::vector<TmapEntry> tmaps;
     // plane path state (owned by plane.cu)
     void* plane = nullptr;
+    // many-patch state (owned by batched.cu); non-null for batched contexts
+    void* batch = nullptr;
 };
 
 // Status helpers -------------------------------------------------------------------------
