@@ -164,6 +164,45 @@ int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int
 int brsmooth_batched_config(const brs_ctx* c, int* kchunk, int* warps_per_cta, int* ctas,
                             int* work_items);
 
+/*
+ * Mixed-precision defect correction (iterative refinement around the sweeps of Sec. 2,
+ * Eq. blockiteration2): starting from the device FP64 iterate `u` (in/out) and FP64
+ * right-hand side `b`, repeat
+ *   r = b - A u in FP64 (stored to FP32), stop if ||r||_2 / ||b||_2 <= rtol or after
+ *   max_outer corrections; c = 0; `inner_sweeps` sweeps of `inner_f32` on A c = r;
+ *   u = u + c in FP64.
+ * `outer_f64` must be a BRS_F64 single-grid context and `inner_f32` a BRS_F32 one with
+ * the same dims and coefficients (either block shape and method).  The inner context owns
+ * two FP32 grid buffers allocated on first use.  Host outputs (each nullable):
+ * *outer_done = corrections applied, *rel_residual = final ||r||/||b||, history[i] =
+ * ||r||/||b|| before correction i (max_outer + 1 entries).  Synchronises `stream` once
+ * per outer step (to read the norm).  Errors: BRS_ERR_ARG (mismatched or wrong-dtype
+ * contexts, null or misaligned arrays, inner_sweeps < 1, max_outer < 0, rtol < 0),
+ * BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ */
+int brsmooth_defect_correction(brs_ctx* outer_f64, brs_ctx* inner_f32, double* u,
+                               const double* b, double rtol, int inner_sweeps, int max_outer,
+                               int* outer_done, double* rel_residual, double* history,
+                               void* stream);
+
+/*
+ * One reverse-mode step of damped x-line block Jacobi (the transpose of one sweep of
+ * Eq. blockiteration2; A and M are symmetric).  For a loss L of the final iterate, with
+ * `lam` = dL/du_{k+1} on entry (device, in/out) and `u_k` the iterate the forward sweep
+ * started from (device, read):
+ *   mu = M^{-1} lam;   lam <- lam - omega A mu            (= dL/du_k on return)
+ *   grad_b[i] += omega mu[i]                               (device array, context dtype)
+ *   grad_a[d] += -omega mu . ((dM/da_d) z_k + T_d u_k)     (device double[3]: ax, ay, az)
+ * with z_k = M^{-1}(b - A u_k), T_d the second difference along axis d and, for x-line
+ * blocks, dM/dax = Tx, dM/day = dM/daz = 2I.  Calls for sweeps K-1 .. 0 in that order
+ * give dL/du_0 in `lam`, dL/db in grad_b and dL/da in grad_a.  The context owns one more
+ * grid buffer and reduction scratch, allocated on first use; the Jacobi scratch buffer
+ * is reused.  Errors: BRS_ERR_ARG (null), BRS_ERR_UNSUPPORTED (not a single-grid x-line
+ * block-Jacobi context), BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ */
+int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, const void* b,
+                           void* grad_b, double* grad_a, void* stream);
+
 /* Number of cell updates one sweep performs (nx*ny*nz summed over patches). */
 long long brsmooth_cells(const brs_ctx* c);
 

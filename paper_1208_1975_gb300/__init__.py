@@ -82,6 +82,11 @@ def lib():
     L.brsmooth_sweep_batched.argtypes = [P, P, P, I, P]
     IP = ctypes.POINTER(ctypes.c_int)
     L.brsmooth_batched_config.argtypes = [P, IP, IP, IP, IP]
+    DP = ctypes.POINTER(D)
+    L.brsmooth_defect_correction.argtypes = [P, P, P, P, D, I, I, IP, DP, DP, P]
+    L.brsmooth_defect_correction.restype = I
+    L.brsmooth_adjoint_sweep.argtypes = [P, P, P, P, P, P, P]
+    L.brsmooth_adjoint_sweep.restype = I
     for name in ("brsmooth_create", "brsmooth_sweep", "brsmooth_residual", "brsmooth_sweep_host",
                  "brsmooth_destroy", "brsmooth_last_error", "brsmooth_create_batched",
                  "brsmooth_sweep_batched", "brsmooth_batched_config"):
@@ -246,6 +251,112 @@ class Context:
 
     def last_error(self) -> int:
         return brsmooth_last_error(self.h)
+
+
+def brsmooth_defect_correction(outer, inner, u_ptr, b_ptr, rtol: float, inner_sweeps: int,
+                               max_outer: int, stream):
+    done = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    hist = (ctypes.c_double * (max_outer + 1))()
+    rc = lib().brsmooth_defect_correction(outer, inner, u_ptr, b_ptr, float(rtol), int(inner_sweeps),
+                                          int(max_outer), ctypes.byref(done), ctypes.byref(rel), hist,
+                                          ctypes.c_void_p(stream))
+    return rc, done.value, rel.value, list(hist)[: done.value + 1]
+
+
+def defect_correction(outer: "Context", inner: "Context", u, b, *, rtol: float = 1e-10,
+                      inner_sweeps: int = 32, max_outer: int = 1000, stream=None):
+    """Mixed-precision defect correction: FP64 outer residual/correction, FP32 inner sweeps.
+
+    `u` (FP64, in/out) and `b` (FP64) are CUDA tensors of outer's shape.  Returns
+    (corrections applied, final ||r||/||b||, history of ||r||/||b||).
+    """
+    rc, done, rel, hist = brsmooth_defect_correction(
+        outer.h, inner.h, _dptr(u, BRS_F64, outer.cells, "u"), _dptr(b, BRS_F64, outer.cells, "b"),
+        rtol, inner_sweeps, max_outer, _stream_handle(stream))
+    _check(rc, "brsmooth_defect_correction")
+    return done, rel, hist
+
+
+def brsmooth_adjoint_sweep(ctx, lam_ptr, u_ptr, b_ptr, gb_ptr, ga_ptr, stream) -> int:
+    return lib().brsmooth_adjoint_sweep(ctx, lam_ptr, u_ptr, b_ptr, gb_ptr, ga_ptr,
+                                        ctypes.c_void_p(stream))
+
+
+def _adjoint_step(c: "Context", lam, u_k, b, gb, ga, stream=None):
+    import torch
+
+    if ga.dtype != torch.float64 or not ga.is_cuda or ga.numel() != 3:
+        raise ValueError("grad_a must be a CUDA float64 tensor of 3 elements")
+    rc = brsmooth_adjoint_sweep(c.h, _dptr(lam, c.dtype_code, c.cells, "lam"),
+                                _dptr(u_k, c.dtype_code, c.cells, "u_k"),
+                                _dptr(b, c.dtype_code, c.cells, "b"),
+                                _dptr(gb, c.dtype_code, c.cells, "grad_b"),
+                                ctypes.c_void_p(ga.data_ptr()), _stream_handle(stream))
+    _check(rc, "brsmooth_adjoint_sweep")
+
+
+def _block_smooth_fn():
+    import torch
+
+    class BlockSmoothFn(torch.autograd.Function):
+        """u_K = K damped x-line block-Jacobi sweeps from u0 with right-hand side b.
+
+        Differentiable in b, u0 and the coefficients a = (ax, ay, az).  The forward keeps
+        the iterate every `ckpt` sweeps; the backward recomputes each segment from its
+        checkpoint and runs the library's adjoint sweeps from the last sweep to the first.
+        """
+
+        @staticmethod
+        def forward(fctx, b, u0, a, nsweeps: int, ckpt: int, omega: float):
+            nz, ny, nx = b.shape
+            dt = "f64" if b.dtype == torch.float64 else "f32"
+            av = tuple(float(x) for x in a.detach().cpu().tolist())
+            c = Context(nx, ny, nz, av, block="line", method="jacobi", dtype=dt, omega=omega)
+            b = b.detach().contiguous()
+            u = u0.detach().clone().contiguous()
+            ckpt = max(1, int(ckpt))
+            saved = []
+            for k in range(0, nsweeps, ckpt):
+                saved.append(u.clone())
+                c.sweep(u, b, min(ckpt, nsweeps - k))
+            fctx.c, fctx.nsweeps, fctx.ckpt = c, int(nsweeps), ckpt
+            fctx.a_meta = (a.dtype, a.device)
+            fctx.save_for_backward(b, *saved)
+            return u
+
+        @staticmethod
+        def backward(fctx, grad_u):
+            c, K, ck = fctx.c, fctx.nsweeps, fctx.ckpt
+            b, *saved = fctx.saved_tensors
+            lam = grad_u.detach().clone().contiguous()
+            gb = torch.zeros_like(b)
+            ga = torch.zeros(3, dtype=torch.float64, device=b.device)
+            for seg in range(len(saved) - 1, -1, -1):
+                k0 = seg * ck
+                k1 = min(K, k0 + ck)
+                us = [saved[seg]]
+                for _ in range(k0 + 1, k1):
+                    nxt = us[-1].clone()
+                    c.sweep(nxt, b, 1)
+                    us.append(nxt)
+                for k in range(k1 - 1, k0 - 1, -1):
+                    _adjoint_step(c, lam, us[k - k0], b, gb, ga)
+            adt, adev = fctx.a_meta
+            return gb, lam, ga.to(dtype=adt, device=adev), None, None, None
+
+    return BlockSmoothFn
+
+
+_BSF = None
+
+
+def block_smooth(b, u0, a, nsweeps: int = 8, *, ckpt: int = 4, omega: float = 0.8):
+    """Differentiable K-sweep x-line block Jacobi (see BlockSmoothFn)."""
+    global _BSF
+    if _BSF is None:
+        _BSF = _block_smooth_fn()
+    return _BSF.apply(b, u0, a, nsweeps, ckpt, omega)
 
 
 class BatchedContext:

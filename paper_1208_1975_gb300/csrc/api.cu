@@ -92,6 +92,7 @@ void free_ctx(brs_ctx* c)
     line_teardown(c);
     plane_teardown(c);
     batched_teardown(c);
+    adjoint_teardown(c);
     if (c->scratch)
         cudaFree(c->scratch);
     if (c->partials)
@@ -100,6 +101,10 @@ void free_ctx(brs_ctx* c)
         cudaFree(c->host_u_dev);
     if (c->host_b_dev)
         cudaFree(c->host_b_dev);
+    if (c->dc_r)
+        cudaFree(c->dc_r);
+    if (c->dc_c)
+        cudaFree(c->dc_c);
     if (c->dev_status)
         cudaFreeHost(c->dev_status);
     delete c;

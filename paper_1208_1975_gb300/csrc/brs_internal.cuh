@@ -69,6 +69,11 @@ struct brs_ctx {
     void* plane = nullptr;
     // many-patch state (owned by batched.cu); non-null for batched contexts
     void* batch = nullptr;
+    // defect-correction buffers of an FP32 inner context: residual and correction
+    float* dc_r = nullptr;
+    float* dc_c = nullptr;
+    // adjoint-sweep state (owned by adjoint.cu)
+    void* adjoint = nullptr;
 };
 
 // Status helpers -------------------------------------------------------------------------
@@ -85,6 +90,14 @@ int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cu
 int residual_setup(brs_ctx* c);
 int residual_launch(brs_ctx* c, const void* u, const void* b, void* r, bool want_norm,
                     cudaStream_t s);
+// FP64 residual of an FP64 context stored as FP32 (fused cast), norm into norm_dev.
+int residual_launch_f32out(brs_ctx* c, const double* u, const double* b, float* r,
+                           cudaStream_t s);
+// ||x||_2^2 of a grid array (context dtype) into norm_dev.
+int norm2sq_launch(brs_ctx* c, const void* x, cudaStream_t s);
+
+// Adjoint (adjoint.cu) ------------------------------------------------------------------------
+void adjoint_teardown(brs_ctx* c);
 
 // Tensor maps (api.cu) ---------------------------------------------------------------------
 // 3D tiled map over a grid array with box (bx, rows, 1); cached per (pointer, rows).

@@ -51,7 +51,7 @@ std::vector<T> line_tables(int nx, double ax, double ay, double az, double omega
             Af[l] *= c[l * E + q];
             Ab[l] *= e[l * E + q];
         }
-    std::vector<T> tab(3 * NP + 2 * LG * G);
+    std::vector<T> tab(4 * NP + 2 * LG * G);
     for (int i = 0; i < NP; ++i) {
         tab[i] = (T)c[i];
         tab[NP + i] = (T)e[i];
@@ -67,6 +67,9 @@ std::vector<T> line_tables(int nx, double ax, double ay, double az, double omega
             tab[3 * NP + t * G + l] = (T)f;
             tab[3 * NP + LG * G + t * G + l] = (T)b;
         }
+    // unscaled pivots p_i (x = p w) for the plain block solve of the adjoint
+    for (int i = 0; i < NP; ++i)
+        tab[3 * NP + 2 * LG * G + i] = (T)(i < nx ? p[i] : 0.0);
     return tab;
 }
 

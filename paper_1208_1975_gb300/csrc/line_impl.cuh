@@ -35,6 +35,7 @@ namespace brs {
 //   [2NP, 3NP)     omega * p_i (0 beyond nx)
 //   [3NP, 3NP+G*LG)       forward scan multipliers, step t at [t*G + lane]
 //   [3NP+G*LG, 3NP+2G*LG) backward scan multipliers
+//   [3NP+2G*LG, 4NP+2G*LG) p_i (0 beyond nx)
 template <int G>
 struct Log2 {
     static constexpr int value = (G <= 1) ? 0 : 1 + Log2<G / 2>::value;

@@ -9,10 +9,10 @@ namespace {
 
 constexpr int kResThreads = 256;
 
-template <typename T>
+template <typename T, typename TR>
 __global__ void __launch_bounds__(kResThreads) residual_kernel(const T* __restrict__ u,
                                                                const T* __restrict__ b,
-                                                               T* __restrict__ r, int nx, int ny,
+                                                               TR* __restrict__ r, int nx, int ny,
                                                                int nz, double ax, double ay,
                                                                double az, double* partials)
 {
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kResThreads) residual_kernel(const T* __restri
         // b - A u = b - d u + ax sx + ay sy + az sz
         const T rv = fma(cz, sz, fma(cy, sy, fma(cx, sx, fma(-dg, u[t], b[t]))));
         if (r)
-            r[t] = rv;
+            r[t] = (TR)rv;
         acc += (double)rv * (double)rv;
     }
     // block reduction in a fixed tree
@@ -86,24 +86,19 @@ int residual_setup(brs_ctx* c)
     return BRS_OK;
 }
 
-int residual_launch(brs_ctx* c, const void* u, const void* b, void* r, bool want_norm,
-                    cudaStream_t s)
+template <typename T, typename TR>
+int residual_run(brs_ctx* c, const T* u, const T* b, TR* r, bool want_norm, double ax,
+                 double ay, double az, cudaStream_t s)
 {
     const brs_params& p = c->p;
-    const long long n = (long long)p.nx * p.ny * p.nz;
+    const long long n = c->cells;
     long long need = (n + kResThreads - 1) / kResThreads;
     int blocks = (int)(need < c->npartials ? need : c->npartials);
     if (blocks < 1)
         blocks = 1;
     double* part = want_norm ? c->partials : nullptr;
-    if (p.dtype == BRS_F64)
-        residual_kernel<double><<<blocks, kResThreads, 0, s>>>(
-            (const double*)u, (const double*)b, (double*)r, p.nx, p.ny, p.nz, p.ax, p.ay, p.az,
-            part);
-    else
-        residual_kernel<float><<<blocks, kResThreads, 0, s>>>(
-            (const float*)u, (const float*)b, (float*)r, p.nx, p.ny, p.nz, p.ax, p.ay, p.az,
-            part);
+    residual_kernel<T, TR><<<blocks, kResThreads, 0, s>>>(u, b, r, p.nx, p.ny, p.nz, ax, ay, az,
+                                                          part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return brs_cuda_status(e);
@@ -112,4 +107,32 @@ int residual_launch(brs_ctx* c, const void* u, const void* b, void* r, bool want
         e = cudaGetLastError();
     }
     return brs_cuda_status(e);
+}
+
+int residual_launch(brs_ctx* c, const void* u, const void* b, void* r, bool want_norm,
+                    cudaStream_t s)
+{
+    const brs_params& p = c->p;
+    if (p.dtype == BRS_F64)
+        return residual_run<double, double>(c, (const double*)u, (const double*)b, (double*)r,
+                                            want_norm, p.ax, p.ay, p.az, s);
+    return residual_run<float, float>(c, (const float*)u, (const float*)b, (float*)r, want_norm,
+                                      p.ax, p.ay, p.az, s);
+}
+
+int residual_launch_f32out(brs_ctx* c, const double* u, const double* b, float* r,
+                           cudaStream_t s)
+{
+    const brs_params& p = c->p;
+    return residual_run<double, float>(c, u, b, r, true, p.ax, p.ay, p.az, s);
+}
+
+int norm2sq_launch(brs_ctx* c, const void* x, cudaStream_t s)
+{
+    // with zero coefficients the residual kernel returns b itself: ||x||^2 into norm_dev
+    if (c->p.dtype == BRS_F64)
+        return residual_run<double, double>(c, (const double*)x, (const double*)x, nullptr, true,
+                                            0.0, 0.0, 0.0, s);
+    return residual_run<float, float>(c, (const float*)x, (const float*)x, nullptr, true, 0.0,
+                                      0.0, 0.0, s);
 }
