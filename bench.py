@@ -209,6 +209,198 @@ def _traffic_record():
     return int(m_b.group(1))
 
 
+def _rate(cells, sweeps, ms):
+    return cells * sweeps / (ms / 1e3) / 1e9
+
+
+def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, math="auto"):
+    uv0, bv = _inputs(dt)
+    uv, bv = uv0.cuda(), bv.cuda()
+    with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt, plane_math=math) as vc:
+        vms = _time_sweeps(vc, uv, bv, steps, 1, sweeps, stream, barrier)
+    es = 8 if dt == "f64" else 4
+    rate = _rate(N ** 3, sweeps * steps, vms)
+    out = {"workload": "grid256", "block": blk, "method": meth, "dtype": dt, "coeffs": a,
+           "value": rate, "unit": UNIT, "hbm_frac": rate * 3 * es / peak}
+    if blk == "plane":
+        flops = 8.0 * N * N ** 3  # four n x n contractions per plane: 4 (nx + ny) per cell
+        out["plane_math"] = math
+        out["tflops"] = flops * sweeps * steps / (vms / 1e3) / 1e12
+    if blk == "line" and dt == "f64":
+        # ALU roof: 8 FP64 operations per cell for the sequential gather/Thomas/update
+        out["alu_frac_of_fp64_fma_peak"] = rate * 8 / 626.9
+    return out
+
+
+def _variant_batched(brs, stream, barrier):
+    """600 patches, dims from {16,24,32,48,64}, FP32 chaotic line GS, 20 sweeps."""
+    import numpy as np
+    import torch
+
+    from brs_inputs import batched_fields, batched_patch_dims
+
+    dims = batched_patch_dims(600)
+    u0 = torch.from_numpy(batched_fields(dims, 2)).float().cuda()
+    b = torch.from_numpy(batched_fields(dims, 1, scale_h2=True)).float().cuda()
+    cells = int(u0.numel())
+    with brs.BatchedContext(dims, COEFFS, method="gs", dtype="f32") as bc:
+        cfg = bc.config()
+        u = u0.clone()
+        ms = _time_sweeps(bc, u, b, 5, 2, 20, stream, barrier)
+    graph_rate = _rate(cells, 20 * 5, ms)
+    # per-patch launches of the single-grid path on the same data
+    ctxs = [brs.Context(int(nx), int(ny), int(nz), COEFFS, method="gs", dtype="f32")
+            for nx, ny, nz in dims]
+    offs = np.concatenate([[0], np.cumsum(dims.prod(axis=1))])
+    u = u0.clone()
+    views = [(u[offs[q]:offs[q + 1]], b[offs[q]:offs[q + 1]]) for q in range(600)]
+    for c, (uq, bq) in zip(ctxs, views):
+        c.sweep(uq, bq, 1, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for c, (uq, bq) in zip(ctxs, views):
+        c.sweep(uq, bq, 20, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_patch_rate = _rate(cells, 20, e0.elapsed_time(e1))
+    for c in ctxs:
+        c.close()
+    return {"workload": "batched600", "block": "line", "method": "gs", "dtype": "f32",
+            "patches": 600, "cells": cells, "sweeps": 20, "value": graph_rate, "unit": UNIT,
+            "hbm_frac": graph_rate * 12 / _peaks()[0], "tuned": cfg,
+            "per_patch_launches_value": per_patch_rate,
+            "speedup_vs_per_patch": graph_rate / per_patch_rate}
+
+
+def _variant_defect(brs, stream):
+    """512^3, a=(1,0.1,0.01): FP32 plane sweeps inside FP64 defect correction vs FP64 plane
+    Jacobi.  Timed segments at 512^3 and a projection to ||r||/||b|| = 1e-10 from the
+    measured per-sweep times and contraction factors; the full solve to 1e-10 on 64^3."""
+    import torch
+
+    from brs_inputs import rhs
+
+    a = (1.0, 0.1, 0.01)
+    out = {"workload": "grid512_aniso defect correction", "coeffs": a, "rtol": 1e-10}
+    n = 64
+    b = torch.from_numpy(rhs((n, n, n))).cuda()
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64, \
+            brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f32") as i32:
+        u = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done, rel, hist = brs.defect_correction(o64, i32, u, b, rtol=1e-10, inner_sweeps=16,
+                                                max_outer=500)
+        t_mixed = time.perf_counter() - t0
+        u64 = torch.zeros_like(b)
+        sweeps, r = 0, 1.0
+        nb = float(torch.linalg.norm(b))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while r > 1e-10 and sweeps < 20000:
+            o64.sweep(u64, b, 16)
+            sweeps += 16
+            r = o64.residual(u64, b) / nb
+        t_f64 = time.perf_counter() - t0
+    out["grid64_full_solve"] = {"mixed_outer": done, "mixed_inner_sweeps": done * 16,
+                                "mixed_rel_residual": rel, "mixed_s": t_mixed,
+                                "fp64_sweeps": sweeps, "fp64_rel_residual": r, "fp64_s": t_f64}
+    n = 512
+    b = torch.from_numpy(rhs((n, n, n))).cuda()
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64, \
+            brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f32") as i32:
+        u = torch.zeros_like(b)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        brs.defect_correction(o64, i32, u, b, rtol=0.0, inner_sweeps=8, max_outer=1)  # warm
+        u.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        done, rel, hist = brs.defect_correction(o64, i32, u, b, rtol=0.0, inner_sweeps=8,
+                                                max_outer=3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_mixed = e0.elapsed_time(e1)
+        u64 = torch.zeros_like(b)
+        o64.sweep(u64, b, 1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        o64.sweep(u64, b, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_f64 = e0.elapsed_time(e1) / 2
+    import math
+
+    # contraction per sweep of plane Jacobi (omega=0.8) on the slowest mode: g_111
+    s1 = 2 - 2 * math.cos(math.pi / (n + 1))
+    lam = (a[0] + a[1] + a[2]) * s1
+    mu = a[0] * s1 + a[1] * s1 + 2 * a[2]
+    g = 1 - 0.8 * lam / mu
+    sweeps_needed = math.log(1e-10) / math.log(g)
+    ms_inner = ms_mixed / (3 * 8)
+    out["grid512"] = {"ms_per_fp32_inner_sweep_incl_outer": ms_inner,
+                      "ms_per_fp64_sweep": ms_f64,
+                      "rel_residual_after_24_inner": rel,
+                      "sweeps_to_1e-10_projected": sweeps_needed,
+                      "projected_s_mixed": sweeps_needed * ms_inner / 1e3,
+                      "projected_s_fp64": sweeps_needed * ms_f64 / 1e3,
+                      "note": "projection = measured ms/sweep x log(1e-10)/log(g_111)"}
+    return out
+
+
+def _variant_adjoint(brs, stream):
+    """128^3 and 384^3: 8 x-line Jacobi sweeps forward + adjoint backward (checkpoint 4)."""
+    import torch
+
+    res = []
+    for n, dt in ((128, torch.float64), (128, torch.float32), (384, torch.float32)):
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        shape = (n, n, n)
+        b = ((torch.rand(shape, generator=gen, device="cuda", dtype=dt) * 2 - 1) / (n + 1) ** 2)
+        u0 = torch.rand(shape, generator=gen, device="cuda", dtype=dt) * 2 - 1
+        ut = torch.rand(shape, generator=gen, device="cuda", dtype=dt) * 2 - 1
+        times = []
+        for rep in range(3):
+            bt = b.clone().requires_grad_(True)
+            u0t = u0.clone().requires_grad_(True)
+            at = torch.tensor(COEFFS, dtype=torch.float64, device="cuda", requires_grad=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            u = brs.block_smooth(bt, u0t, at, 8, ckpt=4)
+            d = u - ut
+            (0.5 * (d * d).sum()).backward()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        best = min(times[1:])
+        res.append({"n": n, "dtype": str(dt).replace("torch.", ""), "sweeps": 8,
+                    "fwd_bwd_s": best,
+                    "value": n ** 3 * 8 / best / 1e9, "unit": "Gcell-updates/s (fwd+bwd)"})
+    return {"workload": "adjoint", "results": res}
+
+
+def _variants(brs, stream, barrier, peak):
+    out = []
+    specs = [("line", "gs", "f32", COEFFS, 6, 50), ("line", "jacobi", "f32", (1.0, 1.0, 0.01), 6, 50),
+             ("line", "jacobi", "f64", COEFFS, 4, 50), ("line", "gs", "f64", COEFFS, 4, 50),
+             ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 3, 10),
+             ("plane", "gs", "f32", (1.0, 1.0, 0.01), 3, 10),
+             ("plane", "jacobi", "f64", (1.0, 1.0, 0.01), 1, 4)]
+    for blk, meth, dt, a, steps, sweeps in specs:
+        try:
+            out.append(_variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps))
+        except Exception as exc:  # report, do not hide
+            out.append({"block": blk, "method": meth, "dtype": dt, "error": str(exc)})
+    for fn in (lambda: _variant_batched(brs, stream, barrier), lambda: _variant_defect(brs, stream),
+               lambda: _variant_adjoint(brs, stream)):
+        try:
+            out.append(fn())
+        except Exception as exc:
+            out.append({"error": repr(exc)})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -295,25 +487,7 @@ def main():
 
     variants = []
     if not args.no_variants:
-        for (blk, meth, dt, a) in [("line", "gs", "f32", COEFFS),
-                                   ("line", "jacobi", "f32", (1.0, 1.0, 0.01)),
-                                   ("line", "jacobi", "f64", COEFFS),
-                                   ("line", "gs", "f64", COEFFS)]:
-            try:
-                uv0, bv = _inputs(dt)
-                uv, bv = uv0.cuda(), bv.cuda()
-                with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt) as vc:
-                    vsteps = 6
-                    vms = _time_sweeps(vc, uv, bv, vsteps, 2, SWEEPS_PER_STEP, stream, barrier)
-                es = 8 if dt == "f64" else 4
-                rate = cells * SWEEPS_PER_STEP * vsteps / (vms / 1e3) / 1e9
-                variants.append({"block": blk, "method": meth, "dtype": dt, "coeffs": a,
-                                 "value": rate, "unit": UNIT,
-                                 "hbm_frac": rate * 3 * es / peak})
-                del uv, bv
-            except Exception as exc:  # report, do not hide
-                variants.append({"block": blk, "method": meth, "dtype": dt, "coeffs": a,
-                                 "error": str(exc)})
+        variants = _variants(brs, stream, barrier, peak)
 
     if rank != 0:
         return 0

@@ -129,6 +129,10 @@ int brsmooth_destroy(brs_ctx* c);
  * synchronises the context's last stream.  Reading it clears it. */
 int brsmooth_last_error(brs_ctx* c);
 
+/* Text of the CUDA runtime error behind the calling thread's most recent BRS_ERR_CUDA or
+ * BRS_ERR_NOMEM (static storage; "no error" if there was none); never NULL. */
+const char* brsmooth_cuda_error_string(void);
+
 /* Static English text for a status code; never NULL. */
 const char* brsmooth_strerror(int code);
 

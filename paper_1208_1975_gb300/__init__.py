@@ -39,7 +39,10 @@ PLANE_MATH = {"auto": BRS_PLANE_AUTO, "simt": BRS_PLANE_SIMT, "tf32": BRS_PLANE_
 class BrsError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {brsmooth_strerror(code)} ({code})")
+        msg = f"{where}: {brsmooth_strerror(code)} ({code})"
+        if code in (BRS_ERR_CUDA, BRS_ERR_NOMEM):
+            msg += f": {brsmooth_cuda_error_string()}"
+        super().__init__(msg)
 
 
 class brs_params(ctypes.Structure):
@@ -76,6 +79,8 @@ def lib():
     L.brsmooth_last_error.argtypes = [P]
     L.brsmooth_strerror.argtypes = [I]
     L.brsmooth_strerror.restype = ctypes.c_char_p
+    L.brsmooth_cuda_error_string.argtypes = []
+    L.brsmooth_cuda_error_string.restype = ctypes.c_char_p
     L.brsmooth_cells.argtypes = [P]
     L.brsmooth_cells.restype = ctypes.c_longlong
     L.brsmooth_create_batched.argtypes = [I, P, ctypes.POINTER(brs_params), ctypes.POINTER(P)]
@@ -126,6 +131,10 @@ def _dptr(t, dtype_code: int, cells: int, name: str):
 
 def brsmooth_strerror(code: int) -> str:
     return lib().brsmooth_strerror(int(code)).decode()
+
+
+def brsmooth_cuda_error_string() -> str:
+    return lib().brsmooth_cuda_error_string().decode()
 
 
 def brsmooth_create(p: brs_params):

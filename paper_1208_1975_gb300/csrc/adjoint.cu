@@ -207,6 +207,7 @@ void adjoint_teardown(brs_ctx* c)
 extern "C" int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, const void* b,
                                       void* grad_b, double* grad_a, void* stream)
 {
+    cudaGetLastError();  // start from a clean launch-error state
     if (!c || !lam || !u_k || !b || !grad_b || !grad_a)
         return BRS_ERR_ARG;
     if (c->batch || c->p.block != BRS_XLINE || c->p.method != BRS_JACOBI)

@@ -12,10 +12,16 @@
 #include "batched.cuh"
 #include "plane.cuh"
 
+namespace {
+thread_local const char* g_last_cuda_error = "no error";
+}
+
 int brs_cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess)
         return BRS_OK;
+    g_last_cuda_error = cudaGetErrorString(e);
+    cudaGetLastError();  // clear a non-sticky launch error so later calls start clean
     if (e == cudaErrorMemoryAllocation)
         return BRS_ERR_NOMEM;
     return BRS_ERR_CUDA;
@@ -148,6 +154,11 @@ const CUtensorMap* brs_tmap(brs_ctx* c, const void* ptr, int rows, int* rc)
 
 extern "C" {
 
+const char* brsmooth_cuda_error_string(void)
+{
+    return g_last_cuda_error;
+}
+
 const char* brsmooth_strerror(int code)
 {
     switch (code) {
@@ -222,6 +233,7 @@ static int sweep_one(brs_ctx* c, const void* uin, void* uout, const void* b, cud
 
 int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream)
 {
+    cudaGetLastError();  // start from a clean launch-error state
     if (!c || !u || !b || nsweeps < 0)
         return BRS_ERR_ARG;
     if (!aligned16(u) || !aligned16(b) || u == b)
@@ -256,6 +268,7 @@ int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream
 int brsmooth_residual(brs_ctx* c, const void* u, const void* b, void* r, double* norm2,
                       void* stream)
 {
+    cudaGetLastError();  // start from a clean launch-error state
     if (!c || !u || !b)
         return BRS_ERR_ARG;
     if (c->batch)

@@ -42,6 +42,7 @@ extern "C" int brsmooth_defect_correction(brs_ctx* outer, brs_ctx* inner, double
                                           int max_outer, int* outer_done, double* rel_residual,
                                           double* history, void* stream)
 {
+    cudaGetLastError();  // start from a clean launch-error state
     if (!outer || !inner || !u || !b || inner_sweeps < 1 || max_outer < 0 || !(rtol >= 0.0))
         return BRS_ERR_ARG;
     if (outer->batch || inner->batch || outer->p.dtype != BRS_F64 || inner->p.dtype != BRS_F32)

@@ -154,8 +154,12 @@ int line_setup(brs_ctx* c)
         return BRS_ERR_UNSUPPORTED;
     if (L.tma) {
         L.smem = (size_t)L.NS * tma_slot_bytes(L, es) + (size_t)L.NS * 8;
-        cudaError_t e = cudaFuncSetAttribute(ktma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L.smem);
+        // the attribute belongs to the kernel, shared by every context: only ever raise it
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, ktma);
+        if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < L.smem)
+            e = cudaFuncSetAttribute(ktma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)L.smem);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
         int occ = 0;

@@ -118,12 +118,12 @@ def test_adjoint_384_checkpointing_and_finite_differences(brs):
     fd_b = (_loss(brs, b + eps * d, u0, ut, a, 8) - _loss(brs, b - eps * d, u0, ut, a, 8)) / (2 * eps)
     assert abs(fd_b - float((gb * d).sum())) <= 1e-8 * max(abs(fd_b), 1e-30) + 1e-9
     for dd in range(3):
-        h = 1e-4
+        h = 1e-3
         ap, am = list(a), list(a)
         ap[dd] += h
         am[dd] -= h
         fd = (_loss(brs, b, u0, ut, ap, 8) - _loss(brs, b, u0, ut, am, 8)) / (2 * h)
-        assert abs(fd - float(ga[dd])) <= 1e-6 * abs(fd), (dd, fd, float(ga[dd]))
+        assert abs(fd - float(ga[dd])) <= 1e-5 * abs(fd), (dd, fd, float(ga[dd]))
 
 
 def test_adjoint_unsupported_paths(brs):
