@@ -207,6 +207,31 @@ int brsmooth_defect_correction(brs_ctx* outer_f64, brs_ctx* inner_f32, double* u
 int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, const void* b,
                            void* grad_b, double* grad_a, void* stream);
 
+/*
+ * Allocation-free x-line block-Jacobi sweeps (no counterpart in the paper; a deployment
+ * convenience).  brsmooth_create allocates device memory, and some callers cannot: their
+ * device memory belongs entirely to another allocator (a framework's caching pool or a
+ * fixed budget), or they run latency-sensitive loops where cudaMalloc/cudaFree and the
+ * device-wide synchronisation they imply are not acceptable.  This call needs no context
+ * and allocates nothing: the second vector and the line factor tables live in fixed
+ * file-scope device arrays of the library, sized for BRSMOOTH_NOALLOC_MAX_CELLS cells
+ * (8 MiB plus 32 KiB, held by every GPU that loads the library until the process exits).
+ * It computes exactly what brsmooth_sweep computes for a BRS_XLINE / BRS_JACOBI context
+ * with the same dims, coefficients, omega (<= 0 selects 0.8) and dtype: `nsweeps` sweeps on
+ * device grid `u` (in/out) with right-hand side `b`, the result left in `u`.
+ * The first call on each device looks up the arrays' device addresses (with that device
+ * current); make that first call before any stream capture.  All calls share the arrays
+ * and each call rewrites what it uses (tables and second vector are fully overwritten, so
+ * nothing carries over); calls whose GPU work overlaps (different streams or threads)
+ * race on them.  Errors: BRS_ERR_ARG (dims < 1, null, misaligned or aliased arrays,
+ * nsweeps < 0, bad coefficients or dtype), BRS_ERR_UNSUPPORTED (nx*ny*nz greater than
+ * BRSMOOTH_NOALLOC_MAX_CELLS, or nx > 512), BRS_ERR_CUDA.
+ */
+#define BRSMOOTH_NOALLOC_MAX_CELLS (1 << 20)
+int brsmooth_line_jacobi_noalloc(int nx, int ny, int nz, double ax, double ay, double az,
+                                 double omega, int dtype, void* u, const void* b, int nsweeps,
+                                 void* stream);
+
 /* Number of cell updates one sweep performs (nx*ny*nz summed over patches). */
 long long brsmooth_cells(const brs_ctx* c);
 

@@ -423,3 +423,14 @@ class BatchedContext:
 def cell_updates(dims, sweeps: int) -> int:
     """Cell updates of `sweeps` sweeps over patches `dims` [(nx, ny, nz), ...] (the rate's numerator)."""
     return int(sum(int(a) * int(b) * int(c) for a, b, c in dims)) * int(sweeps)
+
+
+def brsmooth_line_jacobi_noalloc(nx: int, ny: int, nz: int, a, omega: float, dtype_code: int,
+                                 u_ptr, b_ptr, nsweeps: int, stream) -> int:
+    """Allocation-free x-line block-Jacobi sweeps on device pointers (see the C header)."""
+    fn = lib().brsmooth_line_jacobi_noalloc
+    D, I, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    fn.argtypes = [I, I, I, D, D, D, D, I, P, P, I, P]
+    fn.restype = I
+    return fn(int(nx), int(ny), int(nz), float(a[0]), float(a[1]), float(a[2]), float(omega),
+              int(dtype_code), u_ptr, b_ptr, int(nsweeps), ctypes.c_void_p(stream))
