@@ -118,6 +118,11 @@ void free_ctx(brs_ctx* c)
 
 }  // namespace
 
+PFN_encode_tiled brs_encoder()
+{
+    return reinterpret_cast<PFN_encode_tiled>(encoder());
+}
+
 const CUtensorMap* brs_tmap(brs_ctx* c, const void* ptr, int rows, int* rc)
 {
     for (auto& t : c->tmaps)

@@ -100,6 +100,12 @@ int norm2sq_launch(brs_ctx* c, const void* x, cudaStream_t s);
 void adjoint_teardown(brs_ctx* c);
 
 // Tensor maps (api.cu) ---------------------------------------------------------------------
+typedef CUresult (*PFN_encode_tiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                     const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                     const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// cuTensorMapEncodeTiled from the driver (nullptr if unavailable).
+PFN_encode_tiled brs_encoder();
 // 3D tiled map over a grid array with box (bx, rows, 1); cached per (pointer, rows).
 const CUtensorMap* brs_tmap(brs_ctx* c, const void* ptr, int rows, int* rc);
 

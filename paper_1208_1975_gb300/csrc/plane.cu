@@ -22,21 +22,37 @@
 // updates in place, even planes first and odd planes second, so odd planes read their
 // neighbours' new values (one admissible outcome of the unordered update of Alg. 1).
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "plane.cuh"
+#include "plane_tc.cuh"
 
 namespace {
 
 struct PlaneState {
     int nx = 0, ny = 0;
     int math = BRS_PLANE_SIMT;
-    void* sx = nullptr;    // [nx][nx] DST-I (context dtype)
+    void* sx = nullptr;    // [nx][nx] DST-I (context dtype; tensor path: TF32 hi part)
     void* sy = nullptr;    // [ny][ny]
     void* ilam = nullptr;  // [nx][ny]: 1 / (ax s_p + ay s_q + 2 az) at [p][q]
-    void* t1 = nullptr;    // grid-sized intermediates
+    void* t1 = nullptr;    // grid-sized intermediates (tensor path: hi parts)
     void* t2 = nullptr;
+    // tensor path: TF32 lo parts and the TMA maps of the four products
+    void* sx_lo = nullptr;
+    void* sy_lo = nullptr;
+    void* t1_lo = nullptr;
+    void* t2_lo = nullptr;
+    CUtensorMap m_sx_hi, m_sx_lo, m_sy_hi, m_sy_lo;  // 2D, box (32, 128)
+    CUtensorMap m_R_hi, m_R_lo;    // t2 as [k][y][x]  (B of P1, box rows BN)
+    CUtensorMap m_C1_hi, m_C1_lo;  // t1 as [k][p][y]  (A of P2, box rows 128)
+    CUtensorMap m_Q_hi, m_Q_lo;    // t2 as [k][p][q]  (B of P3, box rows BN)
+    CUtensorMap m_W_hi, m_W_lo;    // t1 as [k][y][p]  (A of P4, box rows 128)
+    CUtensorMap m_sxB_hi, m_sxB_lo, m_syB_hi, m_syB_lo;  // S as B operands, box rows BN
 };
+
+constexpr int kTcBN = 128;
+constexpr int kTcStages = 3;
 
 PlaneState* ps(brs_ctx* c)
 {
@@ -160,6 +176,93 @@ cudaError_t launch_gemm(const T* A, const T* B, T* C, const GemmArgs& g, int bat
     return cudaGetLastError();
 }
 
+// R_k = b_k + az (u_{k-1} + u_{k+1}) split into TF32 hi/lo parts, stored at plane k.
+__global__ void plane_gather_split_kernel(const float* __restrict__ u, const float* __restrict__ b,
+                                          float* __restrict__ rhi, float* __restrict__ rlo,
+                                          int nx, int ny, int nz, float az, int k0, int kstep,
+                                          int nbatch, int split)
+{
+    const long long plane = (long long)nx * ny;
+    const long long total = plane * nbatch;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long bi = t / plane;
+        const long long o = t - bi * plane;
+        const int k = k0 + (int)bi * kstep;
+        const long long gi = (long long)k * plane + o;
+        const float sz = (k > 0 ? u[gi - plane] : 0.f) + (k + 1 < nz ? u[gi + plane] : 0.f);
+        const float r = fmaf(az, sz, b[gi]);
+        const uint32_t hi = brs_tc::tf32_rn(r);
+        rhi[gi] = __uint_as_float(hi);
+        if (split == 3)
+            rlo[gi] = __uint_as_float(brs_tc::tf32_rn(r - __uint_as_float(hi)));
+    }
+}
+
+template <int SPLIT, int EPI>
+cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
+                      const CUtensorMap& bl, const brs_tc::TcArgs& g, int nbatch, cudaStream_t s)
+{
+    const void* k = (const void*)brs_tc::tc_gemm_kernel<SPLIT, EPI, kTcBN, kTcStages>;
+    dim3 grid((g.N + kTcBN - 1) / kTcBN, (g.M + brs_tc::BM - 1) / brs_tc::BM, nbatch);
+    const size_t stage = (size_t)(SPLIT == 3 ? 2 : 1) * (brs_tc::BM + kTcBN) * brs_tc::BK * 4;
+    const size_t smem = 1024 + kTcStages * stage + (2 * kTcStages + 1) * 8 + 16;
+    CUtensorMap a0 = ah, a1 = al, b0 = bh, b1 = bl;
+    brs_tc::TcArgs gg = g;
+    void* args[] = {&a0, &a1, &b0, &b1, &gg};
+    return cudaLaunchKernel(k, grid, dim3(128), args, smem, s);
+}
+
+template <int SPLIT>
+int plane_pass_tc(brs_ctx* c, const float* uin, float* uout, const float* b, int k0, int kstep,
+                  int nbatch, cudaStream_t s)
+{
+    PlaneState* P = ps(c);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const long long plane = (long long)nx * ny;
+    {
+        int blocks = (int)((plane * nbatch + 255) / 256);
+        if (blocks > 152 * 16)
+            blocks = 152 * 16;
+        plane_gather_split_kernel<<<blocks, 256, 0, s>>>(uin, b, (float*)P->t2, (float*)P->t2_lo,
+                                                         nx, ny, nz, (float)c->p.az, k0, kstep,
+                                                         nbatch, SPLIT);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+    }
+    brs_tc::TcArgs g{};
+    g.k0 = k0;
+    g.kstep = kstep;
+    g.plane = plane;
+    g.status = c->dev_status;
+    cudaError_t e;
+    // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]
+    g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
+    g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo;
+    e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P->m_sx_hi, P->m_sx_lo, P->m_R_hi, P->m_R_lo, g, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P2: Q[p][q] = (sum_y C1[p][y] Sy[q][y]) / L[q][p]
+    g.M = nx; g.N = ny; g.K = ny; g.a_batched = 1; g.b_batched = 0;
+    g.out_hi = (float*)P->t2; g.out_lo = (float*)P->t2_lo; g.scale = (const float*)P->ilam;
+    e = launch_tc<SPLIT, brs_tc::EPI_SCALE_SPLIT>(P->m_C1_hi, P->m_C1_lo, P->m_syB_hi, P->m_syB_lo, g,
+                                           nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P3: W[y][p] = sum_q Sy[y][q] Q[p][q]
+    g.M = ny; g.N = nx; g.K = ny; g.a_batched = 0; g.b_batched = 1;
+    g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo; g.scale = nullptr;
+    e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P->m_sy_hi, P->m_sy_lo, P->m_Q_hi, P->m_Q_lo, g, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P4: X[y][x] = sum_p W[y][p] Sx[x][p]; u_k <- (1-omega) u_k + omega X
+    g.M = ny; g.N = nx; g.K = nx; g.a_batched = 1; g.b_batched = 0;
+    g.out_hi = nullptr; g.out_lo = nullptr; g.u = uin; g.uout = uout; g.omega = (float)c->omega;
+    e = launch_tc<SPLIT, brs_tc::EPI_UPDATE>(P->m_W_hi, P->m_W_lo, P->m_sxB_hi, P->m_sxB_lo, g, nbatch, s);
+    return brs_cuda_status(e);
+}
+
 // One plane-block solve + update for planes k0, k0+kstep, ... (nbatch of them), reading
 // neighbours from `uin` and writing the updated planes to `uout`.
 template <typename T>
@@ -239,6 +342,115 @@ int upload(void** dst, const std::vector<double>& src)
     return brs_cuda_status(e);
 }
 
+// Round a value to TF32 (10 explicit mantissa bits), nearest with ties away from zero,
+// the rounding of cvt.rna.tf32.f32.
+float tf32_round(double x)
+{
+    float f = (float)x;
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+int upload_split(void** hi, void** lo, const std::vector<double>& src)
+{
+    std::vector<float> h(src.size()), l(src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+        h[i] = tf32_round(src[i]);
+        l[i] = tf32_round(src[i] - (double)h[i]);
+    }
+    cudaError_t e = cudaMalloc(hi, h.size() * 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*hi, h.data(), h.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(lo, l.size() * 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*lo, l.data(), l.size() * 4, cudaMemcpyHostToDevice);
+    return brs_cuda_status(e);
+}
+
+PFN_encode_tiled g_encode_fn = nullptr;
+
+// FP32 map with the K axis innermost, box (32, rows[, 1]), 128-byte swizzle.
+int encode_map(CUtensorMap* m, const void* ptr, int kdim, int rows, int planes, int box_rows)
+{
+    cuuint64_t gdim[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t gstr[2] = {(cuuint64_t)kdim * 4, (cuuint64_t)kdim * rows * 4};
+    cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
+    cuuint32_t es[3] = {1u, 1u, 1u};
+    const int rank = planes > 0 ? 3 : 2;
+    CUresult r = g_encode_fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(ptr),
+                             gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? BRS_OK : BRS_ERR_CUDA;
+}
+
+int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double>& sy)
+{
+    PlaneState* P = ps(c);
+    g_encode_fn = brs_encoder();
+    if (!g_encode_fn)
+        return BRS_ERR_CUDA;
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    int rc = upload_split(&P->sx, &P->sx_lo, sx);
+    if (rc == BRS_OK)
+        rc = upload_split(&P->sy, &P->sy_lo, sy);
+    const size_t bytes = (size_t)c->cells * 4;
+    for (void** q : {&P->t1, &P->t2, &P->t1_lo, &P->t2_lo})
+        if (rc == BRS_OK)
+            rc = brs_cuda_status(cudaMalloc(q, bytes));
+    if (rc != BRS_OK)
+        return rc;
+    const int BN = kTcBN, BMr = brs_tc::BM;
+    int e = BRS_OK;
+    auto enc = [&](CUtensorMap* m, const void* p, int k, int r, int pl, int br) {
+        if (e == BRS_OK)
+            e = encode_map(m, p, k, r, pl, br);
+    };
+    enc(&P->m_sx_hi, P->sx, nx, nx, 0, BMr);
+    enc(&P->m_sx_lo, P->sx_lo, nx, nx, 0, BMr);
+    enc(&P->m_sy_hi, P->sy, ny, ny, 0, BMr);
+    enc(&P->m_sy_lo, P->sy_lo, ny, ny, 0, BMr);
+    enc(&P->m_sxB_hi, P->sx, nx, nx, 0, BN);
+    enc(&P->m_sxB_lo, P->sx_lo, nx, nx, 0, BN);
+    enc(&P->m_syB_hi, P->sy, ny, ny, 0, BN);
+    enc(&P->m_syB_lo, P->sy_lo, ny, ny, 0, BN);
+    enc(&P->m_R_hi, P->t2, nx, ny, nz, BN);
+    enc(&P->m_R_lo, P->t2_lo, nx, ny, nz, BN);
+    enc(&P->m_C1_hi, P->t1, ny, nx, nz, BMr);
+    enc(&P->m_C1_lo, P->t1_lo, ny, nx, nz, BMr);
+    enc(&P->m_Q_hi, P->t2, ny, nx, nz, BN);
+    enc(&P->m_Q_lo, P->t2_lo, ny, nx, nz, BN);
+    enc(&P->m_W_hi, P->t1, nx, ny, nz, BMr);
+    enc(&P->m_W_lo, P->t1_lo, nx, ny, nz, BMr);
+    if (e != BRS_OK)
+        return e;
+    // raise the kernels' dynamic shared-memory limit (never lower it)
+    const void* kern[] = {
+        (const void*)brs_tc::tc_gemm_kernel<3, brs_tc::EPI_SPLIT, kTcBN, kTcStages>,
+        (const void*)brs_tc::tc_gemm_kernel<3, brs_tc::EPI_SCALE_SPLIT, kTcBN, kTcStages>,
+        (const void*)brs_tc::tc_gemm_kernel<3, brs_tc::EPI_UPDATE, kTcBN, kTcStages>,
+        (const void*)brs_tc::tc_gemm_kernel<1, brs_tc::EPI_SPLIT, kTcBN, kTcStages>,
+        (const void*)brs_tc::tc_gemm_kernel<1, brs_tc::EPI_SCALE_SPLIT, kTcBN, kTcStages>,
+        (const void*)brs_tc::tc_gemm_kernel<1, brs_tc::EPI_UPDATE, kTcBN, kTcStages>};
+    const int smem[] = {3, 3, 3, 1, 1, 1};
+    for (int i = 0; i < 6; ++i) {
+        const size_t st = (size_t)(smem[i] == 3 ? 2 : 1) * (brs_tc::BM + kTcBN) * brs_tc::BK * 4;
+        const size_t need = 1024 + kTcStages * st + (2 * kTcStages + 1) * 8 + 16;
+        cudaFuncAttributes fa{};
+        cudaError_t ce = cudaFuncGetAttributes(&fa, kern[i]);
+        if (ce == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < need)
+            ce = cudaFuncSetAttribute(kern[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)need);
+        if (ce != cudaSuccess)
+            return brs_cuda_status(ce);
+    }
+    return BRS_OK;
+}
+
 }  // namespace
 
 int plane_setup(brs_ctx* c)
@@ -249,9 +461,11 @@ int plane_setup(brs_ctx* c)
     int math = p.plane_math;
     if (p.dtype == BRS_F64 && (math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32))
         return BRS_ERR_UNSUPPORTED;
+    // tensor-core path: FP32, both plane sides whole 32-element K blocks
+    const bool tc_shape = p.dtype == BRS_F32 && p.nx % 32 == 0 && p.ny % 32 == 0;
     if (math == BRS_PLANE_AUTO)
-        math = BRS_PLANE_SIMT;
-    if (math != BRS_PLANE_SIMT)
+        math = tc_shape ? BRS_PLANE_3XTF32 : BRS_PLANE_SIMT;
+    if ((math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32) && !tc_shape)
         return BRS_ERR_UNSUPPORTED;
     PlaneState* P = new PlaneState();
     c->plane = P;
@@ -266,6 +480,16 @@ int plane_setup(brs_ctx* c)
             il[(size_t)pp * p.ny + q] = 1.0 / (p.ax * spx + p.ay * sqy + 2.0 * p.az);
         }
     int rc;
+    if (math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32) {
+        std::vector<float> ilf(il.begin(), il.end());
+        rc = brs_cuda_status(cudaMalloc(&P->ilam, ilf.size() * 4));
+        if (rc == BRS_OK)
+            rc = brs_cuda_status(
+                cudaMemcpy(P->ilam, ilf.data(), ilf.size() * 4, cudaMemcpyHostToDevice));
+        if (rc == BRS_OK)
+            rc = tc_setup(c, sx, sy);
+        return rc;
+    }
     if (p.dtype == BRS_F64)
         rc = upload<double>(&P->sx, sx);
     else
@@ -287,7 +511,7 @@ void plane_teardown(brs_ctx* c)
     PlaneState* P = ps(c);
     if (!P)
         return;
-    for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2})
+    for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo})
         if (q)
             cudaFree(q);
     delete P;
@@ -313,5 +537,21 @@ int plane_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, c
     };
     if (c->p.dtype == BRS_F64)
         return run(double{});
+    const int math = ps(c)->math;
+    if (math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32) {
+        const float* ui = static_cast<const float*>(uin);
+        float* uo = static_cast<float*>(uout);
+        const float* bb = static_cast<const float*>(b);
+        auto pass = [&](int k0, int kstep, int nb) {
+            return math == BRS_PLANE_3XTF32 ? plane_pass_tc<3>(c, ui, uo, bb, k0, kstep, nb, s)
+                                            : plane_pass_tc<1>(c, ui, uo, bb, k0, kstep, nb, s);
+        };
+        if (!gs)
+            return pass(0, 1, nz);
+        int rc = pass(0, 2, (nz + 1) / 2);
+        if (rc == BRS_OK && nz > 1)
+            rc = pass(1, 2, nz / 2);
+        return rc;
+    }
     return run(float{});
 }

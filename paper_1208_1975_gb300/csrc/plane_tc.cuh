@@ -1,0 +1,299 @@
+// Tensor-core (tcgen05, TF32 / split-TF32) batched products for the xy-plane solve.
+//
+// The plane solve X = Sy [ (Sy R Sx) ./ L ] Sx runs as four batched "TN" products
+// C = A B^T (both operands K-major, one plane per batch index), see plane.cu.  Here each
+// product is one kernel:
+//   * 128 x BN output tile per CTA, K consumed in blocks of 32 FP32 values (one 128-byte
+//     swizzle atom), staged by TMA (SWIZZLE_128B) through an NST-stage shared-memory ring;
+//   * one thread issues tcgen05.mma.kind::tf32 (M=128, N=BN, K=8 per instruction) with
+//     the FP32 accumulator in tensor memory; tcgen05.commit releases ring slots;
+//   * 128 threads read the accumulator back with tcgen05.ld (one TMEM lane = one output
+//     row per thread) and apply the epilogue.
+// Split-TF32 ("3xTF32", the published technique of representing x = hi + lo with both
+// parts TF32 and dropping lo*lo): operands are stored as separate hi and lo arrays,
+// hi = rn_tf32(x), lo = rn_tf32(x - hi); every K-step accumulates hi*hi + hi*lo + lo*hi.
+// With SPLIT = 1 only the hi parts are used (single TF32 pass).
+#pragma once
+
+#include "brs_internal.cuh"
+
+namespace brs_tc {
+
+constexpr int BM = 128;  // MMA M (one TMEM lane per output row)
+constexpr int BK = 32;   // K per ring stage: 32 FP32 = one 128-byte swizzle row
+
+enum Epi { EPI_SPLIT = 0, EPI_SCALE_SPLIT = 1, EPI_UPDATE = 2 };
+
+struct TcArgs {
+    int M, N, K;        // per-plane product sizes
+    int a_batched;      // A is per plane (3D map) or shared (2D map)
+    int b_batched;
+    int k0, kstep;      // blockIdx.z -> plane k0 + blockIdx.z * kstep
+    long long plane;    // elements per plane of the outputs (M * N)
+    float* out_hi;      // EPI_SPLIT / EPI_SCALE_SPLIT outputs, [plane][M][N]
+    float* out_lo;
+    const float* scale; // EPI_SCALE_SPLIT: [M][N]
+    const float* u;     // EPI_UPDATE: old plane values [plane][M][N]
+    float* uout;        // EPI_UPDATE: updated planes
+    float omega;
+    int* status;
+};
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t tf32_rn(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with SWIZZLE_128B:
+// rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* tile)
+{
+    const uint64_t addr = smem_u32(tile);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFFull) >> 4;          // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                  // fixed constant 0b001
+    d |= (uint64_t)2 << 61;                  // swizzle: 128-byte
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int SPLIT, int EPI, int BN, int NST>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(
+    const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+    const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+    TcArgs g)
+{
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "MMA N for M = 128");
+    constexpr uint32_t A_BYTES = BM * BK * 4;   // 16 KB
+    constexpr uint32_t B_BYTES = BN * BK * 4;
+    constexpr uint32_t STAGE = (SPLIT == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
+    constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // align the ring to 1024 bytes (swizzle atom)
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE);
+    uint64_t* empty = full + NST;
+    uint64_t* done = empty + NST;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int plane = g.k0 + (int)blockIdx.z * g.kstep;
+    const int nkb = (g.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_d = *tmem_slot;
+
+    int issued = 0;  // producer: stages issued (thread 0 only)
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads of A and B K-blocks
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % NST;
+            if (kb >= NST) {
+                if (!mbar_wait_bounded(&empty[s], ((kb / NST) - 1) & 1)) {
+                    *abort_flag = 1;
+                    break;
+                }
+            }
+            unsigned char* st = base + s * STAGE;
+            mbar_arrive_expect_tx(&full[s], STAGE);
+            const int kx = kb * BK;
+            if (g.a_batched)
+                tma_load_3d(st, &mA_hi, &full[s], kx, m0, plane);
+            else
+                tma_load_2d(st, &mA_hi, &full[s], kx, m0);
+            if (SPLIT == 3) {
+                if (g.a_batched)
+                    tma_load_3d(st + A_BYTES, &mA_lo, &full[s], kx, m0, plane);
+                else
+                    tma_load_2d(st + A_BYTES, &mA_lo, &full[s], kx, m0);
+            }
+            unsigned char* sb = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
+            if (g.b_batched)
+                tma_load_3d(sb, &mB_hi, &full[s], kx, n0, plane);
+            else
+                tma_load_2d(sb, &mB_hi, &full[s], kx, n0);
+            if (SPLIT == 3) {
+                if (g.b_batched)
+                    tma_load_3d(sb + B_BYTES, &mB_lo, &full[s], kx, n0, plane);
+                else
+                    tma_load_2d(sb + B_BYTES, &mB_lo, &full[s], kx, n0);
+            }
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_tf32(BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % NST;
+            if (*abort_flag || !mbar_wait_bounded(&full[s], (kb / NST) & 1)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            unsigned char* st = base + s * STAGE;
+            unsigned char* sa_hi = st;
+            unsigned char* sa_lo = st + A_BYTES;
+            unsigned char* sb_hi = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
+            unsigned char* sb_lo = sb_hi + B_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 8; ++k) {
+                // K = 8 TF32 per instruction = 32 bytes along the swizzled row
+                const uint64_t ah = smem_desc_sw128(sa_hi) + (uint64_t)((k * 32) >> 4);
+                const uint64_t bh = smem_desc_sw128(sb_hi) + (uint64_t)((k * 32) >> 4);
+                mma_tf32(tmem_d, ah, bh, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                if (SPLIT == 3) {
+                    const uint64_t al = smem_desc_sw128(sa_lo) + (uint64_t)((k * 32) >> 4);
+                    const uint64_t bl = smem_desc_sw128(sb_lo) + (uint64_t)((k * 32) >> 4);
+                    mma_tf32(tmem_d, ah, bl, idesc, 1u);
+                    mma_tf32(tmem_d, al, bh, idesc, 1u);
+                }
+            }
+            mma_commit(&empty[s]);  // slot free once these MMAs have read it
+        }
+        mma_commit(done);  // accumulator complete (covers every MMA issued above)
+    }
+    __syncwarp();
+
+    // epilogue: thread t owns output row m0 + t (TMEM lane t)
+    const bool ok = mbar_wait_bounded(done, 0);
+    tc_fence_after();
+    const bool good = __syncthreads_and(ok && !*abort_flag) != 0;
+    if (good) {
+        const int m = m0 + threadIdx.x;
+        const uint32_t trow = tmem_d + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t r[32];
+            tmem_ld32(trow + (uint32_t)(c * 32), r);
+            const int nb = n0 + c * 32;
+            if (m < g.M) {
+                const long long row = (long long)plane * g.plane + (long long)m * g.N;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int n = nb + q;
+                    if (n < g.N) {
+                        float v = __uint_as_float(r[q]);
+                        if (EPI == EPI_SCALE_SPLIT)
+                            v *= g.scale[(long long)m * g.N + n];
+                        if (EPI == EPI_UPDATE) {
+                            g.uout[row + n] = fmaf(g.omega, v, (1.0f - g.omega) * g.u[row + n]);
+                        } else {
+                            const uint32_t hi = tf32_rn(v);
+                            g.out_hi[row + n] = __uint_as_float(hi);
+                            if (SPLIT == 3)
+                                g.out_lo[row + n] = __uint_as_float(tf32_rn(v - __uint_as_float(hi)));
+                        }
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        set_status(g.status, BRS_ERR_TIMEOUT);
+    }
+    if (!good && warp == 0 && lane == 0) {
+        // drain TMA copies still in flight into this CTA's shared memory
+        for (int kb = (issued > NST ? issued - NST : 0); kb < issued; ++kb)
+            mbar_wait_bounded(&full[kb % NST], (kb / NST) & 1, 200000000ull);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace brs_tc

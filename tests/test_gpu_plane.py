@@ -143,3 +143,67 @@ def test_full_size_256_sampled_planes(brs, orc, dt):
         k0, k1 = max(0, k - 1), min(n, k + 2)
         sub = orc.sweep(u[k0:k1], b[k0:k1], a, block="plane", method="jacobi", omega=0.8)
         assert rel_max_err(got[k], sub[k - k0]) <= TOL[dt]
+
+
+# ----------------------------------------------------------------- tensor-core plane solve
+
+TC_SHAPES = [(32, 32, 4), (64, 96, 3), (96, 64, 5), (256, 256, 3), (160, 128, 2)]
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
+def test_plane_3xtf32_one_sweep_parity(brs, orc, shape, a):
+    """Split-TF32 tcgen05 products hold the FP32 per-sweep tolerance."""
+    nx, ny, nz = shape
+    u = rounded(initial_guess((nz, ny, nx)), "f32")
+    b = rounded(rhs((nz, ny, nx)), "f32")
+    ref = orc.sweep(u, b, a, block="plane", method="jacobi", omega=0.8)
+    got = gpu_run(brs, u, b, a, dt="f32", math="3xtf32")
+    assert rel_max_err(got, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 4), (160, 128, 2)], ids=str)
+def test_plane_single_tf32_error_is_tf32_level(brs, orc, shape):
+    """One TF32 pass per product: per-sweep error at the TF32 unit roundoff 2^-11 ~ 4.9e-4
+    (not held to the FP32 bar; used inside defect correction, where FP64 decides)."""
+    nx, ny, nz = shape
+    a = (1.0, 1.0, 0.01)
+    u = rounded(initial_guess((nz, ny, nx)), "f32")
+    b = rounded(rhs((nz, ny, nx)), "f32")
+    ref = orc.sweep(u, b, a, block="plane", method="jacobi", omega=0.8)
+    err = rel_max_err(gpu_run(brs, u, b, a, dt="f32", math="tf32"), ref)
+    assert err <= 2.0 ** -11
+
+
+def test_plane_3xtf32_gs_perron_and_defect_correction(brs, orc):
+    nx, ny, nz = 64, 32, 12
+    a = (1.0, 1.0, 1.0)
+    m = sine_mode(nx, ny, nz, 1, 1, 1)
+    g = orc.mode_factor(nx, ny, nz, a, "plane", 1.0)[0, 0, 0]
+    with brs.Context(nx, ny, nz, a, block="plane", method="gs", dtype="f32", plane_math="3xtf32") as c:
+        ut, bt = to_dev(m, "f32"), to_dev(np.zeros_like(m), "f32")
+        mr = to_np(ut)
+        for k in range(1, 6):
+            c.sweep(ut, bt, 1)
+            u = to_np(ut)
+            assert np.all(u >= -1e-6 * k) and np.all(u <= g ** k * mr + 2e-6 * (1 + k))
+    # single-pass TF32 inner sweeps still reach an FP64 residual of 1e-10 under defect correction
+    n = 64
+    a = (1.0, 0.1, 0.01)
+    b = rhs((n, n, n))
+    with brs.Context(n, n, n, a, block="plane", dtype="f64") as o64, \
+            brs.Context(n, n, n, a, block="plane", dtype="f32", plane_math="tf32") as i32:
+        ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
+        done, rel, _ = brs.defect_correction(o64, i32, ut, bt, rtol=1e-10, inner_sweeps=16,
+                                             max_outer=500)
+        u = to_np(ut)
+    assert rel <= 1e-10
+    assert orc.residual_norm(u, b, a) <= 1.05e-10 * np.linalg.norm(b)
+
+
+def test_plane_tensor_core_unsupported_shapes(brs):
+    for (nx, ny, dt, math) in [(33, 32, "f32", "3xtf32"), (32, 48, "f32", "tf32"), (32, 32, "f64", "tf32")]:
+        p = brs.brs_params(nx, ny, 4, 1.0, 1.0, 1.0, brs.BRS_XYPLANE, brs.BRS_JACOBI,
+                           brs.DTYPES[dt], 0.0, brs.PLANE_MATH[math])
+        rc, h = brs.brsmooth_create(p)
+        assert rc == brs.BRS_ERR_UNSUPPORTED and not h.value
