@@ -48,6 +48,13 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return float(json.loads(p.read_text())["bf16_tflops"])
+    return 1900.0
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,6 +221,7 @@ def _rate(cells, sweeps, ms):
 
 
 def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, math="auto"):
+    """One 256^3 workload variant: steps x sweeps sweeps timed with CUDA events."""
     uv0, bv = _inputs(dt)
     uv, bv = uv0.cuda(), bv.cuda()
     with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt, plane_math=math) as vc:
@@ -226,6 +234,14 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
         flops = 8.0 * N * N ** 3  # four n x n contractions per plane: 4 (nx + ny) per cell
         out["plane_math"] = math
         out["tflops"] = flops * sweeps * steps / (vms / 1e3) / 1e12
+        if math in ("tf32", "3xtf32"):
+            # tensor work: one TF32 product per contraction, three for split-TF32; the TF32
+            # dense peak is taken as half the measured BF16 GEMM rate (nominal 1:2 ratio)
+            passes = 3 if math == "3xtf32" else 1
+            tf32_peak = _bf16_peak() / 2
+            out["tensor_tflops"] = out["tflops"] * passes
+            out["tensor_frac_of_tf32_peak"] = out["tensor_tflops"] / tf32_peak
+            out["tf32_peak_tflops"] = tf32_peak
     if blk == "line" and dt == "f64":
         # ALU roof: 8 FP64 operations per cell for the sequential gather/Thomas/update
         out["alu_frac_of_fp64_fma_peak"] = rate * 8 / 626.9
@@ -380,24 +396,41 @@ def _variant_adjoint(brs, stream):
     return {"workload": "adjoint", "results": res}
 
 
+VARIANTS = {
+    # name: (block, method, dtype, coeffs, steps, sweeps per step, plane math)
+    "line_gs_f32": ("line", "gs", "f32", COEFFS, 6, 50, "auto"),
+    "line_jacobi_f32_aniso": ("line", "jacobi", "f32", (1.0, 1.0, 0.01), 6, 50, "auto"),
+    "line_jacobi_f64": ("line", "jacobi", "f64", COEFFS, 4, 50, "auto"),
+    "line_gs_f64": ("line", "gs", "f64", COEFFS, 4, 50, "auto"),
+    "plane_jacobi_f32_3xtf32": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 4, 10, "3xtf32"),
+    "plane_gs_f32_3xtf32": ("plane", "gs", "f32", (1.0, 1.0, 0.01), 4, 10, "3xtf32"),
+    "plane_jacobi_f32_tf32": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 4, 10, "tf32"),
+    "plane_jacobi_f32_simt": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 2, 10, "simt"),
+    "plane_jacobi_f64": ("plane", "jacobi", "f64", (1.0, 1.0, 0.01), 1, 4, "auto"),
+}
+SPECIAL = ("batched600", "defect512", "adjoint")
+
+
+def _run_variant(name, brs, stream, barrier, peak, steps=None):
+    if name == "batched600":
+        return _variant_batched(brs, stream, barrier)
+    if name == "defect512":
+        return _variant_defect(brs, stream)
+    if name == "adjoint":
+        return _variant_adjoint(brs, stream)
+    blk, meth, dt, a, st, sw, math = VARIANTS[name]
+    out = _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps or st, sw, math)
+    out["name"] = name
+    return out
+
+
 def _variants(brs, stream, barrier, peak):
     out = []
-    specs = [("line", "gs", "f32", COEFFS, 6, 50), ("line", "jacobi", "f32", (1.0, 1.0, 0.01), 6, 50),
-             ("line", "jacobi", "f64", COEFFS, 4, 50), ("line", "gs", "f64", COEFFS, 4, 50),
-             ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 3, 10),
-             ("plane", "gs", "f32", (1.0, 1.0, 0.01), 3, 10),
-             ("plane", "jacobi", "f64", (1.0, 1.0, 0.01), 1, 4)]
-    for blk, meth, dt, a, steps, sweeps in specs:
+    for name in list(VARIANTS) + list(SPECIAL):
         try:
-            out.append(_variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps))
+            out.append(_run_variant(name, brs, stream, barrier, peak))
         except Exception as exc:  # report, do not hide
-            out.append({"block": blk, "method": meth, "dtype": dt, "error": str(exc)})
-    for fn in (lambda: _variant_batched(brs, stream, barrier), lambda: _variant_defect(brs, stream),
-               lambda: _variant_adjoint(brs, stream)):
-        try:
-            out.append(fn())
-        except Exception as exc:
-            out.append({"error": repr(exc)})
+            out.append({"name": name, "error": repr(exc)})
     return out
 
 
@@ -409,10 +442,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="run one named workload variant and print its JSON (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+
+        import paper_1208_1975_gb300 as brs
+
+        brs.build()
+        res = _run_variant(args.only, brs, torch.cuda.current_stream(), None, _peaks()[0],
+                           steps=args.steps)
+        print(json.dumps(res), flush=True)
+        return 0
 
     import torch
 
