@@ -248,33 +248,61 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(
     tc_fence_after();
     const bool good = __syncthreads_and(ok && !*abort_flag) != 0;
     if (good) {
-        const int m = m0 + threadIdx.x;
+        // TMEM lane = output row: thread t holds row m0 + t.  Each warp stages its 32 x 32
+        // chunk through the (now idle) ring memory so that a warp store covers 32
+        // consecutive columns of one row.
+        float* tile = reinterpret_cast<float*>(base) + warp * (32 * 33);
         const uint32_t trow = tmem_d + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t r[32];
             tmem_ld32(trow + (uint32_t)(c * 32), r);
-            const int nb = n0 + c * 32;
-            if (m < g.M) {
-                const long long row = (long long)plane * g.plane + (long long)m * g.N;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int n = nb + q;
-                    if (n < g.N) {
-                        float v = __uint_as_float(r[q]);
-                        if (EPI == EPI_SCALE_SPLIT)
-                            v *= g.scale[(long long)m * g.N + n];
-                        if (EPI == EPI_UPDATE) {
-                            g.uout[row + n] = fmaf(g.omega, v, (1.0f - g.omega) * g.u[row + n]);
-                        } else {
-                            const uint32_t hi = tf32_rn(v);
-                            g.out_hi[row + n] = __uint_as_float(hi);
-                            if (SPLIT == 3)
-                                g.out_lo[row + n] = __uint_as_float(tf32_rn(v - __uint_as_float(hi)));
-                        }
-                    }
-                }
+            for (int q = 0; q < 32; ++q)
+                tile[lane * 33 + q] = __uint_as_float(r[q]);
+            __syncwarp();
+            const int n = n0 + c * 32 + lane;
+            const bool nok = n < g.N;
+            const int mrow = m0 + warp * 32;
+            const long long obase = (long long)plane * g.plane + (long long)mrow * g.N + n;
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                v[i] = tile[i * 33 + lane];
+            // issue every row's load before using any, so their latencies overlap
+            if (EPI == EPI_SCALE_SPLIT) {
+                float sc[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    sc[i] = (nok && mrow + i < g.M)
+                                ? __ldg(g.scale + (long long)(mrow + i) * g.N + n)
+                                : 0.0f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    v[i] *= sc[i];
             }
+            if (EPI == EPI_UPDATE) {
+                float uo[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    uo[i] = (nok && mrow + i < g.M) ? g.u[obase + (long long)i * g.N] : 0.0f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (nok && mrow + i < g.M)
+                        g.uout[obase + (long long)i * g.N] =
+                            fmaf(g.omega, v[i], (1.0f - g.omega) * uo[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (nok && mrow + i < g.M) {
+                        const uint32_t hi = tf32_rn(v[i]);
+                        g.out_hi[obase + (long long)i * g.N] = __uint_as_float(hi);
+                        if (SPLIT == 3)
+                            g.out_lo[obase + (long long)i * g.N] =
+                                __uint_as_float(tf32_rn(v[i] - __uint_as_float(hi)));
+                    }
+            }
+            __syncwarp();
         }
     } else if (threadIdx.x == 0) {
         set_status(g.status, BRS_ERR_TIMEOUT);
