@@ -22,6 +22,7 @@
 // updates in place, even planes first and odd planes second, so odd planes read their
 // neighbours' new values (one admissible outcome of the unordered update of Alg. 1).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -49,10 +50,21 @@ struct PlaneState {
     CUtensorMap m_Q_hi, m_Q_lo;    // t2 as [k][p][q]  (B of P3, box rows BN)
     CUtensorMap m_W_hi, m_W_lo;    // t1 as [k][y][p]  (A of P4, box rows 128)
     CUtensorMap m_sxB_hi, m_sxB_lo, m_syB_hi, m_syB_lo;  // S as B operands, box rows BN
+    int tc_bn = 128, tc_nst = 3;
 };
 
-constexpr int kTcBN = 128;
-constexpr int kTcStages = 3;
+// Tile shapes of the tensor-core products (N per CTA, ring stages): 128 x 128 tiles with a
+// deep ring at one CTA per SM, or 128 x 64 tiles at two CTAs per SM (one CTA's epilogue
+// overlaps the other's main loop).
+struct TcShape {
+    int bn, nst;
+};
+
+size_t tc_smem(int split, int bn, int nst)
+{
+    const size_t stage = (size_t)(split == 3 ? 2 : 1) * (brs_tc::BM + bn) * brs_tc::BK * 4;
+    return 1024 + nst * stage + (2 * nst + 1) * 8 + 16;
+}
 
 PlaneState* ps(brs_ctx* c)
 {
@@ -199,18 +211,32 @@ __global__ void plane_gather_split_kernel(const float* __restrict__ u, const flo
     }
 }
 
-template <int SPLIT, int EPI>
-cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
-                      const CUtensorMap& bl, const brs_tc::TcArgs& g, int nbatch, cudaStream_t s)
+template <int SPLIT, int EPI, int BNT, int NST>
+const void* tc_kernel()
 {
-    const void* k = (const void*)brs_tc::tc_gemm_kernel<SPLIT, EPI, kTcBN, kTcStages>;
-    dim3 grid((g.N + kTcBN - 1) / kTcBN, (g.M + brs_tc::BM - 1) / brs_tc::BM, nbatch);
-    const size_t stage = (size_t)(SPLIT == 3 ? 2 : 1) * (brs_tc::BM + kTcBN) * brs_tc::BK * 4;
-    const size_t smem = 1024 + kTcStages * stage + (2 * kTcStages + 1) * 8 + 16;
+    return (const void*)brs_tc::tc_gemm_kernel<SPLIT, EPI, BNT, NST>;
+}
+
+template <int SPLIT, int EPI>
+const void* tc_kernel_for(int bn, int nst)
+{
+    if (bn == 64)
+        return SPLIT == 3 ? tc_kernel<SPLIT, EPI, 64, 2>() : tc_kernel<SPLIT, EPI, 64, 4>();
+    return tc_kernel<SPLIT, EPI, 128, 3>();
+}
+
+template <int SPLIT, int EPI>
+cudaError_t launch_tc(const PlaneState* P, const CUtensorMap& ah, const CUtensorMap& al,
+                      const CUtensorMap& bh, const CUtensorMap& bl, const brs_tc::TcArgs& g,
+                      int nbatch, cudaStream_t s)
+{
+    const int bn = P->tc_bn, nst = P->tc_nst;
+    const void* k = tc_kernel_for<SPLIT, EPI>(bn, nst);
+    dim3 grid((g.N + bn - 1) / bn, (g.M + brs_tc::BM - 1) / brs_tc::BM, nbatch);
     CUtensorMap a0 = ah, a1 = al, b0 = bh, b1 = bl;
     brs_tc::TcArgs gg = g;
     void* args[] = {&a0, &a1, &b0, &b1, &gg};
-    return cudaLaunchKernel(k, grid, dim3(128), args, smem, s);
+    return cudaLaunchKernel(k, grid, dim3(128), args, tc_smem(SPLIT, bn, nst), s);
 }
 
 template <int SPLIT>
@@ -240,26 +266,26 @@ int plane_pass_tc(brs_ctx* c, const float* uin, float* uout, const float* b, int
     // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]
     g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
     g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo;
-    e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P->m_sx_hi, P->m_sx_lo, P->m_R_hi, P->m_R_lo, g, nbatch, s);
+    e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P, P->m_sx_hi, P->m_sx_lo, P->m_R_hi, P->m_R_lo, g, nbatch, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
     // P2: Q[p][q] = (sum_y C1[p][y] Sy[q][y]) / L[q][p]
     g.M = nx; g.N = ny; g.K = ny; g.a_batched = 1; g.b_batched = 0;
     g.out_hi = (float*)P->t2; g.out_lo = (float*)P->t2_lo; g.scale = (const float*)P->ilam;
-    e = launch_tc<SPLIT, brs_tc::EPI_SCALE_SPLIT>(P->m_C1_hi, P->m_C1_lo, P->m_syB_hi, P->m_syB_lo, g,
+    e = launch_tc<SPLIT, brs_tc::EPI_SCALE_SPLIT>(P, P->m_C1_hi, P->m_C1_lo, P->m_syB_hi, P->m_syB_lo, g,
                                            nbatch, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
     // P3: W[y][p] = sum_q Sy[y][q] Q[p][q]
     g.M = ny; g.N = nx; g.K = ny; g.a_batched = 0; g.b_batched = 1;
     g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo; g.scale = nullptr;
-    e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P->m_sy_hi, P->m_sy_lo, P->m_Q_hi, P->m_Q_lo, g, nbatch, s);
+    e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P, P->m_sy_hi, P->m_sy_lo, P->m_Q_hi, P->m_Q_lo, g, nbatch, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
     // P4: X[y][x] = sum_p W[y][p] Sx[x][p]; u_k <- (1-omega) u_k + omega X
     g.M = ny; g.N = nx; g.K = nx; g.a_batched = 1; g.b_batched = 0;
     g.out_hi = nullptr; g.out_lo = nullptr; g.u = uin; g.uout = uout; g.omega = (float)c->omega;
-    e = launch_tc<SPLIT, brs_tc::EPI_UPDATE>(P->m_W_hi, P->m_W_lo, P->m_sxB_hi, P->m_sxB_lo, g, nbatch, s);
+    e = launch_tc<SPLIT, brs_tc::EPI_UPDATE>(P, P->m_W_hi, P->m_W_lo, P->m_sxB_hi, P->m_sxB_lo, g, nbatch, s);
     return brs_cuda_status(e);
 }
 
@@ -404,7 +430,14 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
             rc = brs_cuda_status(cudaMalloc(q, bytes));
     if (rc != BRS_OK)
         return rc;
-    const int BN = kTcBN, BMr = brs_tc::BM;
+    const char* env = std::getenv("BRSMOOTH_TC_BN");
+    // measured defaults: split-TF32 128x64 tiles (2 stages, 2 CTAs/SM); single TF32 128x128
+    // tiles (3 stages, 2 CTAs/SM)
+    const int dflt = P->math == BRS_PLANE_3XTF32 ? 64 : 128;
+    const int want = env ? std::atoi(env) : dflt;
+    P->tc_bn = (want == 64 || want == 128) ? want : dflt;
+    P->tc_nst = P->tc_bn == 64 ? (P->math == BRS_PLANE_3XTF32 ? 2 : 4) : 3;
+    const int BN = P->tc_bn, BMr = brs_tc::BM;
     int e = BRS_OK;
     auto enc = [&](CUtensorMap* m, const void* p, int k, int r, int pl, int br) {
         if (e == BRS_OK)
@@ -429,17 +462,19 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
     if (e != BRS_OK)
         return e;
     // raise the kernels' dynamic shared-memory limit (never lower it)
-    const void* kern[] = {
-        (const void*)brs_tc::tc_gemm_kernel<3, brs_tc::EPI_SPLIT, kTcBN, kTcStages>,
-        (const void*)brs_tc::tc_gemm_kernel<3, brs_tc::EPI_SCALE_SPLIT, kTcBN, kTcStages>,
-        (const void*)brs_tc::tc_gemm_kernel<3, brs_tc::EPI_UPDATE, kTcBN, kTcStages>,
-        (const void*)brs_tc::tc_gemm_kernel<1, brs_tc::EPI_SPLIT, kTcBN, kTcStages>,
-        (const void*)brs_tc::tc_gemm_kernel<1, brs_tc::EPI_SCALE_SPLIT, kTcBN, kTcStages>,
-        (const void*)brs_tc::tc_gemm_kernel<1, brs_tc::EPI_UPDATE, kTcBN, kTcStages>};
-    const int smem[] = {3, 3, 3, 1, 1, 1};
-    for (int i = 0; i < 6; ++i) {
-        const size_t st = (size_t)(smem[i] == 3 ? 2 : 1) * (brs_tc::BM + kTcBN) * brs_tc::BK * 4;
-        const size_t need = 1024 + kTcStages * st + (2 * kTcStages + 1) * 8 + 16;
+    const int split = P->math == BRS_PLANE_3XTF32 ? 3 : 1;
+    const void* kern[3];
+    if (split == 3) {
+        kern[0] = tc_kernel_for<3, brs_tc::EPI_SPLIT>(P->tc_bn, P->tc_nst);
+        kern[1] = tc_kernel_for<3, brs_tc::EPI_SCALE_SPLIT>(P->tc_bn, P->tc_nst);
+        kern[2] = tc_kernel_for<3, brs_tc::EPI_UPDATE>(P->tc_bn, P->tc_nst);
+    } else {
+        kern[0] = tc_kernel_for<1, brs_tc::EPI_SPLIT>(P->tc_bn, P->tc_nst);
+        kern[1] = tc_kernel_for<1, brs_tc::EPI_SCALE_SPLIT>(P->tc_bn, P->tc_nst);
+        kern[2] = tc_kernel_for<1, brs_tc::EPI_UPDATE>(P->tc_bn, P->tc_nst);
+    }
+    const size_t need = tc_smem(split, P->tc_bn, P->tc_nst);
+    for (int i = 0; i < 3; ++i) {
         cudaFuncAttributes fa{};
         cudaError_t ce = cudaFuncGetAttributes(&fa, kern[i]);
         if (ce == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < need)

@@ -125,7 +125,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 }
 
 template <int SPLIT, int EPI, int BN, int NST>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(
+__global__ void __launch_bounds__(128, 2) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
     const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
     TcArgs g)

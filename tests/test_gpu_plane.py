@@ -150,10 +150,12 @@ def test_full_size_256_sampled_planes(brs, orc, dt):
 TC_SHAPES = [(32, 32, 4), (64, 96, 3), (96, 64, 5), (256, 256, 3), (160, 128, 2)]
 
 
+@pytest.mark.parametrize("tile_n", ["64", "128"])
 @pytest.mark.parametrize("shape", TC_SHAPES, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
-def test_plane_3xtf32_one_sweep_parity(brs, orc, shape, a):
-    """Split-TF32 tcgen05 products hold the FP32 per-sweep tolerance."""
+def test_plane_3xtf32_one_sweep_parity(brs, orc, shape, a, tile_n, monkeypatch):
+    """Split-TF32 tcgen05 products hold the FP32 per-sweep tolerance (both tile shapes)."""
+    monkeypatch.setenv("BRSMOOTH_TC_BN", tile_n)
     nx, ny, nz = shape
     u = rounded(initial_guess((nz, ny, nx)), "f32")
     b = rounded(rhs((nz, ny, nx)), "f32")
