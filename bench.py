@@ -55,6 +55,27 @@ def _bf16_peak():
     return 1900.0
 
 
+def _live_copy_gbs():
+    """Device-to-device copy bandwidth on this machine right now (read + write bytes, best of 10)."""
+    import torch
+
+    n = 1 << 28  # 1 GiB of float32
+    a = torch.empty(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    b.copy_(a)
+    best = 1e30
+    for _ in range(10):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2 * 4 * n / (best / 1e3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -500,8 +521,10 @@ def main():
     alg_bytes = 3 * 4 * cells
     peak, peak_kind = _peaks()
     achieved = alg_bytes / launch_s / 1e9
+    live = _live_copy_gbs()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": _traffic_record(),
+                "live_copy_gbs": live, "frac_of_live_copy": achieved / live,
                 "kernel": "line_tma_kernel<float,8,32,Jacobi>",
                 "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} hbm_gbs"}
 
