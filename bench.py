@@ -269,7 +269,7 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
     return out
 
 
-def _variant_batched(brs, stream, barrier):
+def _variant_batched(brs, stream, barrier, per_patch=True):
     """600 patches, dims from {16,24,32,48,64}, FP32 chaotic line GS, 20 sweeps."""
     import numpy as np
     import torch
@@ -285,6 +285,10 @@ def _variant_batched(brs, stream, barrier):
         u = u0.clone()
         ms = _time_sweeps(bc, u, b, 5, 2, 20, stream, barrier)
     graph_rate = _rate(cells, 20 * 5, ms)
+    if not per_patch:
+        return {"workload": "batched600", "block": "line", "method": "gs", "dtype": "f32",
+                "patches": 600, "cells": cells, "sweeps": 20, "value": graph_rate, "unit": UNIT,
+                "hbm_frac": graph_rate * 12 / _peaks()[0], "tuned": cfg}
     # per-patch launches of the single-grid path on the same data
     ctxs = [brs.Context(int(nx), int(ny), int(nz), COEFFS, method="gs", dtype="f32")
             for nx, ny, nz in dims]
@@ -430,11 +434,14 @@ VARIANTS = {
     "plane_jacobi_f64": ("plane", "jacobi", "f64", (1.0, 1.0, 0.01), 1, 4, "auto"),
 }
 SPECIAL = ("batched600", "defect512", "adjoint")
+PROFILE_ONLY = ("batched600_graph",)
 
 
 def _run_variant(name, brs, stream, barrier, peak, steps=None):
     if name == "batched600":
         return _variant_batched(brs, stream, barrier)
+    if name == "batched600_graph":
+        return _variant_batched(brs, stream, barrier, per_patch=False)
     if name == "defect512":
         return _variant_defect(brs, stream)
     if name == "adjoint":
