@@ -115,17 +115,30 @@ __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc,
     };
 
     T um[kE], uc[kE], up[kE], r[kE], bv[kE], un[kE], us[kE];
+    // next step's u(k+2), b(k+1) and halo lines (y-block edges), loaded one step ahead
+    T upn[kE], bvn[kE], hnn[kE], hsn[kE];
     ld(ub, j, k0 - 1, um);
     ld(ub, j, k0, uc);
+    ld(ub, j, k0 + 1, upn);
+    ld(bb, j, k0, bvn);
+    ld(ub, g == 0 ? j - 1 : -1, k0, hnn);
+    ld(ub, g == R - 1 ? j + 1 : -1, k0, hsn);
     for (int k = k0; k < k1; ++k) {
-        ld(ub, j, k + 1, up);
-        ld(bb, j, k, bv);
-        // y neighbours: from the adjacent line group in the warp, halo lines from memory
         T hn[kE], hs[kE];
-        if (g == 0)
-            ld(ub, j - 1, k, hn);
-        if (g == R - 1)
-            ld(ub, j + 1, k, hs);
+#pragma unroll
+        for (int q = 0; q < kE; ++q) {
+            up[q] = upn[q];
+            bv[q] = bvn[q];
+            hn[q] = hnn[q];
+            hs[q] = hsn[q];
+        }
+        if (k + 1 < k1) {
+            ld(ub, j, k + 2, upn);
+            ld(bb, j, k + 1, bvn);
+            // y neighbours at the block edges come from memory (row -1 reads as zero)
+            ld(ub, g == 0 ? j - 1 : -1, k + 1, hnn);
+            ld(ub, g == R - 1 ? j + 1 : -1, k + 1, hsn);
+        }
 #pragma unroll
         for (int q = 0; q < kE; ++q) {
             T a = __shfl_up_sync(0xffffffffu, uc[q], G);
