@@ -51,6 +51,7 @@ struct PlaneState {
     CUtensorMap m_W_hi, m_W_lo;    // t1 as [k][y][p]  (A of P4, box rows 128)
     CUtensorMap m_sxB_hi, m_sxB_lo, m_syB_hi, m_syB_lo;  // S as B operands, box rows BN
     int tc_bn = 128, tc_nst = 3;
+    int tc_persistent = 0, tc_pbn = 128, sms = 152;
 };
 
 // Tile shapes of the tensor-core products (N per CTA, ring stages): 128 x 128 tiles with a
@@ -225,11 +226,43 @@ const void* tc_kernel_for(int bn, int nst)
     return tc_kernel<SPLIT, EPI, 128, 3>();
 }
 
+// Persistent products: ring stages per (split, tile N) so that the ring is about 192 KB.
+constexpr int pers_nst(int split, int bn)
+{
+    return split == 3 ? (bn == 128 ? 3 : 4) : (bn == 128 ? 6 : 8);
+}
+
+size_t pers_smem(int split, int bn)
+{
+    const int nst = pers_nst(split, bn);
+    const size_t stage = (size_t)(split == 3 ? 2 : 1) * (brs_tc::BM + bn) * brs_tc::BK * 4;
+    return 1024 + nst * stage + 4 * 32 * 33 * 4 + (2 * nst + 5) * 8 + 16;
+}
+
+template <int SPLIT, int EPI>
+const void* pers_kernel_for(int bn)
+{
+    if (bn == 64)
+        return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 64, pers_nst(SPLIT, 64)>;
+    return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 128, pers_nst(SPLIT, 128)>;
+}
+
 template <int SPLIT, int EPI>
 cudaError_t launch_tc(const PlaneState* P, const CUtensorMap& ah, const CUtensorMap& al,
                       const CUtensorMap& bh, const CUtensorMap& bl, const brs_tc::TcArgs& g,
                       int nbatch, cudaStream_t s)
 {
+    if (P->tc_persistent) {
+        const int bn = P->tc_pbn;
+        int tn = (g.N + bn - 1) / bn, tm = (g.M + brs_tc::BM - 1) / brs_tc::BM, nb = nbatch;
+        const long long ntiles = (long long)tn * tm * nb;
+        const int grid = (int)(ntiles < P->sms ? ntiles : P->sms);
+        CUtensorMap a0 = ah, a1 = al, b0 = bh, b1 = bl;
+        brs_tc::TcArgs gg = g;
+        void* args[] = {&a0, &a1, &b0, &b1, &gg, &tn, &tm, &nb};
+        return cudaLaunchKernel(pers_kernel_for<SPLIT, EPI>(bn), dim3(grid), dim3(192), args,
+                                pers_smem(SPLIT, bn), s);
+    }
     const int bn = P->tc_bn, nst = P->tc_nst;
     const void* k = tc_kernel_for<SPLIT, EPI>(bn, nst);
     dim3 grid((g.N + bn - 1) / bn, (g.M + brs_tc::BM - 1) / brs_tc::BM, nbatch);
@@ -437,6 +470,16 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
     const int want = env ? std::atoi(env) : dflt;
     P->tc_bn = (want == 64 || want == 128) ? want : dflt;
     P->tc_nst = P->tc_bn == 64 ? (P->math == BRS_PLANE_3XTF32 ? 2 : 4) : 3;
+    // persistent warp-specialised products (double-buffered TMEM accumulator)
+    const char* penv = std::getenv("BRSMOOTH_TC_PERSISTENT");
+    // measured: split-TF32 gains from overlapping epilogues with the next tile's MMAs
+    // (37 -> 43 Gcell/s at 256^3); single TF32 is faster with two per-tile CTAs per SM
+    P->tc_persistent = penv ? std::atoi(penv) != 0 : (P->math == BRS_PLANE_3XTF32 ? 1 : 0);
+    const char* pbn = std::getenv("BRSMOOTH_TC_PBN");
+    P->tc_pbn = (pbn && std::atoi(pbn) == 64) ? 64 : 128;
+    cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (P->tc_persistent)
+        P->tc_bn = P->tc_pbn;  // B maps' box rows follow the tile N in use
     const int BN = P->tc_bn, BMr = brs_tc::BM;
     int e = BRS_OK;
     auto enc = [&](CUtensorMap* m, const void* p, int k, int r, int pl, int br) {
@@ -473,7 +516,19 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
         kern[1] = tc_kernel_for<1, brs_tc::EPI_SCALE_SPLIT>(P->tc_bn, P->tc_nst);
         kern[2] = tc_kernel_for<1, brs_tc::EPI_UPDATE>(P->tc_bn, P->tc_nst);
     }
-    const size_t need = tc_smem(split, P->tc_bn, P->tc_nst);
+    size_t need = tc_smem(split, P->tc_bn, P->tc_nst);
+    if (P->tc_persistent) {
+        need = pers_smem(split, P->tc_pbn);
+        if (split == 3) {
+            kern[0] = pers_kernel_for<3, brs_tc::EPI_SPLIT>(P->tc_pbn);
+            kern[1] = pers_kernel_for<3, brs_tc::EPI_SCALE_SPLIT>(P->tc_pbn);
+            kern[2] = pers_kernel_for<3, brs_tc::EPI_UPDATE>(P->tc_pbn);
+        } else {
+            kern[0] = pers_kernel_for<1, brs_tc::EPI_SPLIT>(P->tc_pbn);
+            kern[1] = pers_kernel_for<1, brs_tc::EPI_SCALE_SPLIT>(P->tc_pbn);
+            kern[2] = pers_kernel_for<1, brs_tc::EPI_UPDATE>(P->tc_pbn);
+        }
+    }
     for (int i = 0; i < 3; ++i) {
         cudaFuncAttributes fa{};
         cudaError_t ce = cudaFuncGetAttributes(&fa, kern[i]);

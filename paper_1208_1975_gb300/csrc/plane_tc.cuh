@@ -322,6 +322,255 @@ __global__ void __launch_bounds__(128, 2) tc_gemm_kernel(
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent variant: one CTA per SM walks tiles t = blockIdx.x, +gridDim.x, ... of the
+// (n-tile, m-tile, plane) space.  Warp 0 streams K-blocks of every tile through the TMA
+// ring, warp 1 issues the MMAs into one of two TMEM accumulators, warps 2-5 drain the other
+// accumulator (epilogue of the previous tile) at the same time.
+template <int SPLIT, int EPI, int BN, int NST>
+__global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
+    const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+    const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+    TcArgs g, int tiles_n, int tiles_m, int nbatch)
+{
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "MMA N for M = 128");
+    constexpr uint32_t A_BYTES = BM * BK * 4;
+    constexpr uint32_t B_BYTES = BN * BK * 4;
+    constexpr uint32_t STAGE = (SPLIT == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
+    constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulators
+    constexpr uint32_t STAGING = 4 * 32 * 33 * 4;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* staging = reinterpret_cast<float*>(base + NST * STAGE);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE + STAGING);
+    uint64_t* empty = full + NST;
+    uint64_t* accf = empty + NST;  // accumulator a holds a finished tile
+    uint64_t* acce = accf + 2;     // accumulator a has been read out
+    uint64_t* done = acce + 2;     // every MMA issued by this CTA has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = (g.K + BK - 1) / BK;
+    const long long ntiles = (long long)tiles_n * tiles_m * nbatch;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], 4);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto decode = [&](long long t, int* m0, int* n0, int* plane) {
+        const int tn = (int)(t % tiles_n);
+        const long long r = t / tiles_n;
+        const int tm = (int)(r % tiles_m);
+        const int b = (int)(r / tiles_m);
+        *n0 = tn * BN;
+        *m0 = tm * BM;
+        *plane = g.k0 + b * g.kstep;
+    };
+
+    long long issued = 0;  // producer: K-blocks issued (thread 0)
+    if (warp == 0 && lane == 0) {
+        long long kg = 0;
+        for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+            int m0, n0, plane;
+            decode(t, &m0, &n0, &plane);
+            for (int kb = 0; kb < nkb; ++kb, ++kg) {
+                const int s = (int)(kg % NST);
+                if (kg >= NST && !mbar_wait_bounded(&empty[s], (uint32_t)(((kg / NST) - 1) & 1))) {
+                    *abort_flag = 1;
+                    break;
+                }
+                unsigned char* st = base + s * STAGE;
+                mbar_arrive_expect_tx(&full[s], STAGE);
+                const int kx = kb * BK;
+                if (g.a_batched)
+                    tma_load_3d(st, &mA_hi, &full[s], kx, m0, plane);
+                else
+                    tma_load_2d(st, &mA_hi, &full[s], kx, m0);
+                if (SPLIT == 3) {
+                    if (g.a_batched)
+                        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], kx, m0, plane);
+                    else
+                        tma_load_2d(st + A_BYTES, &mA_lo, &full[s], kx, m0);
+                }
+                unsigned char* sb = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
+                if (g.b_batched)
+                    tma_load_3d(sb, &mB_hi, &full[s], kx, n0, plane);
+                else
+                    tma_load_2d(sb, &mB_hi, &full[s], kx, n0);
+                if (SPLIT == 3) {
+                    if (g.b_batched)
+                        tma_load_3d(sb + B_BYTES, &mB_lo, &full[s], kx, n0, plane);
+                    else
+                        tma_load_2d(sb + B_BYTES, &mB_lo, &full[s], kx, n0);
+                }
+                issued = kg + 1;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_tf32(BN);
+        long long kg = 0;
+        int ti = 0;
+        for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++ti) {
+            const int a = ti & 1;
+            if (ti >= 2 && !mbar_wait_bounded(&acce[a], (uint32_t)(((ti >> 1) - 1) & 1))) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tacc = tmem_base + (uint32_t)(a * BN);
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb, ++kg) {
+                const int s = (int)(kg % NST);
+                if (*abort_flag || !mbar_wait_bounded(&full[s], (uint32_t)((kg / NST) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                unsigned char* st = base + s * STAGE;
+                unsigned char* sa_hi = st;
+                unsigned char* sa_lo = st + A_BYTES;
+                unsigned char* sb_hi = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
+                unsigned char* sb_lo = sb_hi + B_BYTES;
+#pragma unroll
+                for (int k = 0; k < BK / 8; ++k) {
+                    const uint64_t ah = smem_desc_sw128(sa_hi) + (uint64_t)((k * 32) >> 4);
+                    const uint64_t bh = smem_desc_sw128(sb_hi) + (uint64_t)((k * 32) >> 4);
+                    mma_tf32(tacc, ah, bh, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    if (SPLIT == 3) {
+                        const uint64_t al = smem_desc_sw128(sa_lo) + (uint64_t)((k * 32) >> 4);
+                        const uint64_t bl = smem_desc_sw128(sb_lo) + (uint64_t)((k * 32) >> 4);
+                        mma_tf32(tacc, ah, bl, idesc, 1u);
+                        mma_tf32(tacc, al, bh, idesc, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                break;
+            }
+            mma_commit(&accf[a]);
+        }
+        mma_commit(done);
+    } else if (warp >= 2) {
+        // epilogue: this warp reads TMEM lanes 32*(warp % 4) .. +31 = tile rows
+        const int q = warp & 3;
+        float* tile = staging + (warp - 2) * (32 * 33);
+        int ti = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
+            const int a = ti & 1;
+            const bool ok = mbar_wait_bounded(&accf[a], (uint32_t)((ti >> 1) & 1));
+            if (__any_sync(0xffffffffu, !ok || *abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            int m0, n0, plane;
+            decode(t, &m0, &n0, &plane);
+            const uint32_t trow = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(trow + (uint32_t)(c * 32), r);
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    tile[lane * 33 + i] = __uint_as_float(r[i]);
+                __syncwarp();
+                const int n = n0 + c * 32 + lane;
+                const bool nok = n < g.N;
+                const int mrow = m0 + q * 32;
+                const long long obase = (long long)plane * g.plane + (long long)mrow * g.N + n;
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    v[i] = tile[i * 33 + lane];
+                if (EPI == EPI_SCALE_SPLIT) {
+                    float sc[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        sc[i] = (nok && mrow + i < g.M)
+                                    ? __ldg(g.scale + (long long)(mrow + i) * g.N + n)
+                                    : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        v[i] *= sc[i];
+                }
+                if (EPI == EPI_UPDATE) {
+                    float uo[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        uo[i] = (nok && mrow + i < g.M) ? g.u[obase + (long long)i * g.N] : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nok && mrow + i < g.M)
+                            g.uout[obase + (long long)i * g.N] =
+                                fmaf(g.omega, v[i], (1.0f - g.omega) * uo[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nok && mrow + i < g.M) {
+                            const uint32_t hi = tf32_rn(v[i]);
+                            g.out_hi[obase + (long long)i * g.N] = __uint_as_float(hi);
+                            if (SPLIT == 3)
+                                g.out_lo[obase + (long long)i * g.N] =
+                                    __uint_as_float(tf32_rn(v[i] - __uint_as_float(hi)));
+                        }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&acce[a]);
+        }
+    }
+    __syncwarp();
+    // every MMA of this CTA has completed before TMEM is released; TMA copies still in
+    // flight (abort only) are drained by the producer
+    const bool fin = mbar_wait_bounded(done, 0);
+    if (warp == 0 && lane == 0 && (*abort_flag || !fin)) {
+        set_status(g.status, BRS_ERR_TIMEOUT);
+        for (long long kg = (issued > NST ? issued - NST : 0); kg < issued; ++kg)
+            mbar_wait_bounded(&full[kg % NST], (uint32_t)((kg / NST) & 1), 200000000ull);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 #endif  // __CUDACC__
 
 }  // namespace brs_tc
