@@ -156,8 +156,9 @@ TC_SHAPES = [(32, 32, 4), (64, 96, 3), (96, 64, 5), (256, 256, 3), (160, 128, 2)
 def test_plane_3xtf32_one_sweep_parity(brs, orc, shape, a, kernel, monkeypatch):
     """Split-TF32 tcgen05 products hold the FP32 per-sweep tolerance (every kernel shape)."""
     pers = kernel.startswith("persistent")
+    tile = kernel[len("persistent"):] if pers else kernel[len("tile"):]
     monkeypatch.setenv("BRSMOOTH_TC_PERSISTENT", "1" if pers else "0")
-    monkeypatch.setenv("BRSMOOTH_TC_PBN" if pers else "BRSMOOTH_TC_BN", kernel[-3:].lstrip("e"))
+    monkeypatch.setenv("BRSMOOTH_TC_PBN" if pers else "BRSMOOTH_TC_BN", tile)
     nx, ny, nz = shape
     u = rounded(initial_guess((nz, ny, nx)), "f32")
     b = rounded(rhs((nz, ny, nx)), "f32")
