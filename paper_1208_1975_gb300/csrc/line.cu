@@ -140,7 +140,7 @@ int line_setup(brs_ctx* c)
         jt = 256 / L.G;
     L.JT = jt;
     // ring depth: stages s..s+2 are being read, the rest are loads in flight
-    L.NS = env_int("BRSMOOTH_LINE_NS", 4);
+    L.NS = env_int("BRSMOOTH_LINE_NS", p.dtype == BRS_F64 ? 4 : 6);
     if (L.NS < 3)
         L.NS = 3;
     while (L.NS > 3 && (size_t)L.NS * (tma_slot_bytes(L, es) + 8) > 227u * 1024u)

@@ -147,13 +147,14 @@ __device__ __forceinline__ void ld_shared_vec_rot(T (&v)[E], const T* p, int lan
     }
 }
 
-// Measured on the 256^3 FP32 workload: conflict-free row reads and three CTAs per SM
-// (80 registers, 4-stage ring) beat two CTAs with a deeper ring.
+// Measured on the 256^3 FP32 workload (same-box A/B): conflict-free row reads with two
+// CTAs per SM (128 registers, 6-stage ring) are fastest; three CTAs per SM cap registers
+// at 80 and spill, and a one-CTA minimum lets ptxas grow past 128 registers.
 #ifndef BRS_LINE_ROT
 #define BRS_LINE_ROT 1
 #endif
 #ifndef BRS_LINE_MINB
-#define BRS_LINE_MINB 3
+#define BRS_LINE_MINB 2
 #endif
 
 template <typename T, int E>
