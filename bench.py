@@ -76,6 +76,24 @@ def _live_copy_gbs():
     return 2 * 4 * n / (best / 1e3) / 1e9
 
 
+def max_over_ranks(x: float, ws: int, device="cuda") -> float:
+    """Largest value of x over all ranks (identity when running alone)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, sweeps: int, slowest_s: float, ws: int) -> float:
+    """Gcell-updates/s of the whole job: every rank sweeps its own replica, the job ends with
+    the slowest rank."""
+    return ws * cells_per_rank * sweeps / slowest_s / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -516,14 +534,9 @@ def main():
     sampler = ClockSampler(local)
     ms = _time_sweeps(ctx, u, b, args.steps, args.warmup, SWEEPS_PER_STEP, stream, barrier)
     clocks = sampler.stop()
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws)
     sweeps_total = args.steps * SWEEPS_PER_STEP
-    value = ws * cells * sweeps_total / (ms / 1e3) / 1e9
+    value = whole_job_rate(cells, sweeps_total, ms / 1e3, ws)
     launch_s = ms / 1e3 / sweeps_total  # one kernel launch per sweep, back to back
     alg_bytes = 3 * 4 * cells
     peak, peak_kind = _peaks()
@@ -549,13 +562,8 @@ def main():
         ctx.sweep_host(uh, bh, SWEEPS_PER_STEP, stream=stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * cells * SWEEPS_PER_STEP * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, ws)
+    e2e = {"value": whole_job_rate(cells, SWEEPS_PER_STEP * e2e_steps, e2e_s, ws), "unit": UNIT,
            "h2d_bytes_per_step": 2 * 4 * cells, "d2h_bytes_per_step": 4 * cells,
            "steps": e2e_steps, "timer": "host wall clock around synchronising calls"}
     ctx.close()

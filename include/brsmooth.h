@@ -232,6 +232,16 @@ int brsmooth_line_jacobi_noalloc(int nx, int ny, int nz, double ax, double ay, d
                                  double omega, int dtype, void* u, const void* b, int nsweeps,
                                  void* stream);
 
+/*
+ * Diagnostic for the failure-detection path: enqueues one CTA that waits on a device-side
+ * barrier nothing ever signals, using the same bounded wait as the sweep kernels; after
+ * `limit_ns` (0 .. 1e9) it records BRS_ERR_TIMEOUT in the context's sticky status and
+ * returns normally (no trap, no fault).  The next call on the context then returns
+ * BRS_ERR_TIMEOUT until brsmooth_last_error() reads and clears it.
+ * Errors: BRS_ERR_ARG (null context or limit out of range), BRS_ERR_CUDA.
+ */
+int brsmooth_selftest_wait(brs_ctx* c, long long limit_ns, void* stream);
+
 /* Number of cell updates one sweep performs (nx*ny*nz summed over patches). */
 long long brsmooth_cells(const brs_ctx* c);
 

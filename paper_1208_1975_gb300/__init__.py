@@ -434,3 +434,11 @@ def brsmooth_line_jacobi_noalloc(nx: int, ny: int, nz: int, a, omega: float, dty
     fn.restype = I
     return fn(int(nx), int(ny), int(nz), float(a[0]), float(a[1]), float(a[2]), float(omega),
               int(dtype_code), u_ptr, b_ptr, int(nsweeps), ctypes.c_void_p(stream))
+
+
+def brsmooth_selftest_wait(ctx, limit_ns: int, stream) -> int:
+    """Bounded wait on a never-signalled device barrier (see the C header)."""
+    fn = lib().brsmooth_selftest_wait
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    return fn(ctx, int(limit_ns), ctypes.c_void_p(stream))
