@@ -20,6 +20,7 @@
 
 #include "batched.cuh"
 #include "line_impl.cuh"
+#include "thomas_tables.h"
 
 namespace {
 
@@ -216,41 +217,7 @@ const void* kernel_for(int dtype, bool gs)
 // single-grid line path).
 std::vector<double> tables_for(int nx, int G, const brs_params& p, double omega)
 {
-    const int E = kE, NP = G * E;
-    int LG = 0;
-    while ((1 << LG) < G) ++LG;
-    const double d = 2.0 * (p.ax + p.ay + p.az);
-    std::vector<double> pv(NP, 0.0), c(NP, 0.0), e(NP, 0.0);
-    pv[0] = 1.0 / d;
-    for (int i = 1; i < nx; ++i)
-        pv[i] = 1.0 / (d - p.ax * p.ax * pv[i - 1]);
-    for (int i = 1; i < nx; ++i)
-        c[i] = p.ax * pv[i - 1];
-    for (int i = 0; i + 1 < nx; ++i)
-        e[i] = p.ax * pv[i + 1];
-    std::vector<double> Af(G, 1.0), Ab(G, 1.0);
-    for (int l = 0; l < G; ++l)
-        for (int q = 0; q < E; ++q) {
-            Af[l] *= c[l * E + q];
-            Ab[l] *= e[l * E + q];
-        }
-    std::vector<double> tab(3 * NP + 2 * LG * G);
-    for (int i = 0; i < NP; ++i) {
-        tab[i] = c[i];
-        tab[NP + i] = e[i];
-        tab[2 * NP + i] = i < nx ? omega * pv[i] : 0.0;
-    }
-    for (int t = 0; t < LG; ++t)
-        for (int l = 0; l < G; ++l) {
-            double f = 1.0, bb = 1.0;
-            for (int m = std::max(0, l - (1 << t) + 1); m <= l; ++m)
-                f *= Af[m];
-            for (int m = l; m < G && m < l + (1 << t); ++m)
-                bb *= Ab[m];
-            tab[3 * NP + t * G + l] = f;
-            tab[3 * NP + LG * G + t * G + l] = bb;
-        }
-    return tab;
+    return scan_thomas_tables<double>(nx, p.ax, 2.0 * (p.ax + p.ay + p.az), omega, kE, G, false);
 }
 
 int build_items(brs_ctx* c, int KC)

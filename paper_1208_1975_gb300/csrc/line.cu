@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "line_impl.cuh"
+#include "thomas_tables.h"
 
 namespace {
 
@@ -28,49 +29,13 @@ int env_int(const char* name, int dflt)
     return (v && *v) ? std::atoi(v) : dflt;
 }
 
-// Factor tables of M_line = tridiag(-ax, d, -ax), d = 2(ax+ay+az), computed once in FP64
-// (the constant block is factored once and shared by every line, Sec. 2 / Sec. 4.3).
+// Factor tables of M_line = tridiag(-ax, 2(ax+ay+az), -ax), computed once in FP64 (the
+// constant block is factored once and shared by every line, Sec. 2 / Sec. 4.3), with the
+// unscaled pivots appended for the adjoint's plain block solve.
 template <typename T>
 std::vector<T> line_tables(int nx, double ax, double ay, double az, double omega, int E, int G)
 {
-    const int NP = G * E;
-    int LG = 0;
-    while ((1 << LG) < G) ++LG;
-    const double d = 2.0 * (ax + ay + az);
-    std::vector<double> p(NP, 0.0), c(NP, 0.0), e(NP, 0.0);
-    p[0] = 1.0 / d;
-    for (int i = 1; i < nx; ++i)
-        p[i] = 1.0 / (d - ax * ax * p[i - 1]);
-    for (int i = 1; i < nx; ++i)
-        c[i] = ax * p[i - 1];
-    for (int i = 0; i + 1 < nx; ++i)
-        e[i] = ax * p[i + 1];
-    std::vector<double> Af(G, 1.0), Ab(G, 1.0);
-    for (int l = 0; l < G; ++l)
-        for (int q = 0; q < E; ++q) {
-            Af[l] *= c[l * E + q];
-            Ab[l] *= e[l * E + q];
-        }
-    std::vector<T> tab(4 * NP + 2 * LG * G);
-    for (int i = 0; i < NP; ++i) {
-        tab[i] = (T)c[i];
-        tab[NP + i] = (T)e[i];
-        tab[2 * NP + i] = (T)(i < nx ? omega * p[i] : 0.0);
-    }
-    for (int t = 0; t < LG; ++t)
-        for (int l = 0; l < G; ++l) {
-            double f = 1.0, b = 1.0;
-            for (int m = (l - (1 << t) + 1 > 0 ? l - (1 << t) + 1 : 0); m <= l; ++m)
-                f *= Af[m];
-            for (int m = l; m < G && m < l + (1 << t); ++m)
-                b *= Ab[m];
-            tab[3 * NP + t * G + l] = (T)f;
-            tab[3 * NP + LG * G + t * G + l] = (T)b;
-        }
-    // unscaled pivots p_i (x = p w) for the plain block solve of the adjoint
-    for (int i = 0; i < NP; ++i)
-        tab[3 * NP + 2 * LG * G + i] = (T)(i < nx ? p[i] : 0.0);
-    return tab;
+    return scan_thomas_tables<T>(nx, ax, 2.0 * (ax + ay + az), omega, E, G, true);
 }
 
 template <typename T, int E, int G>

@@ -26,8 +26,10 @@
 #include <cstring>
 #include <vector>
 
+#include "line_impl.cuh"
 #include "plane.cuh"
 #include "plane_tc.cuh"
+#include "thomas_tables.h"
 
 namespace {
 
@@ -52,6 +54,13 @@ struct PlaneState {
     CUtensorMap m_sxB_hi, m_sxB_lo, m_syB_hi, m_syB_lo;  // S as B operands, box rows BN
     int tc_bn = 128, tc_nst = 3;
     int tc_persistent = 0, tc_pbn = 128, sms = 152;
+    // x-DST + y-Thomas form: per-mode scan-Thomas tables along y and the map of t2 as the
+    // [k][y][p] A operand of the inverse x-transform
+    int form = 2;          // 2: 2D sine basis (four products); 1: x-DST + y-Thomas
+    int yE = 0;            // cells per lane of the y solve (32 lanes per line)
+    int ytab_len = 0;      // table entries per x-mode
+    void* ytab = nullptr;  // [nx][ytab_len], context dtype (FP32 on the tensor path)
+    CUtensorMap m_W2_hi, m_W2_lo;
 };
 
 // Tile shapes of the tensor-core products (N per CTA, ring stages): 128 x 128 tiles with a
@@ -322,6 +331,158 @@ int plane_pass_tc(brs_ctx* c, const float* uin, float* uout, const float* b, int
     return brs_cuda_status(e);
 }
 
+// y-Thomas of the x-DST form: for x-mode p the plane block reduces to the tridiagonal system
+//   (ay Ty + (ax s_p + 2 az) I) w = C1[p][:]   (along y),
+// solved exactly with the cross-lane scan Thomas (32 lanes per line, E cells per lane) and
+// pivots factored once per mode.  A CTA owns 8 consecutive modes (one warp each, tables
+// loaded once) over a chunk of planes; each plane's 8 solved lines are written transposed,
+// W[k][y][p], through a padded shared-memory tile (32-byte row segments).
+// SPLIT = 3/1: input and output are TF32 hi (+lo) pairs; SPLIT = 0: plain T.
+constexpr int kYModes = 8;     // modes (warps) per CTA
+constexpr int kYPlanes = 8;    // planes per CTA
+
+template <typename T, int E, int SPLIT>
+__global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict__ cin_hi,
+                                                            const T* __restrict__ cin_lo,
+                                                            T* __restrict__ w_hi, T* __restrict__ w_lo,
+                                                            const T* __restrict__ ytab, int tab_len,
+                                                            int nx, int ny, int k0, int kstep,
+                                                            int nbatch)
+{
+    extern __shared__ __align__(16) unsigned char ysm[];
+    T* tile = reinterpret_cast<T*>(ysm);
+    const int stride = (ny % 2 == 0) ? ny + 1 : ny + 2;  // odd: conflict-free columns
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * kYModes + warp;
+    const bool pin = p < nx;  // warp-uniform
+    const long long plane = (long long)nx * ny;
+    brs::LineTables<T, E, 32> tb;
+    tb.load(ytab + (long long)(pin ? p : 0) * tab_len, lane);
+    const int b0 = blockIdx.y * kYPlanes;
+    const int b1 = min(nbatch, b0 + kYPlanes);
+    for (int bi = b0; bi < b1; ++bi) {
+        const int k = k0 + bi * kstep;
+        if (pin) {
+            const long long row = (long long)k * plane + (long long)p * ny;
+            T r[E];
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int y = lane * E + q;
+                T v = T(0);
+                if (y < ny) {
+                    v = cin_hi[row + y];
+                    if (SPLIT == 3)
+                        v += cin_lo[row + y];
+                }
+                r[q] = v;
+            }
+            brs::line_solve<T, E, 32>(r, tb, lane);
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int y = lane * E + q;
+                if (y < ny)
+                    tile[warp * stride + y] = tb.wp[q] * r[q];
+            }
+        }
+        __syncthreads();
+        // transposed write: thread (y-row, mode) pairs, 8 consecutive modes per row
+        for (int t = threadIdx.x; t < ny * kYModes; t += blockDim.x) {
+            const int y = t / kYModes, m = t % kYModes;
+            const int pp = blockIdx.x * kYModes + m;
+            if (pp < nx) {
+                const T v = tile[m * stride + y];
+                const long long o = (long long)k * plane + (long long)y * nx + pp;
+                if (SPLIT == 0) {
+                    w_hi[o] = v;
+                } else {
+                    const uint32_t hi = brs_tc::tf32_rn((float)v);
+                    w_hi[o] = __uint_as_float(hi);
+                    if (SPLIT == 3)
+                        w_lo[o] = __uint_as_float(brs_tc::tf32_rn((float)v - __uint_as_float(hi)));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int SPLIT>
+cudaError_t launch_ythomas(const PlaneState* P, const T* cin_hi, const T* cin_lo, T* w_hi,
+                           T* w_lo, int nx, int ny, int k0, int kstep, int nbatch, cudaStream_t s)
+{
+    const int stride = (ny % 2 == 0) ? ny + 1 : ny + 2;
+    const size_t smem = (size_t)kYModes * stride * sizeof(T);
+    dim3 grid((nx + kYModes - 1) / kYModes, (nbatch + kYPlanes - 1) / kYPlanes);
+    const T* tab = static_cast<const T*>(P->ytab);
+    const int tl = P->ytab_len;
+#define BRS_YT_CASE(EE)                                                                          \
+    if (P->yE == EE) {                                                                           \
+        plane_ythomas_kernel<T, EE, SPLIT><<<grid, 256, smem, s>>>(                              \
+            cin_hi, cin_lo, w_hi, w_lo, tab, tl, nx, ny, k0, kstep, nbatch);                     \
+        return cudaGetLastError();                                                               \
+    }
+    BRS_YT_CASE(4)
+    BRS_YT_CASE(8)
+    BRS_YT_CASE(12)
+    BRS_YT_CASE(16)
+#undef BRS_YT_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int SPLIT>
+const void* ythomas_kernel_for(int E)
+{
+    if (E == 4) return (const void*)plane_ythomas_kernel<T, 4, SPLIT>;
+    if (E == 8) return (const void*)plane_ythomas_kernel<T, 8, SPLIT>;
+    if (E == 12) return (const void*)plane_ythomas_kernel<T, 12, SPLIT>;
+    return (const void*)plane_ythomas_kernel<T, 16, SPLIT>;
+}
+
+// x-DST + y-Thomas form on the tensor path: gather, P1 (x-DST), y-Thomas, P4 (inverse x-DST
+// fused with the update).
+template <int SPLIT>
+int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b, int k0,
+                       int kstep, int nbatch, cudaStream_t s)
+{
+    PlaneState* P = ps(c);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const long long plane = (long long)nx * ny;
+    {
+        int blocks = (int)((plane * nbatch + 255) / 256);
+        if (blocks > 152 * 16)
+            blocks = 152 * 16;
+        plane_gather_split_kernel<<<blocks, 256, 0, s>>>(uin, b, (float*)P->t2, (float*)P->t2_lo,
+                                                         nx, ny, nz, (float)c->p.az, k0, kstep,
+                                                         nbatch, SPLIT);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+    }
+    brs_tc::TcArgs g{};
+    g.k0 = k0;
+    g.kstep = kstep;
+    g.plane = plane;
+    g.status = c->dev_status;
+    // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]  -> t1
+    g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
+    g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo;
+    cudaError_t e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P, P->m_sx_hi, P->m_sx_lo, P->m_R_hi,
+                                                        P->m_R_lo, g, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // y-Thomas per x-mode: t1 [p][y] -> t2 [y][p]
+    e = launch_ythomas<float, SPLIT>(P, (const float*)P->t1, (const float*)P->t1_lo, (float*)P->t2,
+                                     (float*)P->t2_lo, nx, ny, k0, kstep, nbatch, s);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // P4: X[y][x] = sum_p W[y][p] Sx[x][p]; u_k <- (1-omega) u_k + omega X
+    g.M = ny; g.N = nx; g.K = nx; g.a_batched = 1; g.b_batched = 0;
+    g.out_hi = nullptr; g.out_lo = nullptr; g.u = uin; g.uout = uout; g.omega = (float)c->omega;
+    e = launch_tc<SPLIT, brs_tc::EPI_UPDATE>(P, P->m_W2_hi, P->m_W2_lo, P->m_sxB_hi, P->m_sxB_lo,
+                                             g, nbatch, s);
+    return brs_cuda_status(e);
+}
+
 // One plane-block solve + update for planes k0, k0+kstep, ... (nbatch of them), reading
 // neighbours from `uin` and writing the updated planes to `uout`.
 template <typename T>
@@ -354,6 +515,18 @@ int plane_pass(brs_ctx* c, const T* uin, T* uout, const T* b, int k0, int kstep,
     e = launch_gemm<T, EPI_STORE>(Sx, R, T1, g, nbatch, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
+    if (P->form == 1) {
+        // y-Thomas per x-mode (T1 [p][y] -> T2 [y][p]), then the inverse x-DST fused with the
+        // update; P1 wrote plane b of T1 at b*plane, so pass k0 = 0, kstep = 1 here
+        e = launch_ythomas<T, 0>(P, T1, nullptr, T2, nullptr, nx, ny, 0, 1, nbatch, s);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        g = GemmArgs{};
+        g.M = ny; g.N = nx; g.K = nx; g.strideA = plane; g.strideB = 0; g.strideC = plane;
+        g.u = uin; g.strideU = plane; g.k0 = k0; g.kstep = kstep; g.omega = c->omega;
+        e = launch_gemm<T, EPI_UPDATE>(T2, Sx, uout, g, nbatch, s);
+        return brs_cuda_status(e);
+    }
     // P2: Q[p][q] = (sum_y C1[p][y] Sy[q][y]) / L[q][p]
     g = GemmArgs{};
     g.M = nx; g.N = ny; g.K = ny; g.strideA = plane; g.strideB = 0; g.strideC = plane;
@@ -447,6 +620,50 @@ int encode_map(CUtensorMap* m, const void* ptr, int kdim, int rows, int planes, 
     return r == CUDA_SUCCESS ? BRS_OK : BRS_ERR_CUDA;
 }
 
+// Scan-Thomas tables of the y systems of every x-mode p:
+//   tridiag(-ay, ax s_p + 2 ay + 2 az, -ay) of size ny,  s_p = 2 - 2 cos((p+1) pi/(nx+1)).
+template <typename T>
+int ythomas_setup(brs_ctx* c)
+{
+    PlaneState* P = ps(c);
+    const brs_params& p = c->p;
+    const int ny = p.ny;
+    P->yE = ny <= 128 ? 4 : ny <= 256 ? 8 : ny <= 384 ? 12 : 16;
+    std::vector<T> all;
+    for (int q = 0; q < p.nx; ++q) {
+        const double sp = 2.0 - 2.0 * std::cos(M_PI * (q + 1) / (p.nx + 1));
+        auto t = scan_thomas_tables<T>(ny, p.ay, p.ax * sp + 2.0 * p.ay + 2.0 * p.az, 1.0, P->yE,
+                                       32, false);
+        P->ytab_len = (int)t.size();
+        all.insert(all.end(), t.begin(), t.end());
+    }
+    cudaError_t e = cudaMalloc(&P->ytab, all.size() * sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->ytab, all.data(), all.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    const int stride = (ny % 2 == 0) ? ny + 1 : ny + 2;
+    const size_t smem = (size_t)kYModes * stride * sizeof(T);
+    const void* ks[2];
+    if (sizeof(T) == 8) {
+        ks[0] = ythomas_kernel_for<T, 0>(P->yE);
+        ks[1] = ks[0];
+    } else {
+        ks[0] = ythomas_kernel_for<T, 3>(P->yE);
+        ks[1] = ythomas_kernel_for<T, 1>(P->yE);
+    }
+    const void* k0s[] = {ks[0], ks[1], ythomas_kernel_for<T, 0>(P->yE)};
+    for (const void* k : k0s) {
+        cudaFuncAttributes fa{};
+        cudaError_t ce = cudaFuncGetAttributes(&fa, k);
+        if (ce == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
+            ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ce != cudaSuccess)
+            return brs_cuda_status(ce);
+    }
+    return BRS_OK;
+}
+
 int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double>& sy)
 {
     PlaneState* P = ps(c);
@@ -502,6 +719,8 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
     enc(&P->m_Q_lo, P->t2_lo, ny, nx, nz, BN);
     enc(&P->m_W_hi, P->t1, nx, ny, nz, BMr);
     enc(&P->m_W_lo, P->t1_lo, nx, ny, nz, BMr);
+    enc(&P->m_W2_hi, P->t2, nx, ny, nz, BMr);
+    enc(&P->m_W2_lo, P->t2_lo, nx, ny, nz, BMr);
     if (e != BRS_OK)
         return e;
     // raise the kernels' dynamic shared-memory limit (never lower it)
@@ -562,6 +781,13 @@ int plane_setup(brs_ctx* c)
     P->nx = p.nx;
     P->ny = p.ny;
     P->math = math;
+    {
+        const char* fenv = std::getenv("BRSMOOTH_PLANE_FORM");
+        // x-DST + y-Thomas (half the transform work) unless asked for the 2D sine basis or the
+        // y lines exceed the scan-Thomas limit of 512 cells
+        const int want = fenv ? std::atoi(fenv) : 1;
+        P->form = (want == 1 && p.ny <= 512) ? 1 : 2;
+    }
     std::vector<double> sx = dst1(p.nx), sy = dst1(p.ny), il((size_t)p.nx * p.ny);
     for (int pp = 0; pp < p.nx; ++pp)
         for (int q = 0; q < p.ny; ++q) {
@@ -578,6 +804,8 @@ int plane_setup(brs_ctx* c)
                 cudaMemcpy(P->ilam, ilf.data(), ilf.size() * 4, cudaMemcpyHostToDevice));
         if (rc == BRS_OK)
             rc = tc_setup(c, sx, sy);
+        if (rc == BRS_OK && P->form == 1)
+            rc = ythomas_setup<float>(c);
         return rc;
     }
     if (p.dtype == BRS_F64)
@@ -593,6 +821,8 @@ int plane_setup(brs_ctx* c)
         rc = brs_cuda_status(cudaMalloc(&P->t1, bytes));
     if (rc == BRS_OK)
         rc = brs_cuda_status(cudaMalloc(&P->t2, bytes));
+    if (rc == BRS_OK && P->form == 1)
+        rc = p.dtype == BRS_F64 ? ythomas_setup<double>(c) : ythomas_setup<float>(c);
     return rc;
 }
 
@@ -601,7 +831,8 @@ void plane_teardown(brs_ctx* c)
     PlaneState* P = ps(c);
     if (!P)
         return;
-    for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo})
+    for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo,
+                    P->ytab})
         if (q)
             cudaFree(q);
     delete P;
@@ -632,7 +863,12 @@ int plane_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, c
         const float* ui = static_cast<const float*>(uin);
         float* uo = static_cast<float*>(uout);
         const float* bb = static_cast<const float*>(b);
+        const bool xdst = ps(c)->form == 1;
         auto pass = [&](int k0, int kstep, int nb) {
+            if (xdst)
+                return math == BRS_PLANE_3XTF32
+                           ? plane_pass_tc_xdst<3>(c, ui, uo, bb, k0, kstep, nb, s)
+                           : plane_pass_tc_xdst<1>(c, ui, uo, bb, k0, kstep, nb, s);
             return math == BRS_PLANE_3XTF32 ? plane_pass_tc<3>(c, ui, uo, bb, k0, kstep, nb, s)
                                             : plane_pass_tc<1>(c, ui, uo, bb, k0, kstep, nb, s);
         };

@@ -496,8 +496,29 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
             int m0, n0, plane;
             decode(t, &m0, &n0, &plane);
             const uint32_t trow = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
+            // EPI_UPDATE: the old values of the next 32-column chunk are loaded while the
+            // current chunk is processed
+            const int mrow0 = m0 + q * 32;
+            float unext[32];
+            auto load_u = [&](int c, float (&dst)[32]) {
+                const int n = n0 + c * 32 + lane;
+                const long long ob = (long long)plane * g.plane + (long long)mrow0 * g.N + n;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    dst[i] = (n < g.N && mrow0 + i < g.M) ? g.u[ob + (long long)i * g.N] : 0.0f;
+            };
+            if (EPI == EPI_UPDATE)
+                load_u(0, unext);
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
+                float ucur[32];
+                if (EPI == EPI_UPDATE) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        ucur[i] = unext[i];
+                    if (c + 1 < BN / 32)
+                        load_u(c + 1, unext);
+                }
                 uint32_t r[32];
                 tmem_ld32(trow + (uint32_t)(c * 32), r);
 #pragma unroll
@@ -524,15 +545,11 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
                         v[i] *= sc[i];
                 }
                 if (EPI == EPI_UPDATE) {
-                    float uo[32];
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        uo[i] = (nok && mrow + i < g.M) ? g.u[obase + (long long)i * g.N] : 0.0f;
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
                         if (nok && mrow + i < g.M)
                             g.uout[obase + (long long)i * g.N] =
-                                fmaf(g.omega, v[i], (1.0f - g.omega) * uo[i]);
+                                fmaf(g.omega, v[i], (1.0f - g.omega) * ucur[i]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
