@@ -199,25 +199,41 @@ cudaError_t launch_gemm(const T* A, const T* B, T* C, const GemmArgs& g, int bat
 }
 
 // R_k = b_k + az (u_{k-1} + u_{k+1}) split into TF32 hi/lo parts, stored at plane k.
+// Four cells per thread with 16-byte accesses (nx * ny is a multiple of 4 on this path).
 __global__ void plane_gather_split_kernel(const float* __restrict__ u, const float* __restrict__ b,
                                           float* __restrict__ rhi, float* __restrict__ rlo,
                                           int nx, int ny, int nz, float az, int k0, int kstep,
                                           int nbatch, int split)
 {
     const long long plane = (long long)nx * ny;
-    const long long total = plane * nbatch;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+    const long long plane4 = plane / 4;
+    const long long total4 = plane4 * nbatch;
+    const float4* u4 = reinterpret_cast<const float4*>(u);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    float4* hi4 = reinterpret_cast<float4*>(rhi);
+    float4* lo4 = reinterpret_cast<float4*>(rlo);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total4;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long bi = t / plane;
-        const long long o = t - bi * plane;
+        const long long bi = t / plane4;
+        const long long o = t - bi * plane4;
         const int k = k0 + (int)bi * kstep;
-        const long long gi = (long long)k * plane + o;
-        const float sz = (k > 0 ? u[gi - plane] : 0.f) + (k + 1 < nz ? u[gi + plane] : 0.f);
-        const float r = fmaf(az, sz, b[gi]);
-        const uint32_t hi = brs_tc::tf32_rn(r);
-        rhi[gi] = __uint_as_float(hi);
+        const long long gi = (long long)k * plane4 + o;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 um = k > 0 ? u4[gi - plane4] : z4;
+        const float4 up = k + 1 < nz ? u4[gi + plane4] : z4;
+        const float4 bb = b4[gi];
+        float r[4] = {fmaf(az, um.x + up.x, bb.x), fmaf(az, um.y + up.y, bb.y),
+                      fmaf(az, um.z + up.z, bb.z), fmaf(az, um.w + up.w, bb.w)};
+        float h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t hb = brs_tc::tf32_rn(r[q]);
+            h[q] = __uint_as_float(hb);
+            l[q] = __uint_as_float(brs_tc::tf32_rn(r[q] - h[q]));
+        }
+        hi4[gi] = make_float4(h[0], h[1], h[2], h[3]);
         if (split == 3)
-            rlo[gi] = __uint_as_float(brs_tc::tf32_rn(r - __uint_as_float(hi)));
+            lo4[gi] = make_float4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -289,7 +305,7 @@ int plane_pass_tc(brs_ctx* c, const float* uin, float* uout, const float* b, int
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const long long plane = (long long)nx * ny;
     {
-        int blocks = (int)((plane * nbatch + 255) / 256);
+        int blocks = (int)((plane / 4 * nbatch + 255) / 256);
         if (blocks > 152 * 16)
             blocks = 152 * 16;
         plane_gather_split_kernel<<<blocks, 256, 0, s>>>(uin, b, (float*)P->t2, (float*)P->t2_lo,
@@ -341,6 +357,12 @@ int plane_pass_tc(brs_ctx* c, const float* uin, float* uout, const float* b, int
 constexpr int kYModes = 8;     // modes (warps) per CTA
 constexpr int kYPlanes = 8;    // planes per CTA
 
+__host__ __device__ inline int ythomas_stride(int ny)
+{
+    const int s0 = ny + (ny >> 3) + 1;
+    return s0 + (((4 - s0) % 32) + 32) % 32;
+}
+
 template <typename T, int E, int SPLIT>
 __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict__ cin_hi,
                                                             const T* __restrict__ cin_lo,
@@ -351,7 +373,10 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
 {
     extern __shared__ __align__(16) unsigned char ysm[];
     T* tile = reinterpret_cast<T*>(ysm);
-    const int stride = (ny % 2 == 0) ? ny + 1 : ny + 2;  // odd: conflict-free columns
+    // tile[m][y] at m * stride + y + y / 8: a pad word after every 8 cells makes a lane's
+    // 8-cell chunk writes hit distinct banks, and stride = 4 (mod 32) does the same for the
+    // transposed reads of 8 modes x 4 consecutive y
+    const int stride = ythomas_stride(ny);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * kYModes + warp;
     const bool pin = p < nx;  // warp-uniform
@@ -381,7 +406,7 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
             for (int q = 0; q < E; ++q) {
                 const int y = lane * E + q;
                 if (y < ny)
-                    tile[warp * stride + y] = tb.wp[q] * r[q];
+                    tile[warp * stride + y + (y >> 3)] = tb.wp[q] * r[q];
             }
         }
         __syncthreads();
@@ -390,7 +415,7 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
             const int y = t / kYModes, m = t % kYModes;
             const int pp = blockIdx.x * kYModes + m;
             if (pp < nx) {
-                const T v = tile[m * stride + y];
+                const T v = tile[m * stride + y + (y >> 3)];
                 const long long o = (long long)k * plane + (long long)y * nx + pp;
                 if (SPLIT == 0) {
                     w_hi[o] = v;
@@ -410,8 +435,7 @@ template <typename T, int SPLIT>
 cudaError_t launch_ythomas(const PlaneState* P, const T* cin_hi, const T* cin_lo, T* w_hi,
                            T* w_lo, int nx, int ny, int k0, int kstep, int nbatch, cudaStream_t s)
 {
-    const int stride = (ny % 2 == 0) ? ny + 1 : ny + 2;
-    const size_t smem = (size_t)kYModes * stride * sizeof(T);
+    const size_t smem = (size_t)kYModes * ythomas_stride(ny) * sizeof(T);
     dim3 grid((nx + kYModes - 1) / kYModes, (nbatch + kYPlanes - 1) / kYPlanes);
     const T* tab = static_cast<const T*>(P->ytab);
     const int tl = P->ytab_len;
@@ -448,7 +472,7 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const long long plane = (long long)nx * ny;
     {
-        int blocks = (int)((plane * nbatch + 255) / 256);
+        int blocks = (int)((plane / 4 * nbatch + 255) / 256);
         if (blocks > 152 * 16)
             blocks = 152 * 16;
         plane_gather_split_kernel<<<blocks, 256, 0, s>>>(uin, b, (float*)P->t2, (float*)P->t2_lo,
@@ -642,8 +666,7 @@ int ythomas_setup(brs_ctx* c)
         e = cudaMemcpy(P->ytab, all.data(), all.size() * sizeof(T), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    const int stride = (ny % 2 == 0) ? ny + 1 : ny + 2;
-    const size_t smem = (size_t)kYModes * stride * sizeof(T);
+    const size_t smem = (size_t)kYModes * ythomas_stride(ny) * sizeof(T);
     const void* ks[2];
     if (sizeof(T) == 8) {
         ks[0] = ythomas_kernel_for<T, 0>(P->yE);
