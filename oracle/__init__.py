@@ -70,11 +70,15 @@ def _load():
         "orc_plane_minv": [I, I, I, P, P, P],
         "orc_plane_jacobi": [I, I, I, D, D, D, D, P, P, P, P, P],
         "orc_plane_gs": [I, I, I, D, D, D, D, I, P, P, P, P],
+        "orc_box_inverse": [I, I, I, D, D, D, P, P],
+        "orc_box_minv": [I, I, I, I, I, I, P, P, P],
+        "orc_box_jacobi": [I, I, I, I, I, I, D, D, D, D, P, P, P, P, P],
+        "orc_box_gs": [I, I, I, I, I, I, D, D, D, D, I, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = I if name == "orc_plane_factor" else None
+        fn.restype = I if name in ("orc_plane_factor", "orc_box_inverse") else None
     lib.orc_sumsq.argtypes = [L, P]
     lib.orc_sumsq.restype = D
     _lib = lib
@@ -164,8 +168,33 @@ def plane_factor(nx: int, ny: int, a) -> PlaneFactor:
     return _factor_cache[key]
 
 
-def block_minv(r, a, block: str):
-    """M^{-1} r for the block diagonal M of the x-line ('line') or xy-plane ('plane') partition."""
+_box_cache: dict = {}
+
+
+def box_inverse(box, a) -> np.ndarray:
+    """Ahat_b = A_b^{-1} (n x n, n = bx by bz, local order x fastest) of the box block A_b,
+    computed once per block shape and coefficients (Sec. 4.3) by a dense Cholesky solve."""
+    bx, by, bz = (int(v) for v in box)
+    key = (bx, by, bz, tuple(map(float, a)))
+    if key not in _box_cache:
+        n = bx * by * bz
+        inv, work = np.empty((n, n)), np.empty((n, n))
+        if _load().orc_box_inverse(bx, by, bz, *key[3], _ptr(inv), _ptr(work)) != 0:
+            raise ValueError("box block is not positive definite")
+        _box_cache[key] = inv
+    return _box_cache[key]
+
+
+def _check_box(nx, ny, nz, box):
+    bx, by, bz = (int(v) for v in box)
+    if min(bx, by, bz) < 1 or nx % bx or ny % by or nz % bz:
+        raise ValueError(f"box {box} does not tile the {nx}x{ny}x{nz} grid")
+    return bx, by, bz
+
+
+def block_minv(r, a, block: str, box=None):
+    """M^{-1} r for the block diagonal M of the x-line ('line'), xy-plane ('plane') or
+    bx*by*bz box ('box', with box=(bx, by, bz)) partition."""
     r = _f64(r)
     nx, ny, nz = _dims(r)
     out = np.empty_like(r)
@@ -174,6 +203,10 @@ def block_minv(r, a, block: str):
     elif block == "plane":
         f = plane_factor(nx, ny, a)
         _load().orc_plane_minv(nx, ny, nz, _ptr(f.L), _ptr(r), _ptr(out))
+    elif block == "box":
+        bx, by, bz = _check_box(nx, ny, nz, box)
+        inv = box_inverse((bx, by, bz), a)
+        _load().orc_box_minv(nx, ny, nz, bx, by, bz, _ptr(inv), _ptr(r), _ptr(out))
     else:
         raise ValueError(block)
     return out
@@ -181,17 +214,32 @@ def block_minv(r, a, block: str):
 
 # ---------------------------------------------------------------- sweeps
 
-def sweep(u, b, a, *, block: str = "line", method: str = JACOBI, omega: float = 0.8):
+def sweep(u, b, a, *, block: str = "line", method: str = JACOBI, omega: float = 0.8,
+          box=None):
     """One block-relaxation sweep; returns the new iterate (inputs are not modified).
 
     method 'jacobi': v = u + omega M^{-1}(b - A u) from the old iterate only (Alg. 2).
     methods 'gs_lex' / 'gs_reverse' / 'gs_zebra': block Gauss-Seidel (Eq. sm:blockm),
-    blocks visited lexicographically, in reverse, or even-then-odd, newest values read.
+    blocks visited lexicographically, in reverse, or in two colours (even-then-odd j+k for
+    lines, k for planes, bi+bj+bk for boxes), newest values read.
+    block 'box' takes box=(bx, by, bz) (the spatial blocks of Sec. 2 and Sec. 3).
     """
     u, b = _f64(u), _f64(b)
     nx, ny, nz = _dims(u)
     lib = _load()
     a = tuple(map(float, a))
+    if block == "box":
+        bx, by, bz = _check_box(nx, ny, nz, box)
+        inv = box_inverse((bx, by, bz), a)
+        if method == JACOBI:
+            v, work = np.empty_like(u), np.empty_like(u)
+            lib.orc_box_jacobi(nx, ny, nz, bx, by, bz, *a, float(omega), _ptr(inv), _ptr(u),
+                               _ptr(b), _ptr(v), _ptr(work))
+            return v
+        v = u.copy()
+        lib.orc_box_gs(nx, ny, nz, bx, by, bz, *a, float(omega), _GS_ORDER[method], _ptr(inv),
+                       _ptr(v), _ptr(b))
+        return v
     if method == JACOBI:
         v = np.empty_like(u)
         work = np.empty_like(u)
@@ -341,9 +389,14 @@ def assemble_A(nx: int, ny: int, nz: int, a) -> np.ndarray:
     return A
 
 
-def block_of(nx: int, ny: int, nz: int, block: str) -> np.ndarray:
-    """Block label of every cell (x fastest): line -> j + ny k, plane -> k."""
+def block_of(nx: int, ny: int, nz: int, block: str, box=None) -> np.ndarray:
+    """Block label of every cell (x fastest): line -> j + ny k, plane -> k,
+    box -> bi + nbx (bj + nby bk) with (bi, bj, bk) = (i // bx, j // by, k // bz)."""
     k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    if block == "box":
+        bx, by, bz = _check_box(nx, ny, nz, box)
+        nbx, nby = nx // bx, ny // by
+        return (i // bx + nbx * (j // by + nby * (k // bz))).ravel()
     return (j + ny * k).ravel() if block == "line" else k.ravel()
 
 

@@ -17,7 +17,8 @@
  *
  * Block iteration (Sec. 2, Eq. blockiteration2):  u <- u + omega * M^{-1} (b - A u)
  * where M is the block diagonal of A for a partition into full x-lines (one block per
- * (j,k)) or full xy-planes (one block per k).  Block Jacobi evaluates every block from
+ * (j,k)), full xy-planes (one block per k) or bx*by*bz boxes (the spatial blocks of the
+ * paper, one precomputed inverse applied as a dense product).  Block Jacobi evaluates every block from
  * the same old iterate into a second vector (Sec. 2, Alg. 2 step 4); block
  * Gauss-Seidel (Eq. sm:blockm) visits the blocks one after another, always reading the
  * newest values.
@@ -299,4 +300,173 @@ void orc_plane_gs(int nx, int ny, int nz, double ax, double ay, double az, doubl
         for (long q = 0; q < m; ++q)
             u[(long)k * m + q] += omega * work[q];
     }
+}
+
+/*
+ * Box blocks (Sec. 2; block sizes of Sec. 3; inversion of Sec. 4.3).  The grid is cut
+ * into spatial blocks of bx*by*bz cells, every grid dimension a multiple of the block
+ * dimension (the case in which one inverse serves every block, Sec. 4.3).  Inside a block
+ * the cells are numbered x fastest, l = lx + bx*(ly + by*lz), n = bx*by*bz.
+ *
+ * The diagonal block A_b of A is the same for every block: the 7-point stencil restricted
+ * to the block's cells (couplings leaving the block dropped).  Its inverse Ahat_b is
+ * computed once (Sec. 4.3), here by a dense Cholesky factorisation A_b = L L^T followed by
+ * the two triangular solves for every unit vector.  Ainv is n*n, row major.
+ * `work` is caller scratch of n*n doubles.  Returns 0, or -1 if a pivot is not positive.
+ */
+int orc_box_inverse(int bx, int by, int bz, double ax, double ay, double az, double *Ainv,
+                    double *work)
+{
+    int n = bx * by * bz;
+    double *L = work;
+    /* assemble A_b into L (lower part is overwritten by the factor) */
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            int rx = r % bx, ry = (r / bx) % by, rz = r / (bx * by);
+            int cx = c % bx, cy = (c / bx) % by, cz = c / (bx * by);
+            double a = 0.0;
+            if (r == c)
+                a = 2.0 * (ax + ay + az);
+            else if (ry == cy && rz == cz && (rx - cx == 1 || cx - rx == 1))
+                a = -ax;
+            else if (rx == cx && rz == cz && (ry - cy == 1 || cy - ry == 1))
+                a = -ay;
+            else if (rx == cx && ry == cy && (rz - cz == 1 || cz - rz == 1))
+                a = -az;
+            L[(long)r * n + c] = a;
+        }
+    /* Cholesky, column by column (Cholesky-Banachiewicz) */
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c <= r; ++c) {
+            double s = L[(long)r * n + c];
+            for (int t = 0; t < c; ++t)
+                s -= L[(long)r * n + t] * L[(long)c * n + t];
+            if (c < r) {
+                L[(long)r * n + c] = s / L[(long)c * n + c];
+            } else {
+                if (!(s > 0.0))
+                    return -1;
+                L[(long)r * n + r] = sqrt(s);
+            }
+        }
+    /* column c of the inverse: L y = e_c, then L^T x = y */
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int c = 0; c < n; ++c) {
+        for (int r = 0; r < n; ++r) {
+            double s = (r == c) ? 1.0 : 0.0;
+            for (int t = 0; t < r; ++t)
+                s -= L[(long)r * n + t] * y[t];
+            y[r] = s / L[(long)r * n + r];
+        }
+        for (int r = n - 1; r >= 0; --r) {
+            double s = y[r];
+            for (int t = r + 1; t < n; ++t)
+                s -= L[(long)t * n + r] * Ainv[(long)t * n + c];
+            Ainv[(long)r * n + c] = s / L[(long)r * n + r];
+        }
+    }
+    free(y);
+    return 0;
+}
+
+/* Grid index of local cell l of the block with block coordinates (bi, bj, bk). */
+static long box_cell(int nx, int ny, int bx, int by, int bz, int bi, int bj, int bk, int l)
+{
+    int lx = l % bx, ly = (l / bx) % by, lz = l / (bx * by);
+    return IDX(bi * bx + lx, bj * by + ly, bk * bz + lz);
+}
+
+/* out = M^{-1} r for the box partition: for every block d_b = Ahat_b r_b (the dense
+ * matrix-vector product of Alg. 2 step 2).  out may equal r. */
+void orc_box_minv(int nx, int ny, int nz, int bx, int by, int bz, const double *Ainv,
+                  const double *r, double *out)
+{
+    int n = bx * by * bz;
+    int nbx = nx / bx, nby = ny / by, nbz = nz / bz;
+    long nblk = (long)nbx * nby * nbz;
+#pragma omp parallel
+    {
+        double *rb = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        double *db = rb + n;
+#pragma omp for schedule(static)
+        for (long q = 0; q < nblk; ++q) {
+            int bi = (int)(q % nbx), bj = (int)((q / nbx) % nby), bk = (int)(q / ((long)nbx * nby));
+            for (int l = 0; l < n; ++l)
+                rb[l] = r[box_cell(nx, ny, bx, by, bz, bi, bj, bk, l)];
+            for (int l = 0; l < n; ++l) {
+                double s = 0.0;
+                for (int m = 0; m < n; ++m)
+                    s += Ainv[(long)l * n + m] * rb[m];
+                db[l] = s;
+            }
+            for (int l = 0; l < n; ++l)
+                out[box_cell(nx, ny, bx, by, bz, bi, bj, bk, l)] = db[l];
+        }
+        free(rb);
+    }
+}
+
+/*
+ * Damped block Jacobi with box blocks (Alg. 2): r = b - A u, d_b = Ahat_b r_b for every
+ * block, v = u + omega d.  `work` is caller scratch of nx*ny*nz doubles.
+ */
+void orc_box_jacobi(int nx, int ny, int nz, int bx, int by, int bz, double ax, double ay,
+                    double az, double omega, const double *Ainv, const double *u,
+                    const double *b, double *v, double *work)
+{
+    long n = (long)nx * ny * nz;
+    orc_residual(nx, ny, nz, ax, ay, az, u, b, work);
+    orc_box_minv(nx, ny, nz, bx, by, bz, Ainv, work, work);
+#pragma omp parallel for schedule(static)
+    for (long t = 0; t < n; ++t)
+        v[t] = u[t] + omega * work[t];
+}
+
+/*
+ * Block Gauss-Seidel with box blocks (Eq. sm:blockm, Alg. 1 with a fixed visiting order):
+ * the blocks are visited one at a time, each reading the newest values,
+ *   r_b = b_b - (A u)_b,  u_b <- u_b + omega * Ahat_b r_b.
+ * order 0: lexicographic in (bk, bj, bi) with bi fastest; 1: reverse lexicographic;
+ * 2: two colours, blocks with bi+bj+bk even first, then odd, each colour lexicographic.
+ */
+void orc_box_gs(int nx, int ny, int nz, int bx, int by, int bz, double ax, double ay,
+                double az, double omega, int order, const double *Ainv, double *u,
+                const double *b)
+{
+    int n = bx * by * bz;
+    int nbx = nx / bx, nby = ny / by, nbz = nz / bz;
+    long nblk = (long)nbx * nby * nbz;
+    long *seq = (long *)malloc(sizeof(long) * (size_t)nblk);
+    long cnt = 0;
+    if (order == 2) {
+        for (int colour = 0; colour < 2; ++colour)
+            for (long q = 0; q < nblk; ++q) {
+                long s = q % nbx + (q / nbx) % nby + q / ((long)nbx * nby);
+                if ((int)(s & 1) == colour)
+                    seq[cnt++] = q;
+            }
+    } else {
+        for (long q = 0; q < nblk; ++q)
+            seq[q] = (order == 1) ? nblk - 1 - q : q;
+    }
+    double *rb = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    double *db = rb + n;
+    for (long s = 0; s < nblk; ++s) {
+        long q = seq[s];
+        int bi = (int)(q % nbx), bj = (int)((q / nbx) % nby), bk = (int)(q / ((long)nbx * nby));
+        for (int l = 0; l < n; ++l) {
+            int i = bi * bx + l % bx, j = bj * by + (l / bx) % by, k = bk * bz + l / (bx * by);
+            rb[l] = b[IDX(i, j, k)] - stencil_at(u, nx, ny, nz, ax, ay, az, i, j, k);
+        }
+        for (int l = 0; l < n; ++l) {
+            double acc = 0.0;
+            for (int m = 0; m < n; ++m)
+                acc += Ainv[(long)l * n + m] * rb[m];
+            db[l] = acc;
+        }
+        for (int l = 0; l < n; ++l)
+            u[box_cell(nx, ny, bx, by, bz, bi, bj, bk, l)] += omega * db[l];
+    }
+    free(rb);
+    free(seq);
 }
