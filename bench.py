@@ -259,16 +259,32 @@ def _rate(cells, sweeps, ms):
     return cells * sweeps / (ms / 1e3) / 1e9
 
 
-def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, math="auto"):
+def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, math="auto",
+                  box=(0, 0, 0)):
     """One 256^3 workload variant: steps x sweeps sweeps timed with CUDA events."""
     uv0, bv = _inputs(dt)
     uv, bv = uv0.cuda(), bv.cuda()
-    with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt, plane_math=math) as vc:
+    with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt, plane_math=math,
+                     box=box) as vc:
         vms = _time_sweeps(vc, uv, bv, steps, 1, sweeps, stream, barrier)
     es = 8 if dt == "f64" else 4
     rate = _rate(N ** 3, sweeps * steps, vms)
     out = {"workload": "grid256", "block": blk, "method": meth, "dtype": dt, "coeffs": a,
            "value": rate, "unit": UNIT, "hbm_frac": rate * 3 * es / peak}
+    if blk == "box":
+        # the dense block product: n multiply-adds per cell, n = bx by bz (Alg. 2 step 2)
+        nb = box[0] * box[1] * box[2]
+        out["box"] = list(box)
+        out["plane_math"] = math
+        out["tflops"] = rate * 2 * nb / 1e3
+        if math in ("tf32", "3xtf32"):
+            passes = 3 if math == "3xtf32" else 1
+            tf32_peak = _bf16_peak() / 2
+            out["tensor_tflops"] = out["tflops"] * passes
+            out["tensor_frac_of_tf32_peak"] = out["tensor_tflops"] / tf32_peak
+            out["tf32_peak_tflops"] = tf32_peak
+        if dt == "f64":
+            out["alu_frac_of_fp64_fma_peak"] = rate * nb / 626.9
     if blk == "plane":
         flops = 8.0 * N * N ** 3  # four n x n contractions per plane: 4 (nx + ny) per cell
         out["plane_math"] = math
@@ -451,6 +467,16 @@ VARIANTS = {
     "plane_jacobi_f32_simt": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 2, 10, "simt"),
     "plane_jacobi_f64": ("plane", "jacobi", "f64", (1.0, 1.0, 0.01), 1, 4, "auto"),
 }
+BOX_VARIANTS = {
+    # name: (method, dtype, box, steps, sweeps per step, math); a = (1, 1, 1)
+    "box_jacobi_f32_8cubed_3xtf32": ("jacobi", "f32", (8, 8, 8), 4, 10, "3xtf32"),
+    "box_gs_f32_8cubed_3xtf32": ("gs", "f32", (8, 8, 8), 4, 10, "3xtf32"),
+    "box_jacobi_f32_8cubed_tf32": ("jacobi", "f32", (8, 8, 8), 4, 10, "tf32"),
+    "box_jacobi_f32_8cubed_simt": ("jacobi", "f32", (8, 8, 8), 2, 5, "simt"),
+    "box_jacobi_f32_4cubed_3xtf32": ("jacobi", "f32", (4, 4, 4), 4, 10, "3xtf32"),
+    "box_gs_f64_8cubed": ("gs", "f64", (8, 8, 8), 1, 2, "auto"),
+    "box_gs_f64_4cubed": ("gs", "f64", (4, 4, 4), 1, 5, "auto"),
+}
 SPECIAL = ("batched600", "defect512", "adjoint")
 PROFILE_ONLY = ("batched600_graph",)
 
@@ -464,6 +490,12 @@ def _run_variant(name, brs, stream, barrier, peak, steps=None):
         return _variant_defect(brs, stream)
     if name == "adjoint":
         return _variant_adjoint(brs, stream)
+    if name in BOX_VARIANTS:
+        meth, dt, box, st, sw, math = BOX_VARIANTS[name]
+        out = _variant_grid(brs, stream, barrier, peak, "box", meth, dt, COEFFS, steps or st, sw,
+                            math, box)
+        out["name"] = name
+        return out
     blk, meth, dt, a, st, sw, math = VARIANTS[name]
     out = _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps or st, sw, math)
     out["name"] = name
@@ -472,7 +504,7 @@ def _run_variant(name, brs, stream, barrier, peak, steps=None):
 
 def _variants(brs, stream, barrier, peak):
     out = []
-    for name in list(VARIANTS) + list(SPECIAL):
+    for name in list(VARIANTS) + list(BOX_VARIANTS) + list(SPECIAL):
         try:
             out.append(_run_variant(name, brs, stream, barrier, peak))
         except Exception as exc:  # report, do not hide

@@ -12,7 +12,12 @@
  * One sweep (Sec. 2, Eq. blockiteration2):  u <- u + omega * M^{-1} (b - A u)
  * with M the block diagonal of A for full x-line blocks (M_line = tridiag(-ax,
  * 2(ax+ay+az), -ax), one block per (j,k)) or full xy-plane blocks (M_plane = ax Tx (x) I
- * + ay I (x) Ty + 2 az I, one block per k).  Every block is solved exactly.  Updates are
+ * + ay I (x) Ty + 2 az I, one block per k) or bx*by*bz boxes (the spatial blocks of
+ * Sec. 2 and Sec. 3: M_box = the stencil restricted to the box's cells, inverted once
+ * (Sec. 4.3) and applied as a dense product, Alg. 2 step 2).  Every block is solved
+ * exactly.  Box-block Gauss-Seidel visits the boxes in two colours (bi+bj+bk even, then
+ * odd): each colour reads the other colour's newest values, one admissible order of
+ * the chaotic scheme, and the result is deterministic.  Updates are
  * damped block Jacobi (Sec. 2, Alg. 2: new values into a second buffer, then swap) or
  * chaotic block Gauss-Seidel (Sec. 2, Alg. 1: in place, blocks processed concurrently
  * with no ordering; a block may read its neighbours' old or new values).
@@ -48,6 +53,7 @@ extern "C" {
 /* Block shape: full x-lines or full xy-planes (Sec. 2, block partition of A). */
 #define BRS_XLINE 0
 #define BRS_XYPLANE 1
+#define BRS_BOX 2 /* bx*by*bz spatial blocks with one precomputed inverse (Sec. 2, Sec. 4.3) */
 
 /* Update scheme between blocks. */
 #define BRS_JACOBI 0     /* damped block Jacobi, paper default omega = 0.8 (Sec. 2.1) */
@@ -68,11 +74,14 @@ typedef struct brs_ctx brs_ctx; /* opaque; owned by the library */
 typedef struct brs_params {
     int nx, ny, nz;     /* interior cells per axis, each >= 1 */
     double ax, ay, az;  /* stencil coefficients, each > 0 and finite */
-    int block;          /* BRS_XLINE or BRS_XYPLANE */
+    int block;          /* BRS_XLINE, BRS_XYPLANE or BRS_BOX */
     int method;         /* BRS_JACOBI or BRS_CHAOTIC_GS */
     int dtype;          /* BRS_F64 or BRS_F32 */
     double omega;       /* relaxation weight in (0, 2); <= 0 selects the paper default */
-    int plane_math;     /* BRS_PLANE_* (ignored for x-line blocks) */
+    int plane_math;     /* BRS_PLANE_*: arithmetic of the plane and box block solves
+                           (ignored for x-line blocks) */
+    int bx, by, bz;     /* BRS_BOX only: block dims, each >= 1 and dividing nx, ny, nz;
+                           bx*by*bz <= 512 (the paper's blocks run from 2x2x2 to 8x8x8) */
 } brs_params;
 
 /*
@@ -84,7 +93,12 @@ typedef struct brs_params {
  * brsmooth_destroy.  Errors: BRS_ERR_ARG (null pointer, dims < 1, non-positive or
  * non-finite coefficient, omega >= 2, unknown enum), BRS_ERR_UNSUPPORTED
  * (e.g. TF32 plane math with BRS_F64, or a grid beyond the implemented maxima:
- * x-lines nx <= 512; xy-planes nx, ny <= 1024), BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ * x-lines nx <= 512; xy-planes nx, ny <= 1024; boxes bx*by*bz <= 512, and TF32 box math
+ * needs bx*by*bz a multiple of 4 and >= 32), BRS_ERR_NOMEM, BRS_ERR_CUDA.
+ * Box blocks (BRS_BOX): bx, by, bz must divide nx, ny, nz (BRS_ERR_ARG otherwise; one
+ * inverse then serves every box, Sec. 4.3).  BRS_PLANE_AUTO selects FP64 CUDA-core math
+ * for BRS_F64 and, for BRS_F32, split-TF32 tensor cores when bx*by*bz is a multiple of 4
+ * and >= 32, else FP32 CUDA cores.
  */
 int brsmooth_create(const brs_params* p, brs_ctx** out);
 

@@ -24,12 +24,12 @@ BRS_ERR_NOMEM = -4
 BRS_ERR_TIMEOUT = -5
 BRS_ERR_BOUNDS = -6
 
-BRS_XLINE, BRS_XYPLANE = 0, 1
+BRS_XLINE, BRS_XYPLANE, BRS_BOX = 0, 1, 2
 BRS_JACOBI, BRS_CHAOTIC_GS = 0, 1
 BRS_F64, BRS_F32 = 0, 1
 BRS_PLANE_AUTO, BRS_PLANE_SIMT, BRS_PLANE_TF32, BRS_PLANE_3XTF32 = 0, 1, 2, 3
 
-BLOCKS = {"line": BRS_XLINE, "plane": BRS_XYPLANE}
+BLOCKS = {"line": BRS_XLINE, "plane": BRS_XYPLANE, "box": BRS_BOX}
 METHODS = {"jacobi": BRS_JACOBI, "gs": BRS_CHAOTIC_GS, "chaotic_gs": BRS_CHAOTIC_GS}
 DTYPES = {"f64": BRS_F64, "f32": BRS_F32}
 PLANE_MATH = {"auto": BRS_PLANE_AUTO, "simt": BRS_PLANE_SIMT, "tf32": BRS_PLANE_TF32,
@@ -49,7 +49,8 @@ class brs_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("ax", ctypes.c_double), ("ay", ctypes.c_double), ("az", ctypes.c_double),
                 ("block", ctypes.c_int), ("method", ctypes.c_int), ("dtype", ctypes.c_int),
-                ("omega", ctypes.c_double), ("plane_math", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("plane_math", ctypes.c_int),
+                ("bx", ctypes.c_int), ("by", ctypes.c_int), ("bz", ctypes.c_int)]
 
 
 _lib = None
@@ -197,11 +198,14 @@ class Context:
 
     def __init__(self, nx: int, ny: int, nz: int, a=(1.0, 1.0, 1.0), *, block: str = "line",
                  method: str = "jacobi", dtype: str = "f64", omega: float = 0.0,
-                 plane_math: str = "auto"):
+                 plane_math: str = "auto", box=(0, 0, 0)):
+        """block 'box' takes box=(bx, by, bz); plane_math also selects the box arithmetic."""
         self.shape = (nz, ny, nx)
         self.dtype_code = DTYPES[dtype]
+        bx, by, bz = (int(v) for v in box)
         self.p = brs_params(nx, ny, nz, float(a[0]), float(a[1]), float(a[2]), BLOCKS[block],
-                            METHODS[method], self.dtype_code, float(omega), PLANE_MATH[plane_math])
+                            METHODS[method], self.dtype_code, float(omega), PLANE_MATH[plane_math],
+                            bx, by, bz)
         rc, h = brsmooth_create(self.p)
         _check(rc, "brsmooth_create")
         self.h = h

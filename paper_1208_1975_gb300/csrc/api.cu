@@ -10,6 +10,7 @@
 
 #include "brs_internal.cuh"
 #include "batched.cuh"
+#include "box.cuh"
 #include "plane.cuh"
 
 namespace {
@@ -75,7 +76,10 @@ int validate(const brs_params* p)
         return BRS_ERR_ARG;
     if (!finite_pos(p->ax) || !finite_pos(p->ay) || !finite_pos(p->az))
         return BRS_ERR_ARG;
-    if (p->block != BRS_XLINE && p->block != BRS_XYPLANE)
+    if (p->block != BRS_XLINE && p->block != BRS_XYPLANE && p->block != BRS_BOX)
+        return BRS_ERR_ARG;
+    if (p->block == BRS_BOX &&
+        (p->bx < 1 || p->by < 1 || p->bz < 1 || p->nx % p->bx || p->ny % p->by || p->nz % p->bz))
         return BRS_ERR_ARG;
     if (p->method != BRS_JACOBI && p->method != BRS_CHAOTIC_GS)
         return BRS_ERR_ARG;
@@ -97,6 +101,7 @@ void free_ctx(brs_ctx* c)
         return;
     line_teardown(c);
     plane_teardown(c);
+    box_teardown(c);
     batched_teardown(c);
     adjoint_teardown(c);
     if (c->scratch)
@@ -206,8 +211,10 @@ int brsmooth_create(const brs_params* p, brs_ctx** out)
     *c->dev_status = 0;
     if (p->block == BRS_XLINE)
         rc = line_setup(c);
-    else
+    else if (p->block == BRS_XYPLANE)
         rc = plane_setup(c);
+    else
+        rc = box_setup(c);
     if (rc == BRS_OK)
         rc = residual_setup(c);
     if (rc == BRS_OK && p->method == BRS_JACOBI) {
@@ -233,7 +240,9 @@ static int sweep_one(brs_ctx* c, const void* uin, void* uout, const void* b, cud
 {
     if (c->p.block == BRS_XLINE)
         return line_sweep_launch(c, uin, uout, b, s);
-    return plane_sweep_launch(c, uin, uout, b, s);
+    if (c->p.block == BRS_XYPLANE)
+        return plane_sweep_launch(c, uin, uout, b, s);
+    return box_sweep_launch(c, uin, uout, b, s);
 }
 
 int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream)

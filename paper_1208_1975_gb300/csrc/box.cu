@@ -1,0 +1,477 @@
+// Box blocks: the grid is cut into bx*by*bz spatial blocks (Sec. 2; the block sizes of
+// Sec. 3), every block is solved with the one precomputed inverse Ahat_b of the diagonal
+// block (Sec. 4.3), applied as a dense product (Alg. 2 step 2).
+//
+// One sweep runs all blocks of a pass as one matrix product.  R holds one row per block:
+// its n = bx*by*bz right-hand sides rhs = b + N u (the gather form of the update, with N the
+// couplings that leave the block), local cells numbered x fastest.  Then D = R Ahat^T
+// (Ahat is symmetric, so both operands are K-major rows), and the epilogue writes
+//   u'[cell] = (1 - omega) u[cell] + omega D[block][l]
+// back into the grid.  Block Jacobi reads u and writes the second vector; block
+// Gauss-Seidel visits the blocks in two colours (bi+bj+bk even, then odd): blocks of one
+// colour share no face, so each colour is one product that reads the other colour's
+// newest values.
+//
+// Arithmetic: FP64 and FP32 on CUDA cores (a tiled SIMT product), or FP32 on the tensor
+// cores (tcgen05.mma kind::tf32, single TF32 or split-TF32 hi*hi + hi*lo + lo*hi) through the
+// persistent product kernel of plane_tc.cuh with its EPI_BOX epilogue.
+#include <cmath>
+#include <vector>
+
+#include "box.cuh"
+#include "plane_tc.cuh"
+#include "tc_host.cuh"
+
+namespace {
+
+struct BoxState {
+    int bx = 1, by = 1, bz = 1, n = 1;
+    long long nbx = 1, nby = 1, nbz = 1, nblk = 1;
+    int math = BRS_PLANE_SIMT;   // SIMT, TF32 or 3XTF32
+    int split = 0;               // tensor path: 1 or 3
+    int bn = 32;                 // tensor path: tile N
+    int sms = 1;
+    void* inv = nullptr;         // SIMT: Ahat in the context dtype, [n][n]
+    void* inv_lo = nullptr;      // tensor path: inv = TF32 hi part, inv_lo = lo part
+    void* R = nullptr;           // [nblk][n]: context dtype (SIMT) or TF32 hi (tensor)
+    void* R_lo = nullptr;
+    long long* rows = nullptr;   // packed block coordinates of each R row, in pass order
+    long long cnt[2] = {0, 0};   // rows per pass (Jacobi: one pass of nblk)
+    int* loc = nullptr;          // local cell l -> lx | ly << 10 | lz << 20
+    int* off = nullptr;          // local cell l -> lx + nx (ly + ny lz)
+    CUtensorMap mR_hi, mR_lo, mA_hi, mA_lo;
+};
+
+BoxState* bs(brs_ctx* c) { return static_cast<BoxState*>(c->box); }
+
+// rhs of one block row: b + ax/ay/az times the neighbours that lie outside the block and
+// inside the grid (zero Dirichlet values outside).  SPLIT 0: store in T; 1: TF32 hi only;
+// 3: TF32 hi and lo.
+template <typename T, int SPLIT>
+__global__ void __launch_bounds__(256) box_gather_kernel(
+    const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ rhi, float* __restrict__ rlo,
+    const long long* __restrict__ rows, const int* __restrict__ loc, long long cnt, int n, int bx,
+    int by, int bz, int nx, int ny, int nz, T ax, T ay, T az)
+{
+    const long long total = cnt * n;
+    const long long plane = (long long)nx * ny;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long q = t / n;
+        const int l = (int)(t - q * n);
+        const long long pk = __ldg(rows + q);
+        const int lc = __ldg(loc + l);
+        const int lx = lc & 1023, ly = (lc >> 10) & 1023, lz = lc >> 20;
+        const int i = (int)(pk & 0x1FFFFF) * bx + lx;
+        const int j = (int)((pk >> 21) & 0x1FFFFF) * by + ly;
+        const int k = (int)(pk >> 42) * bz + lz;
+        const long long cell = i + (long long)nx * j + plane * k;
+        T sx = T(0), sy = T(0), sz = T(0);
+        if (lx == 0 && i > 0)
+            sx += u[cell - 1];
+        if (lx == bx - 1 && i + 1 < nx)
+            sx += u[cell + 1];
+        if (ly == 0 && j > 0)
+            sy += u[cell - nx];
+        if (ly == by - 1 && j + 1 < ny)
+            sy += u[cell + nx];
+        if (lz == 0 && k > 0)
+            sz += u[cell - plane];
+        if (lz == bz - 1 && k + 1 < nz)
+            sz += u[cell + plane];
+        const T v = fma(az, sz, fma(ay, sy, fma(ax, sx, b[cell])));
+        if (SPLIT == 0) {
+            rhi[t] = v;
+        } else {
+            const uint32_t hb = brs_tc::tf32_rn((float)v);
+            rhi[t] = __uint_as_float(hb);
+            if (SPLIT == 3)
+                rlo[t] = __uint_as_float(brs_tc::tf32_rn((float)v - __uint_as_float(hb)));
+        }
+    }
+}
+
+// D = R Ahat^T on CUDA cores, fused with the update.  Tile 64 blocks x BN local cells,
+// K in steps of 16; thread (tx, ty) owns rows ty + 16 i (i < 4) and columns tx + 16 j.
+// Grid: x = row tiles, y = column tiles.
+template <typename T, int BN>
+__global__ void __launch_bounds__(256) box_gemm_simt(
+    const T* __restrict__ R, const T* __restrict__ Ainv, const T* u, T* uout,
+    const long long* __restrict__ rows, const int* __restrict__ off, long long M, int n, int bx,
+    int by, int bz, int nx, int ny, double omega)
+{
+    constexpr int BMS = 64, BKS = 16, TN = BN / 16;
+    __shared__ T As[BKS][BMS + 1];
+    __shared__ T Bs[BKS][BN + 1];
+    const long long m0 = (long long)blockIdx.x * BMS;
+    const int n0 = blockIdx.y * BN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+            acc[i][j] = T(0);
+    for (int k0 = 0; k0 < n; k0 += BKS) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = threadIdx.x + r * 256;
+            const int row = idx / BKS, kk = idx % BKS;
+            const long long gm = m0 + row;
+            const int gk = k0 + kk;
+            As[kk][row] = (gm < M && gk < n) ? R[gm * n + gk] : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < TN; ++r) {
+            const int idx = threadIdx.x + r * 256;
+            const int row = idx / BKS, kk = idx % BKS;
+            const int gl = n0 + row, gk = k0 + kk;
+            Bs[kk][row] = (gl < n && gk < n) ? Ainv[(long long)gl * n + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BKS; ++kk) {
+            T a[4], bv[TN];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const T om = (T)omega, om1 = (T)(1.0 - omega);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long m = m0 + ty + 16 * i;
+        if (m >= M)
+            continue;
+        const long long pk = rows[m];
+        const long long base = (pk & 0x1FFFFF) * bx +
+                               (long long)nx * (((pk >> 21) & 0x1FFFFF) * by + (long long)ny * (pk >> 42) * bz);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int l = n0 + tx + 16 * j;
+            if (l < n) {
+                const long long cell = base + off[l];
+                uout[cell] = fma(om, acc[i][j], om1 * u[cell]);
+            }
+        }
+    }
+}
+
+template <typename T, int BN>
+cudaError_t launch_simt(const BoxState* B, const T* R, const T* inv, const T* u, T* uout,
+                        const long long* rows, long long M, int nx, int ny, double omega,
+                        cudaStream_t s)
+{
+    const long long tm = (M + 63) / 64;
+    dim3 grid((unsigned)tm, (unsigned)((B->n + BN - 1) / BN));
+    box_gemm_simt<T, BN><<<grid, 256, 0, s>>>(R, inv, u, uout, rows, B->off, M, B->n, B->bx,
+                                              B->by, B->bz, nx, ny, omega);
+    return cudaGetLastError();
+}
+
+template <int SPLIT, int BN>
+const void* tc_kernel()
+{
+    return (const void*)brs_tc::tc_gemm_persistent<SPLIT, brs_tc::EPI_BOX, BN,
+                                                   brs_tc::pers_nst(SPLIT, BN)>;
+}
+
+const void* tc_kernel_for(int split, int bn)
+{
+    if (split == 3)
+        return bn == 128 ? tc_kernel<3, 128>() : bn == 64 ? tc_kernel<3, 64>() : tc_kernel<3, 32>();
+    return bn == 128 ? tc_kernel<1, 128>() : bn == 64 ? tc_kernel<1, 64>() : tc_kernel<1, 32>();
+}
+
+// One pass: gather the rows of `rows[0..M)` from uin, then the product and update into uout.
+template <typename T>
+int box_pass(brs_ctx* c, const T* uin, T* uout, const T* b, const long long* rows, long long M,
+             cudaStream_t s)
+{
+    BoxState* B = bs(c);
+    const brs_params& p = c->p;
+    if (M == 0)
+        return BRS_OK;
+    const long long total = M * B->n;
+    long long gblocks = (total + 255) / 256;
+    if (gblocks > (long long)B->sms * 16)
+        gblocks = (long long)B->sms * 16;
+    const T ax = (T)p.ax, ay = (T)p.ay, az = (T)p.az;
+    cudaError_t e = cudaSuccess;
+    if (B->split == 0) {
+        box_gather_kernel<T, 0><<<(unsigned)gblocks, 256, 0, s>>>(
+            uin, b, static_cast<T*>(B->R), nullptr, rows, B->loc, M, B->n, B->bx, B->by, B->bz,
+            p.nx, p.ny, p.nz, ax, ay, az);
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        const T* R = static_cast<const T*>(B->R);
+        const T* inv = static_cast<const T*>(B->inv);
+        if (B->n <= 16)
+            e = launch_simt<T, 16>(B, R, inv, uin, uout, rows, M, p.nx, p.ny, c->omega, s);
+        else if (B->n <= 32)
+            e = launch_simt<T, 32>(B, R, inv, uin, uout, rows, M, p.nx, p.ny, c->omega, s);
+        else
+            e = launch_simt<T, 64>(B, R, inv, uin, uout, rows, M, p.nx, p.ny, c->omega, s);
+        return brs_cuda_status(e);
+    }
+    if constexpr (sizeof(T) == 4) {
+        float* rhi = static_cast<float*>(B->R);
+        float* rlo = static_cast<float*>(B->R_lo);
+        if (B->split == 3)
+            box_gather_kernel<float, 3><<<(unsigned)gblocks, 256, 0, s>>>(
+                uin, b, rhi, rlo, rows, B->loc, M, B->n, B->bx, B->by, B->bz, p.nx, p.ny, p.nz,
+                ax, ay, az);
+        else
+            box_gather_kernel<float, 1><<<(unsigned)gblocks, 256, 0, s>>>(
+                uin, b, rhi, nullptr, rows, B->loc, M, B->n, B->bx, B->by, B->bz, p.nx, p.ny,
+                p.nz, ax, ay, az);
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        brs_tc::TcArgs g{};
+        g.M = (int)M;
+        g.N = B->n;
+        g.K = B->n;
+        g.u = uin;
+        g.uout = uout;
+        g.omega = (float)c->omega;
+        g.status = c->dev_status;
+        g.box_rows = rows;
+        g.box_off = B->off;
+        g.box_bx = B->bx;
+        g.box_by = B->by;
+        g.box_bz = B->bz;
+        g.box_nx = p.nx;
+        g.box_ny = p.ny;
+        g.box_vec4 = (B->bx % 4 == 0 && p.nx % 4 == 0) ? 1 : 0;
+        int tn = (B->n + B->bn - 1) / B->bn;
+        int tm = (int)((M + brs_tc::BM - 1) / brs_tc::BM);
+        int nb = 1;
+        const long long ntiles = (long long)tn * tm;
+        const int grid = (int)(ntiles < B->sms ? ntiles : B->sms);
+        CUtensorMap a0 = B->mR_hi, a1 = B->mR_lo, b0 = B->mA_hi, b1 = B->mA_lo;
+        void* args[] = {&a0, &a1, &b0, &b1, &g, &tn, &tm, &nb};
+        e = cudaLaunchKernel(tc_kernel_for(B->split, B->bn), dim3(grid), dim3(192), args,
+                             brs_tc::pers_smem(B->split, B->bn), s);
+        return brs_cuda_status(e);
+    }
+    return BRS_ERR_UNSUPPORTED;
+}
+
+// Ahat = A_b^{-1} in FP64 from the block's own sine basis: A_b (zero values outside the
+// block) is ax Tx + ay Ty + az Tz on the block, diagonal in the 3D DST-I of the block with
+// eigenvalues ax s_p + ay s_q + az s_r, s_p = 2 - 2 cos((p+1) pi / (b+1)).
+std::vector<double> block_inverse(int bx, int by, int bz, double ax, double ay, double az)
+{
+    auto basis = [](int m) {
+        std::vector<double> S((size_t)m * m);
+        const double sc = std::sqrt(2.0 / (m + 1));
+        for (int p = 0; p < m; ++p)
+            for (int i = 0; i < m; ++i)
+                S[(size_t)p * m + i] = sc * std::sin(M_PI * (p + 1) * (i + 1) / (m + 1));
+        return S;
+    };
+    auto eig = [](int m, int p) { return 2.0 - 2.0 * std::cos(M_PI * (p + 1) / (m + 1)); };
+    const int n = bx * by * bz;
+    const std::vector<double> Sx = basis(bx), Sy = basis(by), Sz = basis(bz);
+    std::vector<double> Q((size_t)n * n), lam(n);
+    for (int r = 0; r < bz; ++r)
+        for (int q = 0; q < by; ++q)
+            for (int p = 0; p < bx; ++p) {
+                const int kk = p + bx * (q + by * r);
+                lam[kk] = ax * eig(bx, p) + ay * eig(by, q) + az * eig(bz, r);
+                for (int l = 0; l < n; ++l) {
+                    const int lx = l % bx, ly = (l / bx) % by, lz = l / (bx * by);
+                    Q[(size_t)l * n + kk] = Sx[(size_t)p * bx + lx] * Sy[(size_t)q * by + ly] *
+                                            Sz[(size_t)r * bz + lz];
+                }
+            }
+    std::vector<double> inv((size_t)n * n, 0.0);
+    for (int l = 0; l < n; ++l)
+        for (int m = 0; m <= l; ++m) {
+            double s = 0.0;
+            for (int kk = 0; kk < n; ++kk)
+                s += Q[(size_t)l * n + kk] * Q[(size_t)m * n + kk] / lam[kk];
+            inv[(size_t)l * n + m] = s;
+            inv[(size_t)m * n + l] = s;
+        }
+    return inv;
+}
+
+template <typename T>
+int upload(void** dst, const std::vector<T>& v)
+{
+    cudaError_t e = cudaMalloc(dst, v.size() * sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return brs_cuda_status(e);
+}
+
+}  // namespace
+
+int box_setup(brs_ctx* c)
+{
+    const brs_params& p = c->p;
+    if (p.bx < 1 || p.by < 1 || p.bz < 1)
+        return BRS_ERR_ARG;
+    if (p.nx % p.bx || p.ny % p.by || p.nz % p.bz)
+        return BRS_ERR_ARG;
+    const int n = p.bx * p.by * p.bz;
+    if (n > 512 || p.bx > 512 || p.by > 512 || p.bz > 512)
+        return BRS_ERR_UNSUPPORTED;
+    BoxState* B = new (std::nothrow) BoxState();
+    if (!B)
+        return BRS_ERR_NOMEM;
+    c->box = B;
+    B->bx = p.bx;
+    B->by = p.by;
+    B->bz = p.bz;
+    B->n = n;
+    B->nbx = p.nx / p.bx;
+    B->nby = p.ny / p.by;
+    B->nbz = p.nz / p.bz;
+    B->nblk = B->nbx * B->nby * B->nbz;
+    if (B->nbx >= (1 << 21) || B->nby >= (1 << 21) || B->nbz >= (1 << 21) ||
+        (long long)p.nx * p.ny * p.bz >= (1ll << 31))
+        return BRS_ERR_UNSUPPORTED;
+    // arithmetic
+    int math = p.plane_math;
+    if (p.dtype == BRS_F64) {
+        if (math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32)
+            return BRS_ERR_UNSUPPORTED;
+        math = BRS_PLANE_SIMT;
+    } else if (math == BRS_PLANE_AUTO) {
+        math = (n % 4 == 0 && n >= 32) ? BRS_PLANE_3XTF32 : BRS_PLANE_SIMT;
+    } else if ((math == BRS_PLANE_TF32 || math == BRS_PLANE_3XTF32) && (n % 4 != 0 || n < 32)) {
+        // K-major rows of n FP32 must be 16-byte multiples and span one 32-value TMA box
+        return BRS_ERR_UNSUPPORTED;
+    }
+    B->math = math;
+    B->split = math == BRS_PLANE_3XTF32 ? 3 : math == BRS_PLANE_TF32 ? 1 : 0;
+    B->bn = n >= 128 ? 128 : n >= 64 ? 64 : 32;
+    cudaError_t e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    // the inverse, once (Sec. 4.3)
+    const std::vector<double> inv = block_inverse(p.bx, p.by, p.bz, p.ax, p.ay, p.az);
+    int rc = BRS_OK;
+    if (B->split) {
+        rc = brs_tc::upload_split(&B->inv, &B->inv_lo, inv);
+    } else if (p.dtype == BRS_F64) {
+        rc = upload(&B->inv, inv);
+    } else {
+        rc = upload(&B->inv, std::vector<float>(inv.begin(), inv.end()));
+    }
+    if (rc != BRS_OK)
+        return rc;
+    // row tables: lexicographic for Jacobi, colour 0 then colour 1 for Gauss-Seidel
+    std::vector<long long> rows;
+    rows.reserve((size_t)B->nblk);
+    auto pack = [](long long i, long long j, long long k) { return i | (j << 21) | (k << 42); };
+    if (p.method == BRS_JACOBI) {
+        for (long long k = 0; k < B->nbz; ++k)
+            for (long long j = 0; j < B->nby; ++j)
+                for (long long i = 0; i < B->nbx; ++i)
+                    rows.push_back(pack(i, j, k));
+        B->cnt[0] = B->nblk;
+    } else {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (long long k = 0; k < B->nbz; ++k)
+                for (long long j = 0; j < B->nby; ++j)
+                    for (long long i = 0; i < B->nbx; ++i)
+                        if (((i + j + k) & 1) == colour)
+                            rows.push_back(pack(i, j, k));
+            B->cnt[colour] = (long long)rows.size() - (colour ? B->cnt[0] : 0);
+        }
+    }
+    rc = upload(reinterpret_cast<void**>(&B->rows), rows);
+    std::vector<int> loc(n), off(n);
+    for (int l = 0; l < n; ++l) {
+        const int lx = l % p.bx, ly = (l / p.bx) % p.by, lz = l / (p.bx * p.by);
+        loc[l] = lx | (ly << 10) | (lz << 20);
+        off[l] = lx + p.nx * (ly + p.ny * lz);
+    }
+    if (rc == BRS_OK)
+        rc = upload(reinterpret_cast<void**>(&B->loc), loc);
+    if (rc == BRS_OK)
+        rc = upload(reinterpret_cast<void**>(&B->off), off);
+    if (rc != BRS_OK)
+        return rc;
+    // R buffers (rows of the largest pass)
+    const size_t relem = (size_t)B->nblk * n;
+    e = cudaMalloc(&B->R, relem * (B->split ? 4 : c->esize));
+    if (e == cudaSuccess && B->split == 3)
+        e = cudaMalloc(&B->R_lo, relem * 4);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    if (B->split) {
+        const int nrows = (int)B->nblk;
+        if (B->nblk >= (1ll << 31))
+            return BRS_ERR_UNSUPPORTED;
+        rc = brs_tc::encode_map(&B->mR_hi, B->R, n, nrows, 0, brs_tc::BM);
+        if (rc == BRS_OK)
+            rc = brs_tc::encode_map(&B->mR_lo, B->split == 3 ? B->R_lo : B->R, n, nrows, 0, brs_tc::BM);
+        if (rc == BRS_OK)
+            rc = brs_tc::encode_map(&B->mA_hi, B->inv, n, n, 0, B->bn);
+        if (rc == BRS_OK)
+            rc = brs_tc::encode_map(&B->mA_lo, B->split == 3 ? B->inv_lo : B->inv, n, n, 0, B->bn);
+        if (rc != BRS_OK)
+            return rc;
+        const void* k = tc_kernel_for(B->split, B->bn);
+        const size_t smem = brs_tc::pers_smem(B->split, B->bn);
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+    }
+    return BRS_OK;
+}
+
+void box_teardown(brs_ctx* c)
+{
+    BoxState* B = bs(c);
+    if (!B)
+        return;
+    void* bufs[] = {B->inv, B->inv_lo, B->R, B->R_lo, B->rows, B->loc, B->off};
+    for (void* q : bufs)
+        if (q)
+            cudaFree(q);
+    delete B;
+    c->box = nullptr;
+}
+
+int box_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s)
+{
+    BoxState* B = bs(c);
+    if (c->p.method == BRS_JACOBI) {
+        if (c->p.dtype == BRS_F64)
+            return box_pass<double>(c, static_cast<const double*>(uin), static_cast<double*>(uout),
+                                    static_cast<const double*>(b), B->rows, B->cnt[0], s);
+        return box_pass<float>(c, static_cast<const float*>(uin), static_cast<float*>(uout),
+                               static_cast<const float*>(b), B->rows, B->cnt[0], s);
+    }
+    // two colours, in place
+    int rc = BRS_OK;
+    for (int colour = 0; colour < 2 && rc == BRS_OK; ++colour) {
+        const long long* rows = B->rows + (colour ? B->cnt[0] : 0);
+        if (c->p.dtype == BRS_F64)
+            rc = box_pass<double>(c, static_cast<const double*>(uout), static_cast<double*>(uout),
+                                  static_cast<const double*>(b), rows, B->cnt[colour], s);
+        else
+            rc = box_pass<float>(c, static_cast<const float*>(uout), static_cast<float*>(uout),
+                                 static_cast<const float*>(b), rows, B->cnt[colour], s);
+    }
+    return rc;
+}

@@ -67,6 +67,8 @@ struct brs_ctx {
     std::vector<TmapEntry> tmaps;
     // plane path state (owned by plane.cu)
     void* plane = nullptr;
+    // box path state (owned by box.cu)
+    void* box = nullptr;
     // many-patch state (owned by batched.cu); non-null for batched contexts
     void* batch = nullptr;
     // defect-correction buffers of an FP32 inner context: residual and correction

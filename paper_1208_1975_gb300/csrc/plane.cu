@@ -29,6 +29,7 @@
 #include "line_impl.cuh"
 #include "plane.cuh"
 #include "plane_tc.cuh"
+#include "tc_host.cuh"
 #include "thomas_tables.h"
 
 namespace {
@@ -251,18 +252,8 @@ const void* tc_kernel_for(int bn, int nst)
     return tc_kernel<SPLIT, EPI, 128, 3>();
 }
 
-// Persistent products: ring stages per (split, tile N) so that the ring is about 192 KB.
-constexpr int pers_nst(int split, int bn)
-{
-    return split == 3 ? (bn == 128 ? 3 : 4) : (bn == 128 ? 6 : 8);
-}
-
-size_t pers_smem(int split, int bn)
-{
-    const int nst = pers_nst(split, bn);
-    const size_t stage = (size_t)(split == 3 ? 2 : 1) * (brs_tc::BM + bn) * brs_tc::BK * 4;
-    return 1024 + nst * stage + 4 * 32 * 33 * 4 + (2 * nst + 5) * 8 + 16;
-}
+using brs_tc::pers_nst;
+using brs_tc::pers_smem;
 
 template <int SPLIT, int EPI>
 const void* pers_kernel_for(int bn)
@@ -598,51 +589,8 @@ int upload(void** dst, const std::vector<double>& src)
     return brs_cuda_status(e);
 }
 
-// Round a value to TF32 (10 explicit mantissa bits), nearest with ties away from zero,
-// the rounding of cvt.rna.tf32.f32.
-float tf32_round(double x)
-{
-    float f = (float)x;
-    uint32_t b;
-    std::memcpy(&b, &f, 4);
-    b = (b + 0x1000u) & 0xFFFFE000u;
-    std::memcpy(&f, &b, 4);
-    return f;
-}
-
-int upload_split(void** hi, void** lo, const std::vector<double>& src)
-{
-    std::vector<float> h(src.size()), l(src.size());
-    for (size_t i = 0; i < src.size(); ++i) {
-        h[i] = tf32_round(src[i]);
-        l[i] = tf32_round(src[i] - (double)h[i]);
-    }
-    cudaError_t e = cudaMalloc(hi, h.size() * 4);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(*hi, h.data(), h.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMalloc(lo, l.size() * 4);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(*lo, l.data(), l.size() * 4, cudaMemcpyHostToDevice);
-    return brs_cuda_status(e);
-}
-
-PFN_encode_tiled g_encode_fn = nullptr;
-
-// FP32 map with the K axis innermost, box (32, rows[, 1]), 128-byte swizzle.
-int encode_map(CUtensorMap* m, const void* ptr, int kdim, int rows, int planes, int box_rows)
-{
-    cuuint64_t gdim[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)planes};
-    cuuint64_t gstr[2] = {(cuuint64_t)kdim * 4, (cuuint64_t)kdim * rows * 4};
-    cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
-    cuuint32_t es[3] = {1u, 1u, 1u};
-    const int rank = planes > 0 ? 3 : 2;
-    CUresult r = g_encode_fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(ptr),
-                             gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? BRS_OK : BRS_ERR_CUDA;
-}
+using brs_tc::encode_map;
+using brs_tc::upload_split;
 
 // Scan-Thomas tables of the y systems of every x-mode p:
 //   tridiag(-ay, ax s_p + 2 ay + 2 az, -ay) of size ny,  s_p = 2 - 2 cos((p+1) pi/(nx+1)).
@@ -690,8 +638,7 @@ int ythomas_setup(brs_ctx* c)
 int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double>& sy)
 {
     PlaneState* P = ps(c);
-    g_encode_fn = brs_encoder();
-    if (!g_encode_fn)
+    if (!brs_encoder())
         return BRS_ERR_CUDA;
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     int rc = upload_split(&P->sx, &P->sx_lo, sx);

@@ -22,7 +22,7 @@ namespace brs_tc {
 constexpr int BM = 128;  // MMA M (one TMEM lane per output row)
 constexpr int BK = 32;   // K per ring stage: 32 FP32 = one 128-byte swizzle row
 
-enum Epi { EPI_SPLIT = 0, EPI_SCALE_SPLIT = 1, EPI_UPDATE = 2 };
+enum Epi { EPI_SPLIT = 0, EPI_SCALE_SPLIT = 1, EPI_UPDATE = 2, EPI_BOX = 3 };
 
 struct TcArgs {
     int M, N, K;        // per-plane product sizes
@@ -37,6 +37,13 @@ struct TcArgs {
     float* uout;        // EPI_UPDATE: updated planes
     float omega;
     int* status;
+    // EPI_BOX (persistent kernel only): output row m is one box block whose packed block
+    // coordinates bi | bj << 21 | bk << 42 are box_rows[m]; column l is local cell l, at grid
+    // offset box_off[l] from the block's first cell.  u / uout are whole grids.
+    const long long* box_rows;
+    const int* box_off;
+    int box_bx, box_by, box_bz, box_nx, box_ny;
+    int box_vec4;  // bx and nx multiples of 4: 4 consecutive local cells are 16 aligned bytes
 };
 
 #ifdef __CUDACC__
@@ -327,6 +334,60 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// EPI_BOX epilogue of one accumulator tile, run by one warp for its 32 TMEM lanes: lane =
+// block (row m), each 32-column chunk = 32 consecutive local cells of that block.
+//   uout[cell] = (1 - omega) u[cell] + omega D[m][l]
+// Lanes are consecutive blocks, so a warp's stores cover whole runs of grid rows.
+template <int BN>
+__device__ __forceinline__ void box_epilogue(const TcArgs& g, uint32_t trow, int m, int n0)
+{
+    const bool mok = m < g.M;
+    long long base = 0;
+    if (mok) {
+        const long long pk = g.box_rows[m];
+        const long long bi = pk & 0x1FFFFF, bj = (pk >> 21) & 0x1FFFFF, bk = pk >> 42;
+        base = bi * g.box_bx + (long long)g.box_nx * (bj * g.box_by + (long long)g.box_ny * bk * g.box_bz);
+    }
+    const float om = g.omega, om1 = 1.0f - g.omega;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(trow + (uint32_t)(c * 32), r);
+        const int l0 = n0 + c * 32;
+        if (mok && g.box_vec4) {
+            long long cell[8];
+            float4 uo[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const int l = l0 + 4 * v;
+                cell[v] = l < g.N ? base + __ldg(g.box_off + l) : -1;
+                if (cell[v] >= 0)
+                    uo[v] = *reinterpret_cast<const float4*>(g.u + cell[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                if (cell[v] >= 0) {
+                    float4 o;
+                    o.x = fmaf(om, __uint_as_float(r[4 * v + 0]), om1 * uo[v].x);
+                    o.y = fmaf(om, __uint_as_float(r[4 * v + 1]), om1 * uo[v].y);
+                    o.z = fmaf(om, __uint_as_float(r[4 * v + 2]), om1 * uo[v].z);
+                    o.w = fmaf(om, __uint_as_float(r[4 * v + 3]), om1 * uo[v].w);
+                    *reinterpret_cast<float4*>(g.uout + cell[v]) = o;
+                }
+        } else if (mok) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int l = l0 + i;
+                if (l < g.N) {
+                    const long long cell = base + __ldg(g.box_off + l);
+                    g.uout[cell] = fmaf(om, __uint_as_float(r[i]), om1 * g.u[cell]);
+                }
+            }
+        }
+        __syncwarp();  // the next tcgen05.ld is warp-collective
+    }
+}
+
 // Persistent variant: one CTA per SM walks tiles t = blockIdx.x, +gridDim.x, ... of the
 // (n-tile, m-tile, plane) space.  Warp 0 streams K-blocks of every tile through the TMA
 // ring, warp 1 issues the MMAs into one of two TMEM accumulators, warps 2-5 drain the other
@@ -496,6 +557,9 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
             int m0, n0, plane;
             decode(t, &m0, &n0, &plane);
             const uint32_t trow = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
+            if constexpr (EPI == EPI_BOX) {
+                box_epilogue<BN>(g, trow, m0 + q * 32 + lane, n0);
+            } else {
             // EPI_UPDATE: the old values of the next 32-column chunk are loaded while the
             // current chunk is processed
             const int mrow0 = m0 + q * 32;
@@ -563,6 +627,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
                 }
                 __syncwarp();
             }
+            }  // EPI != EPI_BOX
             tc_fence_before();
             __syncwarp();
             if (lane == 0)

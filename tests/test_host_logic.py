@@ -69,8 +69,10 @@ def test_strerror_and_null_handling(cuda_lib):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(ny=-1), dict(nz=0), dict(ax=0.0), dict(ay=-1.0), dict(az=float("nan")),
-    dict(ax=float("inf")), dict(block=2), dict(method=5), dict(dtype=3), dict(omega=2.0),
-    dict(omega=float("nan")), dict(plane_math=9)])
+    dict(ax=float("inf")), dict(block=3), dict(method=5), dict(dtype=3), dict(omega=2.0),
+    dict(omega=float("nan")), dict(plane_math=9), dict(block=2),
+    dict(block=2, bx=2, by=2, bz=0), dict(block=2, bx=3, by=2, bz=2),
+    dict(block=2, bx=2, by=16, bz=2)])
 def test_create_rejects_bad_params_before_any_device_call(cuda_lib, bad):
     import paper_1208_1975_gb300 as brs
 
@@ -82,3 +84,28 @@ def test_create_rejects_bad_params_before_any_device_call(cuda_lib, bad):
     assert rc == brs.BRS_ERR_ARG and not h.value
     rc = cuda_lib.brsmooth_create(None, ctypes.byref(ctypes.c_void_p()))
     assert rc == brs.BRS_ERR_ARG
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of brs_params has the C header's size and field offsets."""
+    import shutil
+    import subprocess
+
+    import paper_1208_1975_gb300 as brs
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in brs.brs_params._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "brsmooth.h"',
+             'int main(void) {', '  printf("size %zu\\n", sizeof(brs_params));']
+    lines += [f'  printf("{f} %zu\\n", offsetof(brs_params, {f}));' for f in fields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(brs.brs_params)
+    for f in fields:
+        assert int(out[f]) == getattr(brs.brs_params, f).offset, f
