@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
                 T v = T(0);
                 if (y < ny) {
                     v = cin_hi[row + y];
-                    if (SPLIT == 3)
+                    if (SPLIT == 3 && cin_lo)
                         v += cin_lo[row + y];
                 }
                 r[q] = v;
@@ -478,15 +478,17 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
     g.kstep = kstep;
     g.plane = plane;
     g.status = c->dev_status;
-    // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]  -> t1
+    // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]  -> t1, plain FP32 (the y solve is not a
+    // tensor-core operand, so it needs no TF32 split)
     g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
-    g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo;
+    g.out_hi = (float*)P->t1; g.out_lo = nullptr; g.out_plain = 1;
     cudaError_t e = launch_tc<SPLIT, brs_tc::EPI_SPLIT>(P, P->m_sx_hi, P->m_sx_lo, P->m_R_hi,
                                                         P->m_R_lo, g, nbatch, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    // y-Thomas per x-mode: t1 [p][y] -> t2 [y][p]
-    e = launch_ythomas<float, SPLIT>(P, (const float*)P->t1, (const float*)P->t1_lo, (float*)P->t2,
+    g.out_plain = 0;
+    // y-Thomas per x-mode: t1 [p][y] -> t2 [y][p], split for P4
+    e = launch_ythomas<float, SPLIT>(P, (const float*)P->t1, nullptr, (float*)P->t2,
                                      (float*)P->t2_lo, nx, ny, k0, kstep, nbatch, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);

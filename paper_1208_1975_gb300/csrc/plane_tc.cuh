@@ -32,6 +32,7 @@ struct TcArgs {
     long long plane;    // elements per plane of the outputs (M * N)
     float* out_hi;      // EPI_SPLIT / EPI_SCALE_SPLIT outputs, [plane][M][N]
     float* out_lo;
+    int out_plain;      // EPI_SPLIT / EPI_SCALE_SPLIT: store the FP32 result in out_hi, unsplit
     const float* scale; // EPI_SCALE_SPLIT: [M][N]
     const float* u;     // EPI_UPDATE: old plane values [plane][M][N]
     float* uout;        // EPI_UPDATE: updated planes
@@ -298,6 +299,11 @@ __global__ void __launch_bounds__(128, 2) tc_gemm_kernel(
                     if (nok && mrow + i < g.M)
                         g.uout[obase + (long long)i * g.N] =
                             fmaf(g.omega, v[i], (1.0f - g.omega) * uo[i]);
+            } else if (g.out_plain) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (nok && mrow + i < g.M)
+                        g.out_hi[obase + (long long)i * g.N] = v[i];
             } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
@@ -614,6 +620,11 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
                         if (nok && mrow + i < g.M)
                             g.uout[obase + (long long)i * g.N] =
                                 fmaf(g.omega, v[i], (1.0f - g.omega) * ucur[i]);
+                } else if (g.out_plain) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nok && mrow + i < g.M)
+                            g.out_hi[obase + (long long)i * g.N] = v[i];
                 } else {
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
