@@ -37,58 +37,228 @@ struct BoxState {
     void* R_lo = nullptr;
     long long* rows = nullptr;   // packed block coordinates of each R row, in pass order
     long long cnt[2] = {0, 0};   // rows per pass (Jacobi: one pass of nblk)
-    int* loc = nullptr;          // local cell l -> lx | ly << 10 | lz << 20
     int* off = nullptr;          // local cell l -> lx + nx (ly + ny lz)
     CUtensorMap mR_hi, mR_lo, mA_hi, mA_lo;
 };
 
 BoxState* bs(brs_ctx* c) { return static_cast<BoxState*>(c->box); }
 
-// rhs of one block row: b + ax/ay/az times the neighbours that lie outside the block and
-// inside the grid (zero Dirichlet values outside).  SPLIT 0: store in T; 1: TF32 hi only;
-// 3: TF32 hi and lo.
-template <typename T, int SPLIT>
+// 16-byte vector of T (float4 / double2), and the 8-byte one for float.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+// W consecutive values at p, in 16-byte vectors where W and the element size allow it
+// (callers guarantee the matching alignment).
+template <typename T, int W>
+__device__ __forceinline__ void ld_vec(T (&v)[W], const T* p)
+{
+    using V = typename Vec16<T>::type;
+    constexpr int PER = (int)(16 / sizeof(T));
+    if constexpr (W % PER == 0) {
+#pragma unroll
+        for (int m = 0; m < W / PER; ++m)
+            reinterpret_cast<V*>(v)[m] = __ldg(reinterpret_cast<const V*>(p) + m);
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
+        *reinterpret_cast<float2*>(v) = __ldg(reinterpret_cast<const float2*>(p));
+    } else {
+#pragma unroll
+        for (int m = 0; m < W; ++m)
+            v[m] = p[m];
+    }
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void st_vec(T* p, const T (&v)[W])
+{
+    using V = typename Vec16<T>::type;
+    constexpr int PER = (int)(16 / sizeof(T));
+    if constexpr (W % PER == 0) {
+#pragma unroll
+        for (int m = 0; m < W / PER; ++m)
+            reinterpret_cast<V*>(p)[m] = reinterpret_cast<const V*>(v)[m];
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
+        *reinterpret_cast<float2*>(p) = *reinterpret_cast<const float2*>(v);
+    } else {
+#pragma unroll
+        for (int m = 0; m < W; ++m)
+            p[m] = v[m];
+    }
+}
+
+// One x-row r = ly + by lz of the block with packed coordinates pk into R row q.
+template <typename T, int SPLIT, int BX>
+__device__ __forceinline__ void box_gather_row(const T* __restrict__ u, const T* __restrict__ b,
+                                               T* __restrict__ rhi, float* __restrict__ rlo,
+                                               long long q, long long pk, int r, int n, int by,
+                                               int bz, int nx, int ny, int nz, long long plane,
+                                               T ax, T ay, T az)
+{
+    const int ly = r % by, lz = r / by;  // uniform per CTA
+    const int i0 = (int)(pk & 0x1FFFFF) * BX;
+    const int j = (int)((pk >> 21) & 0x1FFFFF) * by + ly;
+    const int k = (int)(pk >> 42) * bz + lz;
+    const long long cell = i0 + (long long)nx * j + plane * k;
+    T v[BX], t[BX];
+    ld_vec<T, BX>(v, b + cell);
+    if (ly == 0 && j > 0) {
+        ld_vec<T, BX>(t, u + cell - nx);
+#pragma unroll
+        for (int m = 0; m < BX; ++m)
+            v[m] = fma(ay, t[m], v[m]);
+    }
+    if (ly == by - 1 && j + 1 < ny) {
+        ld_vec<T, BX>(t, u + cell + nx);
+#pragma unroll
+        for (int m = 0; m < BX; ++m)
+            v[m] = fma(ay, t[m], v[m]);
+    }
+    if (lz == 0 && k > 0) {
+        ld_vec<T, BX>(t, u + cell - plane);
+#pragma unroll
+        for (int m = 0; m < BX; ++m)
+            v[m] = fma(az, t[m], v[m]);
+    }
+    if (lz == bz - 1 && k + 1 < nz) {
+        ld_vec<T, BX>(t, u + cell + plane);
+#pragma unroll
+        for (int m = 0; m < BX; ++m)
+            v[m] = fma(az, t[m], v[m]);
+    }
+    if (i0 > 0)
+        v[0] = fma(ax, u[cell - 1], v[0]);
+    if (i0 + BX < nx)
+        v[BX - 1] = fma(ax, u[cell + BX], v[BX - 1]);
+    const long long o = q * n + (long long)BX * r;
+    if constexpr (SPLIT == 0) {
+        st_vec<T, BX>(rhi + o, v);
+    } else {
+        float h[BX], l[BX];
+#pragma unroll
+        for (int m = 0; m < BX; ++m) {
+            const uint32_t hb = brs_tc::tf32_rn((float)v[m]);
+            h[m] = __uint_as_float(hb);
+            l[m] = __uint_as_float(brs_tc::tf32_rn((float)v[m] - h[m]));
+        }
+        st_vec<float, BX>(rhi + o, h);
+        if (SPLIT == 3)
+            st_vec<float, BX>(rlo + o, l);
+    }
+}
+
+
+// rhs of RPT consecutive x-rows of a block: b + ax/ay/az times the neighbours that lie
+// outside the block and inside the grid (zero Dirichlet values outside).  Thread = R row q
+// (one block); the CTA's row group gives the first row's index r = ly + by lz inside the
+// block, so adjacent threads read adjacent blocks' rows (one contiguous grid row per warp in the
+// Jacobi order) and write R[q][BX r .. BX (r + RPT)), at least one 32-byte sector.  BX is
+// the block's x size (a template for 1, 2, 4, 8).
+// SPLIT 0: store in T; 1: TF32 hi only; 3: TF32 hi and lo.
+template <typename T, int SPLIT, int BX, int RPT>
 __global__ void __launch_bounds__(256) box_gather_kernel(
     const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ rhi, float* __restrict__ rlo,
-    const long long* __restrict__ rows, const int* __restrict__ loc, long long cnt, int n, int bx,
-    int by, int bz, int nx, int ny, int nz, T ax, T ay, T az)
+    const long long* __restrict__ rows, long long cnt, int n, int by, int bz, int nx, int ny,
+    int nz, T ax, T ay, T az)
 {
-    const long long total = cnt * n;
+    // CTA order: the row groups of one set of 256 blocks are consecutive CTAs, so the grid
+    // is read once, front to back
+    const int groups = by * bz / RPT;
+    const unsigned qc = blockIdx.x / groups;
+    const int r0 = (int)(blockIdx.x - qc * groups) * RPT;
+    const long long q = (long long)qc * blockDim.x + threadIdx.x;
+    if (q >= cnt)
+        return;
+    const long long pk = __ldg(rows + q);
     const long long plane = (long long)nx * ny;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long q = t / n;
-        const int l = (int)(t - q * n);
-        const long long pk = __ldg(rows + q);
-        const int lc = __ldg(loc + l);
-        const int lx = lc & 1023, ly = (lc >> 10) & 1023, lz = lc >> 20;
-        const int i = (int)(pk & 0x1FFFFF) * bx + lx;
-        const int j = (int)((pk >> 21) & 0x1FFFFF) * by + ly;
-        const int k = (int)(pk >> 42) * bz + lz;
-        const long long cell = i + (long long)nx * j + plane * k;
-        T sx = T(0), sy = T(0), sz = T(0);
-        if (lx == 0 && i > 0)
-            sx += u[cell - 1];
-        if (lx == bx - 1 && i + 1 < nx)
-            sx += u[cell + 1];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr)
+        box_gather_row<T, SPLIT, BX>(u, b, rhi, rlo, q, pk, r0 + rr, n, by, bz, nx, ny, nz, plane,
+                                     ax, ay, az);
+}
+
+// The same for any bx (one cell per loop step, scalar accesses).
+template <typename T, int SPLIT>
+__global__ void __launch_bounds__(256) box_gather_any_kernel(
+    const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ rhi, float* __restrict__ rlo,
+    const long long* __restrict__ rows, long long cnt, int n, int bx, int by, int bz, int nx,
+    int ny, int nz, T ax, T ay, T az)
+{
+    const int groups = by * bz;
+    const unsigned qc = blockIdx.x / groups;
+    const int r = (int)(blockIdx.x - qc * groups);
+    const long long q = (long long)qc * blockDim.x + threadIdx.x;
+    if (q >= cnt)
+        return;
+    const int ly = r % by, lz = r / by;
+    const long long plane = (long long)nx * ny;
+    const long long pk = __ldg(rows + q);
+    const int i0 = (int)(pk & 0x1FFFFF) * bx;
+    const int j = (int)((pk >> 21) & 0x1FFFFF) * by + ly;
+    const int k = (int)(pk >> 42) * bz + lz;
+    const long long cell0 = i0 + (long long)nx * j + plane * k;
+    const long long o = q * n + (long long)bx * r;
+    for (int lx = 0; lx < bx; ++lx) {
+        const long long cell = cell0 + lx;
+        T v = b[cell];
         if (ly == 0 && j > 0)
-            sy += u[cell - nx];
+            v = fma(ay, u[cell - nx], v);
         if (ly == by - 1 && j + 1 < ny)
-            sy += u[cell + nx];
+            v = fma(ay, u[cell + nx], v);
         if (lz == 0 && k > 0)
-            sz += u[cell - plane];
+            v = fma(az, u[cell - plane], v);
         if (lz == bz - 1 && k + 1 < nz)
-            sz += u[cell + plane];
-        const T v = fma(az, sz, fma(ay, sy, fma(ax, sx, b[cell])));
-        if (SPLIT == 0) {
-            rhi[t] = v;
+            v = fma(az, u[cell + plane], v);
+        if (lx == 0 && i0 > 0)
+            v = fma(ax, u[cell - 1], v);
+        if (lx == bx - 1 && i0 + bx < nx)
+            v = fma(ax, u[cell + 1], v);
+        if constexpr (SPLIT == 0) {
+            rhi[o + lx] = v;
         } else {
             const uint32_t hb = brs_tc::tf32_rn((float)v);
-            rhi[t] = __uint_as_float(hb);
+            rhi[o + lx] = __uint_as_float(hb);
             if (SPLIT == 3)
-                rlo[t] = __uint_as_float(brs_tc::tf32_rn((float)v - __uint_as_float(hb)));
+                rlo[o + lx] = __uint_as_float(brs_tc::tf32_rn((float)v - __uint_as_float(hb)));
         }
     }
+}
+
+template <typename T, int SPLIT>
+cudaError_t launch_gather(const BoxState* B, const brs_params& p, const T* u, const T* b, T* rhi,
+                          float* rlo, const long long* rows, long long M, cudaStream_t s)
+{
+    const dim3 grid((unsigned)(((M + 255) / 256) * (B->by * B->bz)));
+    const T ax = (T)p.ax, ay = (T)p.ay, az = (T)p.az;
+    // the vector paths need the row start aligned to the vector: bx | nx makes every row
+    // start a multiple of bx
+    // rows per thread: enough for 32 bytes of R per store, dividing the block's row count
+    const int rows_in_block = B->by * B->bz;
+    int want = (int)(32 / (B->bx * sizeof(T)));
+    int rpt = 1;
+    while (rpt * 2 <= want && rows_in_block % (rpt * 2) == 0)
+        rpt *= 2;
+#define BRS_BOX_GATHER(BXV, RPTV)                                                            \
+    if (B->bx == BXV && rpt == RPTV) {                                                       \
+        const dim3 g2((unsigned)(((M + 255) / 256) * (rows_in_block / RPTV)));              \
+        box_gather_kernel<T, SPLIT, BXV, RPTV><<<g2, 256, 0, s>>>(                            \
+            u, b, rhi, rlo, rows, M, B->n, B->by, B->bz, p.nx, p.ny, p.nz, ax, ay, az);       \
+        return cudaGetLastError();                                                           \
+    }
+    BRS_BOX_GATHER(1, 1)
+    BRS_BOX_GATHER(1, 2)
+    BRS_BOX_GATHER(1, 4)
+    BRS_BOX_GATHER(1, 8)
+    BRS_BOX_GATHER(2, 1)
+    BRS_BOX_GATHER(2, 2)
+    BRS_BOX_GATHER(2, 4)
+    BRS_BOX_GATHER(4, 1)
+    BRS_BOX_GATHER(4, 2)
+    BRS_BOX_GATHER(8, 1)
+#undef BRS_BOX_GATHER
+    box_gather_any_kernel<T, SPLIT><<<grid, 256, 0, s>>>(u, b, rhi, rlo, rows, M, B->n, B->bx,
+                                                         B->by, B->bz, p.nx, p.ny, p.nz, ax, ay,
+                                                         az);
+    return cudaGetLastError();
 }
 
 // D = R Ahat^T on CUDA cores, fused with the update.  Tile 64 blocks x BN local cells,
@@ -201,17 +371,9 @@ int box_pass(brs_ctx* c, const T* uin, T* uout, const T* b, const long long* row
     const brs_params& p = c->p;
     if (M == 0)
         return BRS_OK;
-    const long long total = M * B->n;
-    long long gblocks = (total + 255) / 256;
-    if (gblocks > (long long)B->sms * 16)
-        gblocks = (long long)B->sms * 16;
-    const T ax = (T)p.ax, ay = (T)p.ay, az = (T)p.az;
     cudaError_t e = cudaSuccess;
     if (B->split == 0) {
-        box_gather_kernel<T, 0><<<(unsigned)gblocks, 256, 0, s>>>(
-            uin, b, static_cast<T*>(B->R), nullptr, rows, B->loc, M, B->n, B->bx, B->by, B->bz,
-            p.nx, p.ny, p.nz, ax, ay, az);
-        e = cudaGetLastError();
+        e = launch_gather<T, 0>(B, p, uin, b, static_cast<T*>(B->R), nullptr, rows, M, s);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
         const T* R = static_cast<const T*>(B->R);
@@ -228,14 +390,9 @@ int box_pass(brs_ctx* c, const T* uin, T* uout, const T* b, const long long* row
         float* rhi = static_cast<float*>(B->R);
         float* rlo = static_cast<float*>(B->R_lo);
         if (B->split == 3)
-            box_gather_kernel<float, 3><<<(unsigned)gblocks, 256, 0, s>>>(
-                uin, b, rhi, rlo, rows, B->loc, M, B->n, B->bx, B->by, B->bz, p.nx, p.ny, p.nz,
-                ax, ay, az);
+            e = launch_gather<float, 3>(B, p, uin, b, rhi, rlo, rows, M, s);
         else
-            box_gather_kernel<float, 1><<<(unsigned)gblocks, 256, 0, s>>>(
-                uin, b, rhi, nullptr, rows, B->loc, M, B->n, B->bx, B->by, B->bz, p.nx, p.ny,
-                p.nz, ax, ay, az);
-        e = cudaGetLastError();
+            e = launch_gather<float, 1>(B, p, uin, b, rhi, nullptr, rows, M, s);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
         brs_tc::TcArgs g{};
@@ -342,8 +499,9 @@ int box_setup(brs_ctx* c)
     B->nbz = p.nz / p.bz;
     B->nblk = B->nbx * B->nby * B->nbz;
     if (B->nbx >= (1 << 21) || B->nby >= (1 << 21) || B->nbz >= (1 << 21) ||
-        (long long)p.nx * p.ny * p.bz >= (1ll << 31))
-        return BRS_ERR_UNSUPPORTED;
+        (long long)p.nx * p.ny * p.bz >= (1ll << 31) ||
+        (B->nblk + 255) / 256 * (long long)(p.by * p.bz) >= (1ll << 31))
+        return BRS_ERR_UNSUPPORTED;  // packed block coordinates, int offsets, gather grid
     // arithmetic
     int math = p.plane_math;
     if (p.dtype == BRS_F64) {
@@ -395,14 +553,11 @@ int box_setup(brs_ctx* c)
         }
     }
     rc = upload(reinterpret_cast<void**>(&B->rows), rows);
-    std::vector<int> loc(n), off(n);
+    std::vector<int> off(n);
     for (int l = 0; l < n; ++l) {
         const int lx = l % p.bx, ly = (l / p.bx) % p.by, lz = l / (p.bx * p.by);
-        loc[l] = lx | (ly << 10) | (lz << 20);
         off[l] = lx + p.nx * (ly + p.ny * lz);
     }
-    if (rc == BRS_OK)
-        rc = upload(reinterpret_cast<void**>(&B->loc), loc);
     if (rc == BRS_OK)
         rc = upload(reinterpret_cast<void**>(&B->off), off);
     if (rc != BRS_OK)
@@ -444,7 +599,7 @@ void box_teardown(brs_ctx* c)
     BoxState* B = bs(c);
     if (!B)
         return;
-    void* bufs[] = {B->inv, B->inv_lo, B->R, B->R_lo, B->rows, B->loc, B->off};
+    void* bufs[] = {B->inv, B->inv_lo, B->R, B->R_lo, B->rows, B->off};
     for (void* q : bufs)
         if (q)
             cudaFree(q);
