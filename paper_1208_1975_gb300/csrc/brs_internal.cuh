@@ -23,6 +23,7 @@ struct LineCfg {
     bool tma = false;   // TMA ring path (rows 16-byte aligned) or the plain-load path
     int grid = 0;       // persistent CTAs (TMA path)
     size_t smem = 0;    // dynamic shared memory bytes (TMA path)
+    bool pdl = true;    // launch each sweep as a programmatic dependent of the previous one
 };
 
 // Arguments of the line kernels (passed by value).

@@ -141,6 +141,7 @@ int line_setup(brs_ctx* c)
         const long long total = nj * p.nz;
         if (L.grid > total)
             L.grid = (int)total;
+        L.pdl = env_int("BRSMOOTH_LINE_PDL", 1) != 0;
     }
     c->lcfg = L;
 
@@ -207,7 +208,17 @@ int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cu
         void* out = uout;
         const void* tab = c->line_tab;
         void* args[] = {&tu, &tbm, &out, (void*)&tab, &a};
-        e = cudaLaunchKernel(ktma, dim3(L.grid), dim3(L.JT * L.G), args, L.smem, s);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(L.grid);
+        cfg.blockDim = dim3(L.JT * L.G);
+        cfg.dynamicSmemBytes = L.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = L.pdl ? 1 : 0;
+        e = cudaLaunchKernelExC(&cfg, ktma, args);
     } else {
         const int groups = 256 / L.G;
         const long long nlines = (long long)p.ny * p.nz;
