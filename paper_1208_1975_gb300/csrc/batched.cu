@@ -59,6 +59,8 @@ struct BatchState {
     std::vector<int> h_item_patch;
     cudaStream_t cap = nullptr; // private capture stream
     std::vector<Graph> graphs;
+    bool async = false;         // cp.async kernel (every patch row is 16-byte aligned)
+    int stages = 4;             // its ring depth (z-steps of lookahead per warp)
 };
 
 BatchState* bs(brs_ctx* c)
@@ -67,6 +69,11 @@ BatchState* bs(brs_ctx* c)
 }
 
 constexpr int kE = 4;
+// bytes of one warp's cp.async ring: stages x 4 fields x 32 lanes x kE elements
+constexpr size_t async_ring_bytes(int stages, size_t esize)
+{
+    return (size_t)stages * 4 * 32 * kE * esize;
+}
 
 template <typename T, int G, bool GS>
 __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc, int KC,
@@ -175,6 +182,172 @@ __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc,
     }
 }
 
+// 16-byte asynchronous copy global -> shared (per thread); src_bytes = 0 writes zeros
+// without reading global memory (rows and planes outside the patch).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Same work item as batched_item, with the per-step inputs (u(k+1), b(k) and, for the
+// lines at the y-block edges, the halo lines j-1 / j+1 of plane k) staged by cp.async
+// through a per-warp ring of D steps in shared memory.  Every patch row is a
+// multiple of 16 bytes (checked on the host).  Each lane copies and reads back only its
+// own 16-byte pieces, so no cross-lane synchronisation is needed.
+template <typename T, int G, bool GS, int D>
+__device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, int kc, int KC,
+                                                   const T* uin, T* uout,
+                                                   const T* __restrict__ b,
+                                                   const T* __restrict__ tab, T ay, T az, T om1,
+                                                   unsigned char* ring)
+{
+    constexpr int R = 32 / G;
+    constexpr int CH = (int)(kE * sizeof(T) / 16);  // 16-byte chunks per lane and field
+    const int lanew = threadIdx.x & 31;
+    const int g = lanew / G, l = lanew % G;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const int j = jb * R + g;
+    const bool jin = j < ny;
+    const int x0 = l * kE;
+    const bool xin = x0 < nx;
+    const long long plane = (long long)nx * ny;
+    const T* ub = uin + d.off;
+    T* uo = uout + d.off;
+    const T* bb = b + d.off;
+    brs::LineTables<T, kE, G> tb;
+    tb.load(tab + d.tab, l);
+    const int k0 = kc * KC;
+    const int k1 = min(nz, k0 + KC);
+    const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(ring);
+    // byte offset of (slot, field, chunk) for this lane
+    auto soff = [&](int slot, int f, int c) -> uint32_t {
+        return (uint32_t)((((slot * 4 + f) * CH + c) * 32 + lanew) * 16);
+    };
+    auto copy_line = [&](int slot, int f, const T* src, int jj, int kk) {
+        const bool in = xin && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+        const T* p = in ? src + (long long)kk * plane + (long long)jj * nx + x0 : src;
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+            cp_async16(ring0 + soff(slot, f, c), p + c * (16 / sizeof(T)), in ? 16u : 0u);
+    };
+    auto issue = [&](int kk, int slot) {
+        copy_line(slot, 0, ub, j, kk + 1);
+        copy_line(slot, 1, bb, j, kk);
+        if (g == 0)
+            copy_line(slot, 2, ub, j - 1, kk);
+        if (g == R - 1)
+            copy_line(slot, 3, ub, j + 1, kk);
+    };
+    auto read = [&](int slot, int f, T (&v)[kE]) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+            reinterpret_cast<float4*>(v)[c] =
+                *reinterpret_cast<const float4*>(ring + soff(slot, f, c));
+    };
+    auto ld = [&](const T* src, int jj, int kk, T (&v)[kE]) {
+        if (xin && jj >= 0 && jj < ny && kk >= 0 && kk < nz) {
+            const T* p = src + (long long)kk * plane + (long long)jj * nx + x0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                reinterpret_cast<float4*>(v)[c] = reinterpret_cast<const float4*>(p)[c];
+        } else {
+#pragma unroll
+            for (int q = 0; q < kE; ++q)
+                v[q] = T(0);
+        }
+    };
+
+    T um[kE], uc[kE], up[kE], r[kE], bv[kE], un[kE], us[kE], hn[kE], hs[kE];
+    ld(ub, j, k0 - 1, um);
+    ld(ub, j, k0, uc);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        if (k0 + i < k1)
+            issue(k0 + i, i);
+        cp_async_commit();
+    }
+    int slot = 0;
+    for (int k = k0; k < k1; ++k) {
+        cp_async_wait<D - 1>();  // the group of step k (committed D groups ago) is complete
+        read(slot, 0, up);
+        read(slot, 1, bv);
+        if (g == 0)
+            read(slot, 2, hn);
+        if (g == R - 1)
+            read(slot, 3, hs);
+#pragma unroll
+        for (int q = 0; q < kE; ++q) {
+            T a = __shfl_up_sync(0xffffffffu, uc[q], G);
+            T c = __shfl_down_sync(0xffffffffu, uc[q], G);
+            un[q] = (g == 0) ? hn[q] : a;
+            us[q] = (g == R - 1) ? hs[q] : c;
+        }
+#pragma unroll
+        for (int q = 0; q < kE; ++q)
+            r[q] = (xin && jin) ? fma(az, um[q] + up[q], fma(ay, un[q] + us[q], bv[q])) : T(0);
+        brs::line_solve<T, kE, G>(r, tb, l);
+        T v[kE];
+#pragma unroll
+        for (int q = 0; q < kE; ++q)
+            v[q] = fma(tb.wp[q], r[q], om1 * uc[q]);
+        if (xin && jin) {
+            T* p = uo + (long long)k * plane + (long long)j * nx + x0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                reinterpret_cast<float4*>(p)[c] = reinterpret_cast<const float4*>(v)[c];
+        }
+#pragma unroll
+        for (int q = 0; q < kE; ++q) {
+            um[q] = GS ? ((xin && jin) ? v[q] : T(0)) : uc[q];
+            uc[q] = up[q];
+        }
+        // refill the slot just read (its values have been consumed above)
+        if (k + D < k1)
+            issue(k + D, slot);
+        cp_async_commit();
+        slot = slot + 1 == D ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();  // only empty groups remain; the ring is free for the next item
+    __syncwarp();
+}
+
+template <typename T, bool GS, int D>
+__global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __restrict__ desc,
+                                                            const int* __restrict__ item_patch,
+                                                            int nitems, int* counter, int KC,
+                                                            const T* uin, T* uout,
+                                                            const T* __restrict__ b,
+                                                            const T* __restrict__ tab,
+                                                            double ay, double az, double om1)
+{
+    extern __shared__ __align__(16) unsigned char async_smem[];
+    const int lanew = threadIdx.x & 31;
+    unsigned char* ring =
+        async_smem + (size_t)(threadIdx.x >> 5) * async_ring_bytes(D, sizeof(T));
+    while (true) {
+        int item = 0;
+        if (lanew == 0)
+            item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems)
+            return;
+        const PatchDesc d = desc[item_patch[item]];
+        const int local = item - d.item0;
+        const int jb = local % d.njb, kc = local / d.njb;
+        switch (d.cls) {
+        case 0: batched_item_async<T, 4, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
+        case 1: batched_item_async<T, 8, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
+        case 2: batched_item_async<T, 16, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
+        default: batched_item_async<T, 32, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
+        }
+    }
+}
+
 template <typename T, bool GS>
 __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __restrict__ desc,
                                                            const int* __restrict__ item_patch,
@@ -202,6 +375,19 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
         default: batched_item<T, 32, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
         }
     }
+}
+
+// FP32 only (the FP64 item does not fit the register budget with its ring addressing)
+const void* async_kernel_for(bool gs, int stages)
+{
+    if (stages >= 8)
+        return gs ? (const void*)batched_async_kernel<float, true, 8>
+                  : (const void*)batched_async_kernel<float, false, 8>;
+    if (stages >= 6)
+        return gs ? (const void*)batched_async_kernel<float, true, 6>
+                  : (const void*)batched_async_kernel<float, false, 6>;
+    return gs ? (const void*)batched_async_kernel<float, true, 4>
+              : (const void*)batched_async_kernel<float, false, 4>;
 }
 
 const void* kernel_for(int dtype, bool gs)
@@ -275,7 +461,9 @@ int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* coun
                cudaStream_t s)
 {
     BatchState* B = bs(c);
-    const void* k = kernel_for(c->p.dtype, c->p.method == BRS_CHAOTIC_GS);
+    const bool gs = c->p.method == BRS_CHAOTIC_GS;
+    const void* k = B->async ? async_kernel_for(gs, B->stages) : kernel_for(c->p.dtype, gs);
+    const size_t smem = B->async ? (size_t)B->warps * async_ring_bytes(B->stages, c->esize) : 0;
     const PatchDesc* desc = B->d_desc;
     const int* ip = B->d_item_patch;
     int nitems = B->nitems, KC = B->KC;
@@ -284,7 +472,7 @@ int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* coun
     void* args[] = {(void*)&desc, (void*)&ip, &nitems, &counter, &KC, (void*)&uin, &uout,
                     (void*)&b, (void*)&tab, &ay, &az, &om1};
     return brs_cuda_status(
-        cudaLaunchKernel(k, dim3(B->grid), dim3(B->warps * 32), args, 0, s));
+        cudaLaunchKernel(k, dim3(B->grid), dim3(B->warps * 32), args, smem, s));
 }
 
 // Enqueue one call's sweeps (counter reset + one launch per sweep) on stream s.
@@ -362,6 +550,10 @@ int autotune(brs_ctx* c)
             for (int cps : {2, 4, 8}) {
                 if (w * cps > 64)
                     continue;
+                if (B->async &&
+                    ((size_t)w * cps * async_ring_bytes(B->stages, c->esize) > 220u * 1024u ||
+                     (size_t)w * async_ring_bytes(B->stages, c->esize) > 227u * 1024u))
+                    continue;  // the rings of every resident warp must fit one SM
                 if (fixed_kc && kc != fixed_kc)
                     continue;
                 cands.push_back({kc, w, cps});
@@ -480,9 +672,26 @@ int batched_setup(brs_ctx* c, int npatch, const int* dims)
         if (e != cudaSuccess)
             return brs_cuda_status(e);
     }
+    // cp.async kernel when every patch row is a whole number of aligned 16-byte pieces
+    B->async = c->p.dtype == BRS_F32 && env_int("BRSMOOTH_BATCH_ASYNC", 1) != 0;
+    for (const PatchDesc& d : B->h_desc)
+        B->async = B->async && d.vec;
+    B->stages = env_int("BRSMOOTH_BATCH_STAGES", 4);
+    B->stages = B->stages >= 8 ? 8 : B->stages >= 6 ? 6 : 4;
+    if (B->async) {
+        const size_t want =
+            std::min<size_t>(227u * 1024u, 16 * async_ring_bytes(B->stages, c->esize));
+        const void* k = async_kernel_for(c->p.method == BRS_CHAOTIC_GS, B->stages);
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < want)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+    }
     const int kc = env_int("BRSMOOTH_BATCH_KC", 0);
     if (env_int("BRSMOOTH_BATCH_NOTUNE", 0)) {
-        set_shape(c, 8, 4);
+        set_shape(c, 8, B->async ? 2 : 4);
         return build_items(c, kc ? kc : 8);
     }
     return autotune(c);
