@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __r
                                                             double ay, double az, double om1)
 {
     extern __shared__ __align__(16) unsigned char async_smem[];
+    pdl_wait_trigger();
     const int lanew = threadIdx.x & 31;
     unsigned char* ring =
         async_smem + (size_t)(threadIdx.x >> 5) * async_ring_bytes(D, sizeof(T));
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
                                                            const T* __restrict__ tab,
                                                            double ay, double az, double om1)
 {
+    pdl_wait_trigger();
     const int lanew = threadIdx.x & 31;
     while (true) {
         int item = 0;
@@ -471,8 +473,7 @@ int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* coun
     double ay = c->p.ay, az = c->p.az, om1 = 1.0 - c->omega;
     void* args[] = {(void*)&desc, (void*)&ip, &nitems, &counter, &KC, (void*)&uin, &uout,
                     (void*)&b, (void*)&tab, &ay, &az, &om1};
-    return brs_cuda_status(
-        cudaLaunchKernel(k, dim3(B->grid), dim3(B->warps * 32), args, smem, s));
+    return brs_cuda_status(launch_pdl_c(k, dim3(B->grid), dim3(B->warps * 32), smem, s, args));
 }
 
 // Enqueue one call's sweeps (counter reset + one launch per sweep) on stream s.

@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256) box_gather_kernel(
 {
     // CTA order: the row groups of one set of 256 blocks are consecutive CTAs, so the grid
     // is read once, front to back
+    pdl_wait_trigger();
     const int groups = by * bz / RPT;
     const unsigned qc = blockIdx.x / groups;
     const int r0 = (int)(blockIdx.x - qc * groups) * RPT;
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(256) box_gather_any_kernel(
     const long long* __restrict__ rows, long long cnt, int n, int bx, int by, int bz, int nx,
     int ny, int nz, T ax, T ay, T az)
 {
+    pdl_wait_trigger();
     const int groups = by * bz;
     const unsigned qc = blockIdx.x / groups;
     const int r = (int)(blockIdx.x - qc * groups);
@@ -240,9 +242,9 @@ cudaError_t launch_gather(const BoxState* B, const brs_params& p, const T* u, co
 #define BRS_BOX_GATHER(BXV, RPTV)                                                            \
     if (B->bx == BXV && rpt == RPTV) {                                                       \
         const dim3 g2((unsigned)(((M + 255) / 256) * (rows_in_block / RPTV)));              \
-        box_gather_kernel<T, SPLIT, BXV, RPTV><<<g2, 256, 0, s>>>(                            \
-            u, b, rhi, rlo, rows, M, B->n, B->by, B->bz, p.nx, p.ny, p.nz, ax, ay, az);       \
-        return cudaGetLastError();                                                           \
+        return launch_pdl(box_gather_kernel<T, SPLIT, BXV, RPTV>, g2, dim3(256), 0, s, u, b,  \
+                          rhi, rlo, rows, M, B->n, B->by, B->bz, p.nx, p.ny, p.nz, ax, ay,    \
+                          az);                                                               \
     }
     BRS_BOX_GATHER(1, 1)
     BRS_BOX_GATHER(1, 2)
@@ -255,10 +257,8 @@ cudaError_t launch_gather(const BoxState* B, const brs_params& p, const T* u, co
     BRS_BOX_GATHER(4, 2)
     BRS_BOX_GATHER(8, 1)
 #undef BRS_BOX_GATHER
-    box_gather_any_kernel<T, SPLIT><<<grid, 256, 0, s>>>(u, b, rhi, rlo, rows, M, B->n, B->bx,
-                                                         B->by, B->bz, p.nx, p.ny, p.nz, ax, ay,
-                                                         az);
-    return cudaGetLastError();
+    return launch_pdl(box_gather_any_kernel<T, SPLIT>, grid, dim3(256), 0, s, u, b, rhi, rlo,
+                      rows, M, B->n, B->bx, B->by, B->bz, p.nx, p.ny, p.nz, ax, ay, az);
 }
 
 // D = R Ahat^T on CUDA cores, fused with the update.  Tile 64 blocks x BN local cells,
@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(256) box_gemm_simt(
     const long long* __restrict__ rows, const int* __restrict__ off, long long M, int n, int bx,
     int by, int bz, int nx, int ny, double omega)
 {
+    pdl_wait_trigger();
     constexpr int BMS = 64, BKS = 16, TN = BN / 16;
     __shared__ T As[BKS][BMS + 1];
     __shared__ T Bs[BKS][BN + 1];
@@ -343,9 +344,8 @@ cudaError_t launch_simt(const BoxState* B, const T* R, const T* inv, const T* u,
 {
     const long long tm = (M + 63) / 64;
     dim3 grid((unsigned)tm, (unsigned)((B->n + BN - 1) / BN));
-    box_gemm_simt<T, BN><<<grid, 256, 0, s>>>(R, inv, u, uout, rows, B->off, M, B->n, B->bx,
-                                              B->by, B->bz, nx, ny, omega);
-    return cudaGetLastError();
+    return launch_pdl(box_gemm_simt<T, BN>, grid, dim3(256), 0, s, R, inv, u, uout, rows,
+                      (const int*)B->off, M, B->n, B->bx, B->by, B->bz, nx, ny, omega);
 }
 
 template <int SPLIT, int BN>
@@ -418,8 +418,8 @@ int box_pass(brs_ctx* c, const T* uin, T* uout, const T* b, const long long* row
         const int grid = (int)(ntiles < B->sms ? ntiles : B->sms);
         CUtensorMap a0 = B->mR_hi, a1 = B->mR_lo, b0 = B->mA_hi, b1 = B->mA_lo;
         void* args[] = {&a0, &a1, &b0, &b1, &g, &tn, &tm, &nb};
-        e = cudaLaunchKernel(tc_kernel_for(B->split, B->bn), dim3(grid), dim3(192), args,
-                             brs_tc::pers_smem(B->split, B->bn), s);
+        e = launch_pdl_c(tc_kernel_for(B->split, B->bn), dim3(grid), dim3(192),
+                         brs_tc::pers_smem(B->split, B->bn), s, args);
         return brs_cuda_status(e);
     }
     return BRS_ERR_UNSUPPORTED;

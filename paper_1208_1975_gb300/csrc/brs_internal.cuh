@@ -191,4 +191,58 @@ __device__ __forceinline__ void set_status(int* status, int code)
         atomicCAS(status, 0, code);
 }
 
+// Programmatic dependent launch, device side.  pdl_wait: wait until the kernel this one was
+// launched after has completed and its writes are visible.  Every kernel launched with
+// launch_pdl calls it before it reads or writes data the previous kernel touches; for a
+// normal launch it returns at once.  pdl_trigger: let the next kernel in the stream be
+// scheduled as this grid's CTAs retire (without it that happens when they exit).  A
+// long-running kernel that leaves room on its SMs does not trigger early: the next
+// kernel's CTAs would sit beside it, waiting, for its whole run.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_trigger()
+{
+    pdl_wait();
+    pdl_trigger();
+}
+
+// Host side: launch with programmatic stream serialisation, so that the kernel's CTAs may
+// start (and run up to pdl_wait_trigger) while the previous kernel in the stream finishes.
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, A&&... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
+// The same for a kernel given as a function pointer with its argument array.
+inline cudaError_t launch_pdl_c(const void* kernel, dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t s, void** args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
 #endif  // __CUDACC__

@@ -241,8 +241,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
     // constant factor tables, barrier set-up) overlaps that sweep's tail; its grid must have
     // completed before this one reads u or writes the output buffer.  The next sweep may be
     // scheduled as soon as this grid's CTAs begin to retire.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait_trigger();
     __syncthreads();
 
     const long long L0 = (long long)blockIdx.x * a.total / gridDim.x;

@@ -90,6 +90,7 @@ __global__ void plane_gather_kernel(const T* __restrict__ u, const T* __restrict
                                     T* __restrict__ R, int nx, int ny, int nz, double az,
                                     int k0, int kstep, int nbatch)
 {
+    pdl_wait_trigger();
     const long long plane = (long long)nx * ny;
     const long long total = plane * nbatch;
     const T cz = (T)az;
@@ -126,6 +127,7 @@ template <typename T, int EPI>
 __global__ void __launch_bounds__(256) gemm_tn_simt(const T* __restrict__ A,
                                                     const T* __restrict__ B, T* C, GemmArgs g)
 {
+    pdl_wait_trigger();
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
     const int bidx = blockIdx.z;
@@ -195,8 +197,7 @@ cudaError_t launch_gemm(const T* A, const T* B, T* C, const GemmArgs& g, int bat
                         cudaStream_t s)
 {
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
-    gemm_tn_simt<T, EPI><<<grid, 256, 0, s>>>(A, B, C, g);
-    return cudaGetLastError();
+    return launch_pdl(gemm_tn_simt<T, EPI>, grid, dim3(256), 0, s, A, B, C, g);
 }
 
 // R_k = b_k + az (u_{k-1} + u_{k+1}) split into TF32 hi/lo parts, stored at plane k.
@@ -206,6 +207,7 @@ __global__ void plane_gather_split_kernel(const float* __restrict__ u, const flo
                                           int nx, int ny, int nz, float az, int k0, int kstep,
                                           int nbatch, int split)
 {
+    pdl_wait_trigger();
     const long long plane = (long long)nx * ny;
     const long long plane4 = plane / 4;
     const long long total4 = plane4 * nbatch;
@@ -276,8 +278,8 @@ cudaError_t launch_tc(const PlaneState* P, const CUtensorMap& ah, const CUtensor
         CUtensorMap a0 = ah, a1 = al, b0 = bh, b1 = bl;
         brs_tc::TcArgs gg = g;
         void* args[] = {&a0, &a1, &b0, &b1, &gg, &tn, &tm, &nb};
-        return cudaLaunchKernel(pers_kernel_for<SPLIT, EPI>(bn), dim3(grid), dim3(192), args,
-                                pers_smem(SPLIT, bn), s);
+        return launch_pdl_c(pers_kernel_for<SPLIT, EPI>(bn), dim3(grid), dim3(192),
+                            pers_smem(SPLIT, bn), s, args);
     }
     const int bn = P->tc_bn, nst = P->tc_nst;
     const void* k = tc_kernel_for<SPLIT, EPI>(bn, nst);
@@ -285,7 +287,7 @@ cudaError_t launch_tc(const PlaneState* P, const CUtensorMap& ah, const CUtensor
     CUtensorMap a0 = ah, a1 = al, b0 = bh, b1 = bl;
     brs_tc::TcArgs gg = g;
     void* args[] = {&a0, &a1, &b0, &b1, &gg};
-    return cudaLaunchKernel(k, grid, dim3(128), args, tc_smem(SPLIT, bn, nst), s);
+    return launch_pdl_c(k, grid, dim3(128), tc_smem(SPLIT, bn, nst), s, args);
 }
 
 template <int SPLIT>
@@ -299,10 +301,9 @@ int plane_pass_tc(brs_ctx* c, const float* uin, float* uout, const float* b, int
         int blocks = (int)((plane / 4 * nbatch + 255) / 256);
         if (blocks > 152 * 16)
             blocks = 152 * 16;
-        plane_gather_split_kernel<<<blocks, 256, 0, s>>>(uin, b, (float*)P->t2, (float*)P->t2_lo,
-                                                         nx, ny, nz, (float)c->p.az, k0, kstep,
-                                                         nbatch, SPLIT);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(plane_gather_split_kernel, dim3(blocks), dim3(256), 0, s, uin,
+                                   b, (float*)P->t2, (float*)P->t2_lo, nx, ny, nz,
+                                   (float)c->p.az, k0, kstep, nbatch, SPLIT);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
     }
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
     const long long plane = (long long)nx * ny;
     brs::LineTables<T, E, 32> tb;
     tb.load(ytab + (long long)(pin ? p : 0) * tab_len, lane);
+    pdl_wait_trigger();
     const int b0 = blockIdx.y * kYPlanes;
     const int b1 = min(nbatch, b0 + kYPlanes);
     for (int bi = b0; bi < b1; ++bi) {
@@ -432,9 +434,8 @@ cudaError_t launch_ythomas(const PlaneState* P, const T* cin_hi, const T* cin_lo
     const int tl = P->ytab_len;
 #define BRS_YT_CASE(EE)                                                                          \
     if (P->yE == EE) {                                                                           \
-        plane_ythomas_kernel<T, EE, SPLIT><<<grid, 256, smem, s>>>(                              \
-            cin_hi, cin_lo, w_hi, w_lo, tab, tl, nx, ny, k0, kstep, nbatch);                     \
-        return cudaGetLastError();                                                               \
+        return launch_pdl(plane_ythomas_kernel<T, EE, SPLIT>, grid, dim3(256), smem, s, cin_hi,  \
+                          cin_lo, w_hi, w_lo, tab, tl, nx, ny, k0, kstep, nbatch);               \
     }
     BRS_YT_CASE(4)
     BRS_YT_CASE(8)
@@ -466,10 +467,9 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
         int blocks = (int)((plane / 4 * nbatch + 255) / 256);
         if (blocks > 152 * 16)
             blocks = 152 * 16;
-        plane_gather_split_kernel<<<blocks, 256, 0, s>>>(uin, b, (float*)P->t2, (float*)P->t2_lo,
-                                                         nx, ny, nz, (float)c->p.az, k0, kstep,
-                                                         nbatch, SPLIT);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(plane_gather_split_kernel, dim3(blocks), dim3(256), 0, s, uin,
+                                   b, (float*)P->t2, (float*)P->t2_lo, nx, ny, nz,
+                                   (float)c->p.az, k0, kstep, nbatch, SPLIT);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
     }
@@ -519,9 +519,8 @@ int plane_pass(brs_ctx* c, const T* uin, T* uout, const T* b, int k0, int kstep,
         int blocks = (int)((total + 255) / 256);
         if (blocks > 152 * 16)
             blocks = 152 * 16;
-        plane_gather_kernel<T><<<blocks, 256, 0, s>>>(uin, b, R, nx, ny, nz, c->p.az, k0, kstep,
-                                                      nbatch);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(plane_gather_kernel<T>, dim3(blocks), dim3(256), 0, s, uin, b,
+                                   R, nx, ny, nz, c->p.az, k0, kstep, nbatch);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
     }

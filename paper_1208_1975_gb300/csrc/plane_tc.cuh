@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(128, 2) tc_gemm_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_d = *tmem_slot;
+    pdl_wait();  // operands and u come from the previous kernel
 
     int issued = 0;  // producer: stages issued (thread 0 only)
     if (warp == 0 && lane == 0) {
@@ -451,6 +452,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    pdl_wait();  // operands and u come from the previous kernel
 
     auto decode = [&](long long t, int* m0, int* n0, int* plane) {
         const int tn = (int)(t % tiles_n);
