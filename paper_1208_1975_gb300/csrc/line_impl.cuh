@@ -116,16 +116,30 @@ __device__ __forceinline__ void line_solve(T (&r)[E], const LineTables<T, E, G>&
     }
 }
 
+// 16-byte vector with the element type T (loads and stores through it keep T arrays in
+// registers; a vector of another element type would force them into local memory).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+
 // Vector helpers: E consecutive elements, 16-byte chunks.
 template <typename T, int E>
 __device__ __forceinline__ void ld_shared_vec(T (&v)[E], const T* p)
 {
     static_assert((E * sizeof(T)) % 16 == 0, "chunk must be whole 16-byte vectors");
-    const float4* s = reinterpret_cast<const float4*>(p);
+    using V = typename Vec16<T>::type;  // same element type: v stays in registers
+    const V* s = reinterpret_cast<const V*>(p);
 #pragma unroll
     for (int m = 0; m < (int)(E * sizeof(T) / 16); ++m) {
-        float4 f = s[m];
-        reinterpret_cast<float4*>(v)[m] = f;
+        V f = s[m];
+        reinterpret_cast<V*>(v)[m] = f;
     }
 }
 
@@ -137,11 +151,12 @@ __device__ __forceinline__ void ld_shared_vec_rot(T (&v)[E], const T* p, int lan
 {
     constexpr int C = (int)(E * sizeof(T) / 16);
     if constexpr (C == 2) {
-        const float4* s = reinterpret_cast<const float4*>(p);
+        using V = typename Vec16<T>::type;
+        const V* s = reinterpret_cast<const V*>(p);
         const int h = (lane >> 2) & 1;
-        const float4 f0 = s[h], f1 = s[h ^ 1];
-        reinterpret_cast<float4*>(v)[0] = h ? f1 : f0;
-        reinterpret_cast<float4*>(v)[1] = h ? f0 : f1;
+        const V f0 = s[h], f1 = s[h ^ 1];
+        reinterpret_cast<V*>(v)[0] = h ? f1 : f0;
+        reinterpret_cast<V*>(v)[1] = h ? f0 : f1;
     } else {
         ld_shared_vec<T, E>(v, p);
     }
@@ -169,10 +184,11 @@ __device__ __forceinline__ void ld_row(T (&v)[E], const T* p, int lane)
 template <typename T, int E>
 __device__ __forceinline__ void st_global_vec(T* p, const T (&v)[E])
 {
-    float4* d = reinterpret_cast<float4*>(p);
+    using V = typename Vec16<T>::type;
+    V* d = reinterpret_cast<V*>(p);
 #pragma unroll
     for (int m = 0; m < (int)(E * sizeof(T) / 16); ++m)
-        d[m] = reinterpret_cast<const float4*>(v)[m];
+        d[m] = reinterpret_cast<const V*>(v)[m];
 }
 
 // ---------------------------------------------------------------------------------------
