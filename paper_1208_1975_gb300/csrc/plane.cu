@@ -356,15 +356,17 @@ __host__ __device__ inline int ythomas_stride(int ny)
 }
 
 template <typename T, int E, int SPLIT>
-__global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict__ cin_hi,
-                                                            const T* __restrict__ cin_lo,
-                                                            T* __restrict__ w_hi, T* __restrict__ w_lo,
-                                                            const T* __restrict__ ytab, int tab_len,
-                                                            int nx, int ny, int k0, int kstep,
-                                                            int nbatch)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 3 : 1) plane_ythomas_kernel(const T* __restrict__ cin_hi,
+                                                               const T* __restrict__ cin_lo,
+                                                               T* __restrict__ w_hi,
+                                                               T* __restrict__ w_lo,
+                                                               const T* __restrict__ ytab,
+                                                               int tab_len, int nx, int ny, int k0,
+                                                               int kstep, int nbatch)
 {
     extern __shared__ __align__(16) unsigned char ysm[];
-    T* tile = reinterpret_cast<T*>(ysm);
+    // two tiles, alternating by plane: a plane's transposed write reads one tile while the
+    // next plane's solves fill the other, so one barrier per plane suffices.
     // tile[m][y] at m * stride + y + y / 8: a pad word after every 8 cells makes a lane's
     // 8-cell chunk writes hit distinct banks, and stride = 4 (mod 32) does the same for the
     // transposed reads of 8 modes x 4 consecutive y
@@ -373,27 +375,59 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
     const int p = blockIdx.x * kYModes + warp;
     const bool pin = p < nx;  // warp-uniform
     const long long plane = (long long)nx * ny;
+    const bool vec = sizeof(T) == 4 && (ny % 4) == 0 && (E % 4) == 0;  // 16-byte FP32 pieces
     brs::LineTables<T, E, 32> tb;
     tb.load(ytab + (long long)(pin ? p : 0) * tab_len, lane);
     pdl_wait_trigger();
     const int b0 = blockIdx.y * kYPlanes;
     const int b1 = min(nbatch, b0 + kYPlanes);
+    // this lane's E cells of mode p's row in the plane of batch index bi
+    auto load_row = [&](int bi, T (&v)[E]) {
+        const long long row = (long long)(k0 + bi * kstep) * plane + (long long)p * ny;
+        const int y0 = lane * E;
+        if constexpr (sizeof(T) == 4 && E % 4 == 0) {
+            if (vec && y0 + E <= ny) {
+#pragma unroll
+                for (int q = 0; q < E; q += 4) {
+                    const float4 h = __ldg(reinterpret_cast<const float4*>(cin_hi + row + y0 + q));
+                    v[q] = h.x;
+                    v[q + 1] = h.y;
+                    v[q + 2] = h.z;
+                    v[q + 3] = h.w;
+                }
+                if (SPLIT == 3 && cin_lo) {
+#pragma unroll
+                    for (int q = 0; q < E; ++q)
+                        v[q] += cin_lo[row + y0 + q];
+                }
+                return;
+            }
+        }
+        {
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+                v[q] = (y0 + q < ny) ? cin_hi[row + y0 + q] : T(0);
+        }
+        if (SPLIT == 3 && cin_lo) {
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+                if (y0 + q < ny)
+                    v[q] += cin_lo[row + y0 + q];
+        }
+    };
+    T rn[E];
+    if (pin && b0 < b1)
+        load_row(b0, rn);
     for (int bi = b0; bi < b1; ++bi) {
         const int k = k0 + bi * kstep;
+        T* tile = reinterpret_cast<T*>(ysm) + (size_t)((bi - b0) & 1) * kYModes * stride;
         if (pin) {
-            const long long row = (long long)k * plane + (long long)p * ny;
             T r[E];
 #pragma unroll
-            for (int q = 0; q < E; ++q) {
-                const int y = lane * E + q;
-                T v = T(0);
-                if (y < ny) {
-                    v = cin_hi[row + y];
-                    if (SPLIT == 3 && cin_lo)
-                        v += cin_lo[row + y];
-                }
-                r[q] = v;
-            }
+            for (int q = 0; q < E; ++q)
+                r[q] = rn[q];
+            if (bi + 1 < b1)
+                load_row(bi + 1, rn);  // the next plane's row, in flight during this solve
             brs::line_solve<T, E, 32>(r, tb, lane);
 #pragma unroll
             for (int q = 0; q < E; ++q) {
@@ -420,7 +454,6 @@ __global__ void __launch_bounds__(256) plane_ythomas_kernel(const T* __restrict_
                 }
             }
         }
-        __syncthreads();
     }
 }
 
@@ -428,7 +461,7 @@ template <typename T, int SPLIT>
 cudaError_t launch_ythomas(const PlaneState* P, const T* cin_hi, const T* cin_lo, T* w_hi,
                            T* w_lo, int nx, int ny, int k0, int kstep, int nbatch, cudaStream_t s)
 {
-    const size_t smem = (size_t)kYModes * ythomas_stride(ny) * sizeof(T);
+    const size_t smem = 2 * (size_t)kYModes * ythomas_stride(ny) * sizeof(T);
     dim3 grid((nx + kYModes - 1) / kYModes, (nbatch + kYPlanes - 1) / kYPlanes);
     const T* tab = static_cast<const T*>(P->ytab);
     const int tl = P->ytab_len;
@@ -615,7 +648,7 @@ int ythomas_setup(brs_ctx* c)
         e = cudaMemcpy(P->ytab, all.data(), all.size() * sizeof(T), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    const size_t smem = (size_t)kYModes * ythomas_stride(ny) * sizeof(T);
+    const size_t smem = 2 * (size_t)kYModes * ythomas_stride(ny) * sizeof(T);
     const void* ks[2];
     if (sizeof(T) == 8) {
         ks[0] = ythomas_kernel_for<T, 0>(P->yE);
