@@ -74,6 +74,7 @@ def _load():
         "orc_box_minv": [I, I, I, I, I, I, P, P, P],
         "orc_box_jacobi": [I, I, I, I, I, I, D, D, D, D, P, P, P, P, P],
         "orc_box_gs": [I, I, I, I, I, I, D, D, D, D, I, P, P, P],
+        "orc_level_sweep": [I, P, P, P, D, D, D, D, I, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -258,6 +259,32 @@ def sweep(u, b, a, *, block: str = "line", method: str = JACOBI, omega: float = 
         f = plane_factor(nx, ny, a)
         work = np.empty(nx * ny)
         lib.orc_plane_gs(nx, ny, nz, *a, float(omega), order, _ptr(f.L), _ptr(v), _ptr(b), _ptr(work))
+    return v
+
+
+def level_offsets(dims) -> np.ndarray:
+    """Start of each patch in the packed arrays (patches back to back, x fastest)."""
+    d = np.asarray(dims, dtype=np.int64).reshape(-1, 3)
+    return np.concatenate([[0], np.cumsum(d.prod(axis=1))[:-1]]).astype(np.int64)
+
+
+def level_sweep(u, b, dims, nbr, a, *, method: str = JACOBI, omega: float = 0.8):
+    """One smoothing step of a level of patches (packed arrays; Sec. 2 ghost update).
+
+    dims: (npatch, 3) patch sizes (nx, ny, nz); nbr: (npatch, 6) face neighbours in the order
+    -x, +x, -y, +y, -z, +z (patch index, -1 = physical boundary).  Every patch is smoothed
+    with its ghost layer fixed at the neighbours' values from before the step (Jacobi
+    fashion); method 'jacobi' (x-line block Jacobi) or 'gs_lex' (x-line block GS).
+    """
+    u, b = _f64(u).ravel(), _f64(b).ravel()
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+    nb = np.ascontiguousarray(np.asarray(nbr, dtype=np.int32).reshape(-1, 6))
+    off = np.ascontiguousarray(level_offsets(d))
+    v = np.empty_like(u)
+    work = np.empty(2 * int(d.prod(axis=1).max()))
+    m = {JACOBI: 0, GS_LEX: 1}[method]
+    _load().orc_level_sweep(len(d), _ptr(d), _ptr(nb), _ptr(off), *map(float, a), float(omega),
+                            m, _ptr(u), _ptr(b), _ptr(v), _ptr(work))
     return v
 
 

@@ -470,3 +470,65 @@ void orc_box_gs(int nx, int ny, int nz, int bx, int by, int bz, double ax, doubl
     free(rb);
     free(seq);
 }
+
+/*
+ * A level of patches (Sec. 2: "the ghost cells between patches are updated in a Jacobi
+ * fashion at the end of a complete smoothing step over all patches").  Patch p has dims
+ * (nx, ny, nz) = dims[3p..3p+2], its cells at off[p] in the packed arrays (x fastest), and
+ * face neighbours nbr[6p + f] for f = -x, +x, -y, +y, -z, +z (a patch index, or -1 for the
+ * physical boundary, whose ghost values are zero).  Two patches that share a face have the
+ * same extent along the face.
+ *
+ * One smoothing step of the level: every patch is smoothed with its ghost layer fixed at
+ * the neighbours' values from before the step; the ghost values enter the patch's
+ * right-hand side, b_eff = b + a_d * ghost on the patch's boundary cells (the stencil's
+ * coupling to a cell outside the patch moved to the right-hand side).  Each patch is then
+ * one x-line block-Jacobi sweep (method 0) or one lexicographic x-line block Gauss-Seidel
+ * sweep (method 1) with zero values outside it.  `u` is read, `v` receives the new level
+ * iterate (u and v distinct); `work` holds max-patch-size * 2 doubles.
+ */
+static double ghost(const double *u, const long *off, const int *dims, int q, int i, int j,
+                    int k)
+{
+    int qx = dims[3 * q], qy = dims[3 * q + 1];
+    return u[off[q] + (long)i + (long)qx * ((long)j + (long)qy * k)];
+}
+
+void orc_level_sweep(int npatch, const int *dims, const int *nbr, const long *off, double ax,
+                     double ay, double az, double omega, int method, const double *u,
+                     const double *b, double *v, double *work)
+{
+    for (int p = 0; p < npatch; ++p) {
+        int nx = dims[3 * p], ny = dims[3 * p + 1], nz = dims[3 * p + 2];
+        long n = (long)nx * ny * nz;
+        double *beff = work, *up = work + n;
+        const int *nb = nbr + 6 * p;
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    double s = b[off[p] + IDX(i, j, k)];
+                    if (i == 0 && nb[0] >= 0)
+                        s += ax * ghost(u, off, dims, nb[0], dims[3 * nb[0]] - 1, j, k);
+                    if (i == nx - 1 && nb[1] >= 0)
+                        s += ax * ghost(u, off, dims, nb[1], 0, j, k);
+                    if (j == 0 && nb[2] >= 0)
+                        s += ay * ghost(u, off, dims, nb[2], i, dims[3 * nb[2] + 1] - 1, k);
+                    if (j == ny - 1 && nb[3] >= 0)
+                        s += ay * ghost(u, off, dims, nb[3], i, 0, k);
+                    if (k == 0 && nb[4] >= 0)
+                        s += az * ghost(u, off, dims, nb[4], i, j, dims[3 * nb[4] + 2] - 1);
+                    if (k == nz - 1 && nb[5] >= 0)
+                        s += az * ghost(u, off, dims, nb[5], i, j, 0);
+                    beff[IDX(i, j, k)] = s;
+                }
+        if (method == 0) {
+            double *res = (double *)malloc(sizeof(double) * (size_t)n);
+            orc_line_jacobi(nx, ny, nz, ax, ay, az, omega, u + off[p], beff, v + off[p], res);
+            free(res);
+        } else {
+            memcpy(up, u + off[p], sizeof(double) * (size_t)n);
+            orc_line_gs(nx, ny, nz, ax, ay, az, omega, 0, up, beff);
+            memcpy(v + off[p], up, sizeof(double) * (size_t)n);
+        }
+    }
+}
