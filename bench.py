@@ -349,6 +349,38 @@ def _variant_batched(brs, stream, barrier, per_patch=True):
             "speedup_vs_per_patch": graph_rate / per_patch_rate}
 
 
+def _variant_level(brs, stream, barrier, which, dt="f32"):
+    """A level of patches with ghost exchange after every step (Sec. 2), chaotic x-line GS,
+    3 steps per call (the paper's 3 smoothing steps): 96 x 64^3 as a 4 x 4 x 6 array, or the
+    mixed 80-patch set of Table 2.  The same patches without the exchange give its share."""
+    import torch
+
+    from brs_inputs import batched_fields, level_tiling, table2_mixed_level
+
+    if which == "level96x64":
+        dims, nbr = level_tiling((4, 4, 6), (64, 64, 64))
+    else:
+        dims, nbr = table2_mixed_level()
+    td = torch.float64 if dt == "f64" else torch.float32
+    u0 = torch.from_numpy(batched_fields(dims, 2)).to(td).cuda()
+    b = torch.from_numpy(batched_fields(dims, 1, scale_h2=True)).to(td).cuda()
+    cells = int(u0.numel())
+    steps = 10 if dt == "f32" else 2
+    with brs.BatchedContext(dims, COEFFS, method="gs", dtype=dt, nbr=nbr) as lc:
+        u = u0.clone()
+        ms = _time_sweeps(lc, u, b, steps, 2, 3, stream, barrier)
+    with brs.BatchedContext(dims, COEFFS, method="gs", dtype=dt) as bc:
+        u = u0.clone()
+        ms0 = _time_sweeps(bc, u, b, steps, 2, 3, stream, barrier)
+    rate = _rate(cells, 3 * steps, ms)
+    es = 8 if dt == "f64" else 4
+    return {"workload": which, "block": "line", "method": "gs", "dtype": dt,
+            "patches": int(len(dims)), "cells": cells, "sweeps_per_call": 3, "value": rate,
+            "unit": UNIT, "hbm_frac": rate * 3 * es / _peaks()[0],
+            "without_exchange_value": _rate(cells, 3 * steps, ms0),
+            "ghost_exchange_share": max(0.0, (ms - ms0) / ms)}
+
+
 def _variant_defect(brs, stream):
     """512^3, a=(1,0.1,0.01): FP32 plane sweeps inside FP64 defect correction vs FP64 plane
     Jacobi.  Timed segments at 512^3 and a projection to ||r||/||b|| = 1e-10 from the
@@ -477,7 +509,7 @@ BOX_VARIANTS = {
     "box_gs_f64_8cubed": ("gs", "f64", (8, 8, 8), 1, 2, "auto"),
     "box_gs_f64_4cubed": ("gs", "f64", (4, 4, 4), 1, 5, "auto"),
 }
-SPECIAL = ("batched600", "defect512", "adjoint")
+SPECIAL = ("batched600", "level96x64", "table2_mixed", "level96x64_f64", "defect512", "adjoint")
 PROFILE_ONLY = ("batched600_graph",)
 
 
@@ -486,6 +518,14 @@ def _run_variant(name, brs, stream, barrier, peak, steps=None):
         return _variant_batched(brs, stream, barrier)
     if name == "batched600_graph":
         return _variant_batched(brs, stream, barrier, per_patch=False)
+    if name in ("level96x64", "table2_mixed"):
+        out = _variant_level(brs, stream, barrier, name)
+        out["name"] = name
+        return out
+    if name == "level96x64_f64":
+        out = _variant_level(brs, stream, barrier, "level96x64", "f64")
+        out["name"] = name
+        return out
     if name == "defect512":
         return _variant_defect(brs, stream)
     if name == "adjoint":

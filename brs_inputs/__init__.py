@@ -82,6 +82,40 @@ def batched_fields(dims: np.ndarray, seed: int, scale_h2: bool = False, h: float
     return out
 
 
+def level_tiling(P, pdim):
+    """Patch layout of a Px x Py x Pz array of equal patches (patch index x fastest):
+    dims (npatch, 3) and face neighbours (npatch, 6) in the order -x, +x, -y, +y, -z, +z,
+    -1 on the outer boundary."""
+    Px, Py, Pz = P
+    dims, nbr = [], []
+    idx = lambda a, b, c: a + Px * (b + Py * c)
+    for k in range(Pz):
+        for j in range(Py):
+            for i in range(Px):
+                dims.append(list(pdim))
+                nbr.append([idx(i - 1, j, k) if i > 0 else -1,
+                            idx(i + 1, j, k) if i + 1 < Px else -1,
+                            idx(i, j - 1, k) if j > 0 else -1,
+                            idx(i, j + 1, k) if j + 1 < Py else -1,
+                            idx(i, j, k - 1) if k > 0 else -1,
+                            idx(i, j, k + 1) if k + 1 < Pz else -1])
+    return np.array(dims, dtype=np.int64), np.array(nbr, dtype=np.int64)
+
+
+def table2_mixed_level():
+    """The mixed set of the paper's Table 2: 80 patches, 16 each of 64^3, 72^3, 80^3, 88^3
+    and 96^3.  The paper gives no adjacency; here each size class is a 4 x 2 x 2 array of
+    face neighbours (five separate blocks of patches in one level)."""
+    dims, nbr = [], []
+    for n in (64, 72, 80, 88, 96):
+        d, nb = level_tiling((4, 2, 2), (n, n, n))
+        base = len(dims)
+        dims.extend(d.tolist())
+        nbr.extend([[x + base if x >= 0 else -1 for x in row] for row in nb.tolist()])
+    return np.array(dims, dtype=np.int64), np.array(nbr, dtype=np.int64)
+
+
+
 @dataclass(frozen=True)
 class Workload:
     """A named grid workload: interior dims, coefficients, sweeps and dtype."""

@@ -178,6 +178,25 @@ int brsmooth_create_batched(int npatch, const int* dims, const brs_params* commo
 int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int nsweeps,
                            void* stream);
 
+/*
+ * A level of patches (Sec. 2: the ghost cells between patches are updated in a Jacobi
+ * fashion at the end of a complete smoothing step over all patches).  As
+ * brsmooth_create_batched, plus nbr[6 * npatch] (host): for patch p, nbr[6p + f] is the
+ * patch that shares its face f (f = 0..5 for -x, +x, -y, +y, -z, +z) or -1 where the face
+ * is the physical boundary (ghost value zero; fold non-zero boundary data into b).  The
+ * table must be symmetric (q = nbr[6p + f] >= 0 implies nbr[6q + (f ^ 1)] == p; q == p
+ * makes that direction periodic), neighbours across an x face have equal ny and nz (and so
+ * on for y and z faces), and every patch dim must be >= 2.  Each step of
+ * brsmooth_sweep_batched on a level context first writes, for every boundary cell,
+ *   b_eff = b + a_d * (the face neighbour's adjacent value)
+ * into a context-owned array (the neighbours' values from before the step), then smooths
+ * every patch against b_eff with zero values outside the patch.  The context holds one
+ * more packed array (b_eff) than a batched context.  Errors: as brsmooth_create_batched;
+ * BRS_ERR_ARG for a null, out-of-range, asymmetric or face-mismatched table or a dim < 2.
+ */
+int brsmooth_create_level(int npatch, const int* dims, const int* nbr,
+                          const brs_params* common, brs_ctx** out);
+
 /* Launch shape the autotuner chose for a batched context (host outputs). */
 int brsmooth_batched_config(const brs_ctx* c, int* kchunk, int* warps_per_cta, int* ctas,
                             int* work_items);

@@ -86,6 +86,8 @@ def lib():
     L.brsmooth_cells.restype = ctypes.c_longlong
     L.brsmooth_create_batched.argtypes = [I, P, ctypes.POINTER(brs_params), ctypes.POINTER(P)]
     L.brsmooth_sweep_batched.argtypes = [P, P, P, I, P]
+    L.brsmooth_create_level.argtypes = [I, P, P, ctypes.POINTER(brs_params), ctypes.POINTER(P)]
+    L.brsmooth_create_level.restype = I
     IP = ctypes.POINTER(ctypes.c_int)
     L.brsmooth_batched_config.argtypes = [P, IP, IP, IP, IP]
     DP = ctypes.POINTER(D)
@@ -178,6 +180,18 @@ def brsmooth_create_batched(dims, p: brs_params):
     h = ctypes.c_void_p()
     rc = lib().brsmooth_create_batched(len(d) // 3, ctypes.c_void_p(d.ctypes.data), ctypes.byref(p),
                                        ctypes.byref(h))
+    return rc, h
+
+
+def brsmooth_create_level(dims, nbr, p: brs_params):
+    import numpy as np
+
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1))
+    nb = np.ascontiguousarray(np.asarray(nbr, dtype=np.int32).reshape(-1))
+    h = ctypes.c_void_p()
+    rc = lib().brsmooth_create_level(len(d) // 3, ctypes.c_void_p(d.ctypes.data),
+                                     ctypes.c_void_p(nb.ctypes.data), ctypes.byref(p),
+                                     ctypes.byref(h))
     return rc, h
 
 
@@ -376,15 +390,21 @@ class BatchedContext:
     """Many patches (x-line blocks, common coefficients/method/dtype) in one packed array."""
 
     def __init__(self, dims, a=(1.0, 1.0, 1.0), *, method: str = "gs", dtype: str = "f32",
-                 omega: float = 0.0):
+                 omega: float = 0.0, nbr=None):
+        """nbr (npatch x 6 face neighbours, -1 = boundary) makes the patches a level with
+        ghost exchange after every step (brsmooth_create_level)."""
         import numpy as np
 
         self.dims = np.asarray(dims, dtype=np.int64).reshape(-1, 3)
         self.dtype_code = DTYPES[dtype]
         p = brs_params(1, 1, 1, float(a[0]), float(a[1]), float(a[2]), BRS_XLINE, METHODS[method],
                        self.dtype_code, float(omega), BRS_PLANE_AUTO)
-        rc, h = brsmooth_create_batched(self.dims, p)
-        _check(rc, "brsmooth_create_batched")
+        if nbr is None:
+            rc, h = brsmooth_create_batched(self.dims, p)
+            _check(rc, "brsmooth_create_batched")
+        else:
+            rc, h = brsmooth_create_level(self.dims, nbr, p)
+            _check(rc, "brsmooth_create_level")
         self.h = h
         sizes = self.dims.prod(axis=1)
         self.offsets = np.concatenate([[0], np.cumsum(sizes)])

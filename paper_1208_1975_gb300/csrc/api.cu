@@ -407,6 +407,46 @@ int brsmooth_create_batched(int npatch, const int* dims, const brs_params* commo
     return BRS_OK;
 }
 
+int brsmooth_create_level(int npatch, const int* dims, const int* nbr,
+                          const brs_params* common, brs_ctx** out)
+{
+    if (!out)
+        return BRS_ERR_ARG;
+    *out = nullptr;
+    if (npatch < 1 || !dims || !nbr || !common)
+        return BRS_ERR_ARG;
+    // the neighbour table is checked in full before anything touches the device
+    for (int p = 0; p < npatch; ++p) {
+        for (int d = 0; d < 3; ++d)
+            if (dims[3 * p + d] < 2)
+                return BRS_ERR_ARG;
+        for (int f = 0; f < 6; ++f) {
+            const int q = nbr[6 * p + f];
+            if (q < -1 || q >= npatch)
+                return BRS_ERR_ARG;
+            if (q < 0)
+                continue;
+            if (nbr[6 * q + (f ^ 1)] != p)
+                return BRS_ERR_ARG;
+            const int axis = f >> 1;  // the face's normal axis
+            for (int d = 0; d < 3; ++d)
+                if (d != axis && dims[3 * q + d] != dims[3 * p + d])
+                    return BRS_ERR_ARG;
+        }
+    }
+    brs_ctx* c = nullptr;
+    int rc = brsmooth_create_batched(npatch, dims, common, &c);
+    if (rc != BRS_OK)
+        return rc;
+    rc = level_setup(c, nbr);
+    if (rc != BRS_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return BRS_OK;
+}
+
 int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int nsweeps,
                            void* stream)
 {

@@ -33,6 +33,8 @@ struct PatchDesc {
     int nkc;          // z-chunks
     int tab;          // element offset of the patch's line tables
     int vec;          // rows and patch start are 16-byte aligned
+    int bchunk0;      // level: first 256-element chunk of the patch's ghost block
+    long long g0;     // level: start of the patch's ghost block
 };
 
 struct Graph {
@@ -60,6 +62,12 @@ struct BatchState {
     cudaStream_t cap = nullptr; // private capture stream
     std::vector<Graph> graphs;
     bool async = false;         // cp.async kernel (every patch row is 16-byte aligned)
+    // level of patches (ghost exchange between face neighbours after every step)
+    bool level = false;
+    int* d_nbr = nullptr;        // 6 per patch: -x, +x, -y, +y, -z, +z neighbour or -1
+    int* d_chunk_patch = nullptr; // boundary-cell chunk -> patch
+    int nchunks = 0;
+    void* ghost = nullptr;       // ghost blocks of every patch (neighbours' face layers)
     int stages = 4;             // its ring depth (z-steps of lookahead per warp)
 };
 
@@ -69,16 +77,65 @@ BatchState* bs(brs_ctx* c)
 }
 
 constexpr int kE = 4;
-// bytes of one warp's cp.async ring: stages x 4 fields x 32 lanes x kE elements
-constexpr size_t async_ring_bytes(int stages, size_t esize)
+// cp.async ring fields: u(k+1), b(k) and the two halo lines
+constexpr int kFields = 4;
+// x ghosts of one work item of a level, staged per warp: 2 faces x z-steps x lines
+constexpr int kMaxKC = 32;
+constexpr size_t xg_bytes(size_t esize) { return (size_t)2 * kMaxKC * 8 * esize; }
+// bytes of one warp's cp.async area: stages x fields x 32 lanes x kE elements, plus the
+// staged x ghosts of a level
+constexpr size_t async_ring_bytes(int stages, size_t esize, bool level)
 {
-    return (size_t)stages * 4 * 32 * kE * esize;
+    return (size_t)stages * kFields * 32 * kE * esize + (level ? xg_bytes(esize) : 0);
 }
 
-template <typename T, int G, bool GS>
+// Ghost block of a patch of a level (the face neighbours' adjacent layers, copied before
+// every step; zero on the physical boundary), at g0 in the ghost array: the z- and z+ faces
+// ([j][i], nx*ny each), the y- and y+ faces ([k][i], nx*nz), the x- and x+ faces ([k][j],
+// ny*nz), each face starting on a multiple of 4 elements.
+__host__ __device__ __forceinline__ long long round4(long long v) { return (v + 3) & ~3ll; }
+__host__ __device__ __forceinline__ long long ghost_block(int nx, int ny, int nz)
+{
+    return 2 * (round4((long long)nx * ny) + round4((long long)nx * nz) +
+                round4((long long)ny * nz));
+}
+
+// Row (jj, kk) just outside the patch across a z or y face: its x = 0 element in the
+// ghost block, or null (no ghosts, or not a face row).
+template <typename T>
+__device__ __forceinline__ const T* outside_row(const PatchDesc& d, const T* ghost, int jj, int kk)
+{
+    if (!ghost)
+        return nullptr;
+    const long long A = round4((long long)d.nx * d.ny), Bz = round4((long long)d.nx * d.nz);
+    const T* g = ghost + d.g0;
+    if (jj >= 0 && jj < d.ny) {
+        if (kk == -1)
+            return g + (long long)jj * d.nx;
+        if (kk == d.nz)
+            return g + A + (long long)jj * d.nx;
+    } else if (kk >= 0 && kk < d.nz) {
+        if (jj == -1)
+            return g + 2 * A + (long long)kk * d.nx;
+        if (jj == d.ny)
+            return g + 2 * A + Bz + (long long)kk * d.nx;
+    }
+    return nullptr;
+}
+
+// x- face ghost of line (j, k); the x+ ghost is ghost_x(...) + round4(ny * nz).
+template <typename T>
+__device__ __forceinline__ const T* ghost_x(const PatchDesc& d, const T* ghost, int j, int k)
+{
+    const long long A = round4((long long)d.nx * d.ny), Bz = round4((long long)d.nx * d.nz);
+    return ghost + d.g0 + 2 * A + 2 * Bz + j + (long long)d.ny * k;
+}
+
+template <typename T, int G, bool GS, bool LV>
 __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc, int KC,
                                              const T* uin, T* uout, const T* __restrict__ b,
-                                             const T* __restrict__ tab, T ay, T az, T om1)
+                                             const T* __restrict__ tab, T ax, T ay, T az,
+                                             T om1, const T* ghost)
 {
     constexpr int R = 32 / G;
     const int lanew = threadIdx.x & 31;
@@ -97,10 +154,14 @@ __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc,
     const int k0 = kc * KC;
     const int k1 = min(nz, k0 + KC);
 
-    // load E cells of line (jj, kk) of `src`, zero outside the patch
+    // load E cells of line (jj, kk) of `src`; outside the patch the ghost row (u only,
+    // level contexts) or zero
     auto ld = [&](const T* src, int jj, int kk, T (&v)[kE]) {
-        if (xin && jj >= 0 && jj < ny && kk >= 0 && kk < nz) {
-            const T* p = src + (long long)kk * plane + (long long)jj * nx + x0;
+        const bool in = jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+        const T* row = in ? src + (long long)kk * plane + (long long)jj * nx
+                          : ((LV && src == ub) ? outside_row(d, ghost, jj, kk) : nullptr);
+        if (xin && row) {
+            const T* p = row + x0;
             if (d.vec) {
                 if (sizeof(T) == 4) {
                     float4 f = *reinterpret_cast<const float4*>(p);
@@ -125,12 +186,22 @@ __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc,
     T um[kE], uc[kE], up[kE], r[kE], bv[kE], un[kE], us[kE];
     // next step's u(k+2), b(k+1) and halo lines (y-block edges), loaded one step ahead
     T upn[kE], bvn[kE], hnn[kE], hsn[kE];
+    // x ghosts of the line (level contexts): the lane holding x = 0 and the one holding
+    // x = nx - 1 add ax times the neighbour's value, loaded one step ahead
+    const bool xlo = LV && xin && jin && x0 == 0;
+    const bool xhi = LV && xin && jin && x0 <= nx - 1 && nx - 1 < x0 + kE;
+    const long long xpo = round4((long long)ny * nz);
+    T gxm = T(0), gxp = T(0), gxmn = T(0), gxpn = T(0);
+    if (xlo)
+        gxmn = *ghost_x(d, ghost, j, k0);
+    if (xhi)
+        gxpn = ghost_x(d, ghost, j, k0)[xpo];
     ld(ub, j, k0 - 1, um);
     ld(ub, j, k0, uc);
     ld(ub, j, k0 + 1, upn);
     ld(bb, j, k0, bvn);
-    ld(ub, g == 0 ? j - 1 : -1, k0, hnn);
-    ld(ub, g == R - 1 ? j + 1 : -1, k0, hsn);
+    ld(ub, g == 0 ? j - 1 : -2, k0, hnn);
+    ld(ub, g == R - 1 ? j + 1 : -2, k0, hsn);
     for (int k = k0; k < k1; ++k) {
         T hn[kE], hs[kE];
 #pragma unroll
@@ -140,12 +211,18 @@ __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc,
             hn[q] = hnn[q];
             hs[q] = hsn[q];
         }
+        gxm = gxmn;
+        gxp = gxpn;
         if (k + 1 < k1) {
             ld(ub, j, k + 2, upn);
             ld(bb, j, k + 1, bvn);
             // y neighbours at the block edges come from memory (row -1 reads as zero)
-            ld(ub, g == 0 ? j - 1 : -1, k + 1, hnn);
-            ld(ub, g == R - 1 ? j + 1 : -1, k + 1, hsn);
+            ld(ub, g == 0 ? j - 1 : -2, k + 1, hnn);
+            ld(ub, g == R - 1 ? j + 1 : -2, k + 1, hsn);
+            if (xlo)
+                gxmn = *ghost_x(d, ghost, j, k + 1);
+            if (xhi)
+                gxpn = ghost_x(d, ghost, j, k + 1)[xpo];
         }
 #pragma unroll
         for (int q = 0; q < kE; ++q) {
@@ -157,6 +234,14 @@ __device__ __forceinline__ void batched_item(const PatchDesc& d, int jb, int kc,
 #pragma unroll
         for (int q = 0; q < kE; ++q)
             r[q] = (xin && jin) ? fma(az, um[q] + up[q], fma(ay, un[q] + us[q], bv[q])) : T(0);
+        if (xlo)
+            r[0] = fma(ax, gxm, r[0]);
+        if (xhi) {
+#pragma unroll
+            for (int q = 0; q < kE; ++q)
+                if (x0 + q == nx - 1)
+                    r[q] = fma(ax, gxp, r[q]);
+        }
         brs::line_solve<T, kE, G>(r, tb, l);
         T v[kE];
 #pragma unroll
@@ -199,12 +284,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // through a per-warp ring of D steps in shared memory.  Every patch row is a
 // multiple of 16 bytes (checked on the host).  Each lane copies and reads back only its
 // own 16-byte pieces, so no cross-lane synchronisation is needed.
-template <typename T, int G, bool GS, int D>
+template <typename T, int G, bool GS, int D, bool LV>
 __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, int kc, int KC,
                                                    const T* uin, T* uout,
                                                    const T* __restrict__ b,
-                                                   const T* __restrict__ tab, T ay, T az, T om1,
-                                                   unsigned char* ring)
+                                                   const T* __restrict__ tab, T ax, T ay, T az,
+                                                   T om1, const T* ghost, unsigned char* ring)
 {
     constexpr int R = 32 / G;
     constexpr int CH = (int)(kE * sizeof(T) / 16);  // 16-byte chunks per lane and field
@@ -226,15 +311,61 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
     const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(ring);
     // byte offset of (slot, field, chunk) for this lane
     auto soff = [&](int slot, int f, int c) -> uint32_t {
-        return (uint32_t)((((slot * 4 + f) * CH + c) * 32 + lanew) * 16);
+        return (uint32_t)((((slot * kFields + f) * CH + c) * 32 + lanew) * 16);
+    };
+    // Rows of u this item may need from outside the patch (a level's ghost block, else
+    // none): row j of the z- and z+ faces, and the y- / y+ face rows of its edge lines.
+    const T* gzm = nullptr;
+    const T* gzp = nullptr;
+    const T* gym = nullptr;
+    const T* gyp = nullptr;
+    if (LV) {
+        gzm = outside_row(d, ghost, j, -1);
+        gzp = outside_row(d, ghost, j, nz);
+        gym = outside_row(d, ghost, -1, 0);   // + kk * nx for plane kk
+        gyp = outside_row(d, ghost, ny, 0);
+    }
+    // row (jj, kk) of src: inside the patch, else the ghost row (u of a level), else zeros
+    auto row_of = [&](const T* src, int jj, int kk) -> const T* {
+        if (jj >= 0 && jj < ny && kk >= 0 && kk < nz)
+            return src + (long long)kk * plane + (long long)jj * nx;
+        if (!LV || src != ub)
+            return nullptr;
+        if (kk == -1)
+            return jj == j ? gzm : nullptr;
+        if (kk == nz)
+            return jj == j ? gzp : nullptr;
+        if (jj == -1)
+            return gym ? gym + (long long)kk * nx : nullptr;
+        if (jj == ny)
+            return gyp ? gyp + (long long)kk * nx : nullptr;
+        return nullptr;
     };
     auto copy_line = [&](int slot, int f, const T* src, int jj, int kk) {
-        const bool in = xin && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
-        const T* p = in ? src + (long long)kk * plane + (long long)jj * nx + x0 : src;
+        const T* row = row_of(src, jj, kk);
+        const bool ok = xin && row;
+        const T* p = ok ? row + x0 : src;
 #pragma unroll
         for (int c = 0; c < CH; ++c)
-            cp_async16(ring0 + soff(slot, f, c), p + c * (16 / sizeof(T)), in ? 16u : 0u);
+            cp_async16(ring0 + soff(slot, f, c), p + c * (16 / sizeof(T)), ok ? 16u : 0u);
     };
+    // x ghosts of the line (level contexts): the lanes holding x = 0 and x = nx - 1
+    const bool xlo = LV && xin && jin && x0 == 0;
+    const bool xhi = LV && xin && jin && x0 <= nx - 1 && nx - 1 < x0 + kE;
+    // the item's x ghosts, staged once: xg[face][k - k0][line in the warp]
+    T* xg = reinterpret_cast<T*>(ring + (size_t)D * kFields * 32 * kE * sizeof(T));
+    if (LV) {
+        const long long xpo = round4((long long)ny * nz);
+        const int nk = k1 - k0;
+        for (int idx = lanew; idx < 2 * nk * R; idx += 32) {
+            const int face = idx / (nk * R), rem = idx - face * nk * R;
+            const int kk = rem / R, jl = rem - kk * R;
+            const int jj = jb * R + jl;
+            xg[(face * kMaxKC + kk) * 8 + jl] =
+                jj < ny ? ghost_x(d, ghost, jj, k0 + kk)[face ? xpo : 0] : T(0);
+        }
+        __syncwarp();
+    }
     auto issue = [&](int kk, int slot) {
         copy_line(slot, 0, ub, j, kk + 1);
         copy_line(slot, 1, bb, j, kk);
@@ -250,8 +381,9 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
                 *reinterpret_cast<const float4*>(ring + soff(slot, f, c));
     };
     auto ld = [&](const T* src, int jj, int kk, T (&v)[kE]) {
-        if (xin && jj >= 0 && jj < ny && kk >= 0 && kk < nz) {
-            const T* p = src + (long long)kk * plane + (long long)jj * nx + x0;
+        const T* row = row_of(src, jj, kk);
+        if (xin && row) {
+            const T* p = row + x0;
 #pragma unroll
             for (int c = 0; c < CH; ++c)
                 reinterpret_cast<float4*>(v)[c] = reinterpret_cast<const float4*>(p)[c];
@@ -280,6 +412,13 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
             read(slot, 2, hn);
         if (g == R - 1)
             read(slot, 3, hs);
+        T gxm = T(0), gxp = T(0);
+        if (LV) {
+            if (xlo)
+                gxm = xg[(k - k0) * 8 + g];
+            if (xhi)
+                gxp = xg[(kMaxKC + k - k0) * 8 + g];
+        }
 #pragma unroll
         for (int q = 0; q < kE; ++q) {
             T a = __shfl_up_sync(0xffffffffu, uc[q], G);
@@ -290,6 +429,14 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
 #pragma unroll
         for (int q = 0; q < kE; ++q)
             r[q] = (xin && jin) ? fma(az, um[q] + up[q], fma(ay, un[q] + us[q], bv[q])) : T(0);
+        if (xlo)
+            r[0] = fma(ax, gxm, r[0]);
+        if (xhi) {
+#pragma unroll
+            for (int q = 0; q < kE; ++q)
+                if (x0 + q == nx - 1)
+                    r[q] = fma(ax, gxp, r[q]);
+        }
         brs::line_solve<T, kE, G>(r, tb, l);
         T v[kE];
 #pragma unroll
@@ -313,23 +460,24 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
         slot = slot + 1 == D ? 0 : slot + 1;
     }
     cp_async_wait<0>();  // only empty groups remain; the ring is free for the next item
-    __syncwarp();
+    __syncwarp();        // and every lane has read the staged x ghosts
 }
 
-template <typename T, bool GS, int D>
+template <typename T, bool GS, int D, bool LV>
 __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __restrict__ desc,
                                                             const int* __restrict__ item_patch,
                                                             int nitems, int* counter, int KC,
                                                             const T* uin, T* uout,
                                                             const T* __restrict__ b,
                                                             const T* __restrict__ tab,
-                                                            double ay, double az, double om1)
+                                                            double ax, double ay, double az,
+                                                            double om1, const T* ghost)
 {
     extern __shared__ __align__(16) unsigned char async_smem[];
     pdl_wait_trigger();
     const int lanew = threadIdx.x & 31;
     unsigned char* ring =
-        async_smem + (size_t)(threadIdx.x >> 5) * async_ring_bytes(D, sizeof(T));
+        async_smem + (size_t)(threadIdx.x >> 5) * async_ring_bytes(D, sizeof(T), LV);
     while (true) {
         int item = 0;
         if (lanew == 0)
@@ -341,22 +489,81 @@ __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __r
         const int local = item - d.item0;
         const int jb = local % d.njb, kc = local / d.njb;
         switch (d.cls) {
-        case 0: batched_item_async<T, 4, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
-        case 1: batched_item_async<T, 8, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
-        case 2: batched_item_async<T, 16, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
-        default: batched_item_async<T, 32, GS, D>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1, ring); break;
+        case 0: batched_item_async<T, 4, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
+        case 1: batched_item_async<T, 8, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
+        case 2: batched_item_async<T, 16, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
+        default: batched_item_async<T, 32, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
         }
     }
 }
 
-template <typename T, bool GS>
+// Ghost exchange of a level (Sec. 2: ghost cells updated in a Jacobi fashion after each
+// complete smoothing step): every patch's ghost block receives its face neighbours' adjacent
+// layers of u (zero where a face is the physical boundary).  One thread per ghost element,
+// chunks of 256 elements per patch; the sweep that follows reads these values wherever its
+// stencil leaves the patch.
+template <typename T>
+__global__ void __launch_bounds__(256) level_exchange_kernel(const PatchDesc* __restrict__ desc,
+                                                             const int* __restrict__ chunk_patch,
+                                                             const int* __restrict__ nbr,
+                                                             const T* u, T* __restrict__ ghost)
+{
+    pdl_wait_trigger();
+    const int p = __ldg(chunk_patch + blockIdx.x);
+    const int nx = __ldg(&desc[p].nx), ny = __ldg(&desc[p].ny), nz = __ldg(&desc[p].nz);
+    const int t = (int)(blockIdx.x - __ldg(&desc[p].bchunk0)) * (int)blockDim.x + threadIdx.x;
+    const int A = (int)round4((long long)nx * ny), Bz = (int)round4((long long)nx * nz);
+    const int C = (int)round4((long long)ny * nz);
+    if (t >= 2 * (A + Bz + C))
+        return;
+    auto at = [&](int q, int ii, int jj, int kk) -> T {
+        const int qx = __ldg(&desc[q].nx), qy = __ldg(&desc[q].ny);
+        return u[__ldg(&desc[q].off) + ii + (long long)qx * (jj + (long long)qy * kk)];
+    };
+    const int* nb = nbr + 6 * p;
+    T v = T(0);
+    if (t < 2 * A) {  // z faces, [j][i]
+        const bool hi = t >= A;
+        const int r = hi ? t - A : t;
+        if (r >= nx * ny)
+            return;  // padding
+        const int j = r / nx, i = r - j * nx;
+        const int q = __ldg(nb + (hi ? 5 : 4));
+        if (q >= 0)
+            v = at(q, i, j, hi ? 0 : __ldg(&desc[q].nz) - 1);
+    } else if (t < 2 * A + 2 * Bz) {  // y faces, [k][i]
+        const int t2 = t - 2 * A;
+        const bool hi = t2 >= Bz;
+        const int r = hi ? t2 - Bz : t2;
+        if (r >= nx * nz)
+            return;
+        const int k = r / nx, i = r - k * nx;
+        const int q = __ldg(nb + (hi ? 3 : 2));
+        if (q >= 0)
+            v = at(q, i, hi ? 0 : __ldg(&desc[q].ny) - 1, k);
+    } else {  // x faces, [k][j]
+        const int t3 = t - 2 * A - 2 * Bz;
+        const bool hi = t3 >= C;
+        const int r = hi ? t3 - C : t3;
+        if (r >= ny * nz)
+            return;
+        const int k = r / ny, j = r - k * ny;
+        const int q = __ldg(nb + (hi ? 1 : 0));
+        if (q >= 0)
+            v = at(q, hi ? 0 : __ldg(&desc[q].nx) - 1, j, k);
+    }
+    ghost[__ldg(&desc[p].g0) + t] = v;
+}
+
+template <typename T, bool GS, bool LV>
 __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __restrict__ desc,
                                                            const int* __restrict__ item_patch,
                                                            int nitems, int* counter, int KC,
                                                            const T* uin, T* uout,
                                                            const T* __restrict__ b,
                                                            const T* __restrict__ tab,
-                                                           double ay, double az, double om1)
+                                                           double ax, double ay, double az,
+                                                           double om1, const T* ghost)
 {
     pdl_wait_trigger();
     const int lanew = threadIdx.x & 31;
@@ -371,34 +578,46 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
         const int local = item - d.item0;
         const int jb = local % d.njb, kc = local / d.njb;
         switch (d.cls) {
-        case 0: batched_item<T, 4, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
-        case 1: batched_item<T, 8, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
-        case 2: batched_item<T, 16, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
-        default: batched_item<T, 32, GS>(d, jb, kc, KC, uin, uout, b, tab, (T)ay, (T)az, (T)om1); break;
+        case 0: batched_item<T, 4, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
+        case 1: batched_item<T, 8, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
+        case 2: batched_item<T, 16, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
+        default: batched_item<T, 32, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
         }
     }
 }
 
 // FP32 only (the FP64 item does not fit the register budget with its ring addressing)
-const void* async_kernel_for(bool gs, int stages)
+template <bool LV>
+const void* async_kernel_lv(bool gs, int stages)
 {
     if (stages >= 8)
-        return gs ? (const void*)batched_async_kernel<float, true, 8>
-                  : (const void*)batched_async_kernel<float, false, 8>;
+        return gs ? (const void*)batched_async_kernel<float, true, 8, LV>
+                  : (const void*)batched_async_kernel<float, false, 8, LV>;
     if (stages >= 6)
-        return gs ? (const void*)batched_async_kernel<float, true, 6>
-                  : (const void*)batched_async_kernel<float, false, 6>;
-    return gs ? (const void*)batched_async_kernel<float, true, 4>
-              : (const void*)batched_async_kernel<float, false, 4>;
+        return gs ? (const void*)batched_async_kernel<float, true, 6, LV>
+                  : (const void*)batched_async_kernel<float, false, 6, LV>;
+    return gs ? (const void*)batched_async_kernel<float, true, 4, LV>
+              : (const void*)batched_async_kernel<float, false, 4, LV>;
 }
 
-const void* kernel_for(int dtype, bool gs)
+const void* async_kernel_for(bool gs, int stages, bool level)
+{
+    return level ? async_kernel_lv<true>(gs, stages) : async_kernel_lv<false>(gs, stages);
+}
+
+template <bool LV>
+const void* kernel_lv(int dtype, bool gs)
 {
     if (dtype == BRS_F64)
-        return gs ? (const void*)batched_line_kernel<double, true>
-                  : (const void*)batched_line_kernel<double, false>;
-    return gs ? (const void*)batched_line_kernel<float, true>
-              : (const void*)batched_line_kernel<float, false>;
+        return gs ? (const void*)batched_line_kernel<double, true, LV>
+                  : (const void*)batched_line_kernel<double, false, LV>;
+    return gs ? (const void*)batched_line_kernel<float, true, LV>
+              : (const void*)batched_line_kernel<float, false, LV>;
+}
+
+const void* kernel_for(int dtype, bool gs, bool level)
+{
+    return level ? kernel_lv<true>(dtype, gs) : kernel_lv<false>(dtype, gs);
 }
 
 // Line tables of one nx for E = 4 and G lanes (same layout and recurrences as the
@@ -464,16 +683,35 @@ int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* coun
 {
     BatchState* B = bs(c);
     const bool gs = c->p.method == BRS_CHAOTIC_GS;
-    const void* k = B->async ? async_kernel_for(gs, B->stages) : kernel_for(c->p.dtype, gs);
-    const size_t smem = B->async ? (size_t)B->warps * async_ring_bytes(B->stages, c->esize) : 0;
+    const void* k = B->async ? async_kernel_for(gs, B->stages, B->level)
+                             : kernel_for(c->p.dtype, gs, B->level);
+    const size_t smem =
+        B->async ? (size_t)B->warps * async_ring_bytes(B->stages, c->esize, B->level) : 0;
     const PatchDesc* desc = B->d_desc;
     const int* ip = B->d_item_patch;
     int nitems = B->nitems, KC = B->KC;
     const void* tab = B->d_tab;
-    double ay = c->p.ay, az = c->p.az, om1 = 1.0 - c->omega;
+    double ax = c->p.ax, ay = c->p.ay, az = c->p.az, om1 = 1.0 - c->omega;
+    const void* ghost = B->ghost;  // null unless the context is a level
     void* args[] = {(void*)&desc, (void*)&ip, &nitems, &counter, &KC, (void*)&uin, &uout,
-                    (void*)&b, (void*)&tab, &ay, &az, &om1};
+                    (void*)&b, (void*)&tab, &ax, &ay, &az, &om1, (void*)&ghost};
     return brs_cuda_status(launch_pdl_c(k, dim3(B->grid), dim3(B->warps * 32), smem, s, args));
+}
+
+int level_exchange(brs_ctx* c, const void* u, cudaStream_t s)
+{
+    BatchState* B = bs(c);
+    const PatchDesc* desc = B->d_desc;
+    const int* cp = B->d_chunk_patch;
+    const int* nb = B->d_nbr;
+    cudaError_t e;
+    if (c->p.dtype == BRS_F64)
+        e = launch_pdl(level_exchange_kernel<double>, dim3(B->nchunks), dim3(256), 0, s, desc, cp,
+                       nb, static_cast<const double*>(u), static_cast<double*>(B->ghost));
+    else
+        e = launch_pdl(level_exchange_kernel<float>, dim3(B->nchunks), dim3(256), 0, s, desc, cp,
+                       nb, static_cast<const float*>(u), static_cast<float*>(B->ghost));
+    return brs_cuda_status(e);
 }
 
 // Enqueue one call's sweeps (counter reset + one launch per sweep) on stream s.
@@ -488,7 +726,11 @@ int enqueue_sweeps(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t
     void* nxt = gs ? u : c->scratch;
     int rc = BRS_OK;
     for (int k = 0; k < nsweeps && rc == BRS_OK; ++k) {
-        rc = launch_one(c, cur, nxt, b, B->d_counters + k, s);
+        // a level first refreshes its ghost layer from the iterate before the step
+        if (B->level)
+            rc = level_exchange(c, cur, s);
+        if (rc == BRS_OK)
+            rc = launch_one(c, cur, nxt, b, B->d_counters + k, s);
         if (!gs)
             std::swap(cur, nxt);
     }
@@ -544,7 +786,8 @@ int autotune(brs_ctx* c)
             return build_items(c, it->second.KC);
         }
     }
-    const int fixed_kc = env_int("BRSMOOTH_BATCH_KC", 0);
+    int fixed_kc = env_int("BRSMOOTH_BATCH_KC", 0);
+    fixed_kc = fixed_kc > kMaxKC ? kMaxKC : fixed_kc;
     std::vector<TuneVal> cands;
     for (int kc : {4, 8, 16, 32})
         for (int w : {4, 8, 16})
@@ -552,8 +795,8 @@ int autotune(brs_ctx* c)
                 if (w * cps > 64)
                     continue;
                 if (B->async &&
-                    ((size_t)w * cps * async_ring_bytes(B->stages, c->esize) > 220u * 1024u ||
-                     (size_t)w * async_ring_bytes(B->stages, c->esize) > 227u * 1024u))
+                    ((size_t)w * cps * async_ring_bytes(B->stages, c->esize, true) > 220u * 1024u ||
+                     (size_t)w * async_ring_bytes(B->stages, c->esize, true) > 227u * 1024u))
                     continue;  // the rings of every resident warp must fit one SM
                 if (fixed_kc && kc != fixed_kc)
                     continue;
@@ -680,22 +923,64 @@ int batched_setup(brs_ctx* c, int npatch, const int* dims)
     B->stages = env_int("BRSMOOTH_BATCH_STAGES", 4);
     B->stages = B->stages >= 8 ? 8 : B->stages >= 6 ? 6 : 4;
     if (B->async) {
-        const size_t want =
-            std::min<size_t>(227u * 1024u, 16 * async_ring_bytes(B->stages, c->esize));
-        const void* k = async_kernel_for(c->p.method == BRS_CHAOTIC_GS, B->stages);
-        cudaFuncAttributes fa{};
-        e = cudaFuncGetAttributes(&fa, k);
-        if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < want)
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-        if (e != cudaSuccess)
-            return brs_cuda_status(e);
+        // both the plain and the level kernel (a level is set up after the tuner ran)
+        for (bool lv : {false, true}) {
+            const size_t want =
+                std::min<size_t>(227u * 1024u, 16 * async_ring_bytes(B->stages, c->esize, lv));
+            const void* k = async_kernel_for(c->p.method == BRS_CHAOTIC_GS, B->stages, lv);
+            cudaFuncAttributes fa{};
+            e = cudaFuncGetAttributes(&fa, k);
+            if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < want)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)want);
+            if (e != cudaSuccess)
+                return brs_cuda_status(e);
+        }
     }
-    const int kc = env_int("BRSMOOTH_BATCH_KC", 0);
+    int kc = env_int("BRSMOOTH_BATCH_KC", 0);
+    kc = kc > kMaxKC ? kMaxKC : kc;  // a level stages at most kMaxKC z-steps of x ghosts
     if (env_int("BRSMOOTH_BATCH_NOTUNE", 0)) {
         set_shape(c, 8, B->async ? 2 : 4);
         return build_items(c, kc ? kc : 8);
     }
     return autotune(c);
+}
+
+int level_setup(brs_ctx* c, const int* nbr)
+{
+    BatchState* B = bs(c);
+    B->level = true;
+    // boundary-cell chunks per patch (every dim >= 2, checked by the caller)
+    std::vector<int> chunk_patch;
+    long long gtotal = 0;
+    for (int q = 0; q < B->npatch; ++q) {
+        PatchDesc& d = B->h_desc[q];
+        const long long gb = ghost_block(d.nx, d.ny, d.nz);
+        if (gb >= (1ll << 31))
+            return BRS_ERR_UNSUPPORTED;  // the exchange kernel numbers ghosts in 32 bits
+        d.g0 = gtotal;
+        gtotal += gb;
+        d.bchunk0 = (int)chunk_patch.size();
+        for (long long t = 0; t < (gb + 255) / 256; ++t)
+            chunk_patch.push_back(q);
+    }
+    B->nchunks = (int)chunk_patch.size();
+    cudaError_t e = cudaMemcpy(B->d_desc, B->h_desc.data(), sizeof(PatchDesc) * B->npatch,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&B->d_chunk_patch, sizeof(int) * chunk_patch.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_chunk_patch, chunk_patch.data(), sizeof(int) * chunk_patch.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&B->d_nbr, sizeof(int) * 6 * B->npatch);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_nbr, nbr, sizeof(int) * 6 * B->npatch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&B->ghost, (size_t)gtotal * c->esize);
+    if (e == cudaSuccess)
+        e = cudaMemset(B->ghost, 0, (size_t)gtotal * c->esize);
+    return brs_cuda_status(e);
 }
 
 void batched_teardown(brs_ctx* c)
@@ -705,7 +990,8 @@ void batched_teardown(brs_ctx* c)
         return;
     for (auto& g : B->graphs)
         cudaGraphExecDestroy(g.exec);
-    for (void* q : {(void*)B->d_desc, (void*)B->d_item_patch, B->d_tab, (void*)B->d_counters})
+    for (void* q : {(void*)B->d_desc, (void*)B->d_item_patch, B->d_tab, (void*)B->d_counters,
+                    (void*)B->d_nbr, (void*)B->d_chunk_patch, B->ghost})
         if (q)
             cudaFree(q);
     if (B->cap)

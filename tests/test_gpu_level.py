@@ -1,0 +1,109 @@
+"""A level of patches on the GPU (x-line sweeps inside patches, ghost exchange between face
+neighbours after every step, Sec. 2) against the oracle's level sweep.
+
+Jacobi inside patches is deterministic: element-wise parity sweep by sweep, on a regular
+tiling, on patches of different y extents sharing y faces, with a periodic direction, and
+on the paper's 96 x 64^3 level.  Chaotic GS inside patches: convergence of a tiled level to
+the global A^{-1} b.
+"""
+import numpy as np
+import pytest
+
+from brs_inputs import initial_guess, rhs, uniform_field
+from gpu_common import TOL, rel_max_err, rounded, to_dev, to_np
+from test_oracle_level import pack, tiling, unpack
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def brs():
+    import paper_1208_1975_gb300 as brs
+
+    brs.build()
+    return brs
+
+
+def layouts():
+    out = {}
+    d, n = tiling((2, 2, 2), (16, 12, 8))
+    out["tiled2x2x2"] = (d, n)
+    d, n = tiling((3, 1, 2), (24, 20, 6))
+    out["tiled3x1x2"] = (d, n)
+    # two columns of patches with different ny stacked along y (x and z extents agree)
+    out["uneven_y"] = (np.array([[32, 8, 6], [32, 14, 6], [32, 5, 6]]),
+                       np.array([[-1, -1, -1, 1, -1, -1], [-1, -1, 0, 2, -1, -1],
+                                 [-1, -1, 1, -1, -1, -1]]))
+    # periodic in x (a patch is its own x neighbour) next to a plain patch along z
+    out["periodic_x"] = (np.array([[16, 10, 7], [16, 10, 9]]),
+                         np.array([[0, 0, -1, -1, -1, 1], [-1, -1, -1, -1, 0, -1]]))
+    return out
+
+
+LAYOUTS = layouts()
+
+
+def run_level(brs, dims, nbr, u, b, a, dt, nsweeps, method="jacobi"):
+    with brs.BatchedContext(dims, a, method=method, dtype=dt, nbr=nbr) as ctx:
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
+        out = []
+        for _ in range(nsweeps):
+            ctx.sweep(ut, bt, 1)
+            out.append(to_np(ut))
+        assert brs.brsmooth_last_error(ctx.h) == 0
+    return out
+
+
+@pytest.mark.parametrize("name", list(LAYOUTS))
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_level_jacobi_parity(brs, orc, name, dt):
+    dims, nbr = LAYOUTS[name]
+    n = int(np.prod(dims, axis=1).sum())
+    u = rounded(uniform_field((n,), 31), dt)
+    b = rounded(uniform_field((n,), 32) * 1e-3, dt)
+    a = (1.0, 0.5, 0.25)
+    got = run_level(brs, dims, nbr, u, b, a, dt, 3)
+    prev = u
+    for k in range(3):
+        ref = orc.level_sweep(prev, b, dims, nbr, a, method="jacobi", omega=0.8)
+        assert rel_max_err(got[k], ref) <= TOL[dt], (name, k)
+        prev = got[k]  # per-sweep parity from the device's own iterate
+
+
+def test_level_multi_sweep_call_matches_single_calls(brs):
+    dims, nbr = LAYOUTS["tiled2x2x2"]
+    n = int(np.prod(dims, axis=1).sum())
+    u = rounded(uniform_field((n,), 33), "f32")
+    b = rounded(uniform_field((n,), 34) * 1e-3, "f32")
+    one = run_level(brs, dims, nbr, u, b, (1, 1, 1), "f32", 4)[-1]
+    with brs.BatchedContext(dims, (1, 1, 1), method="jacobi", dtype="f32", nbr=nbr) as ctx:
+        ut, bt = to_dev(u, "f32"), to_dev(b, "f32")
+        ctx.sweep(ut, bt, 4)
+        four = to_np(ut)
+    assert np.array_equal(one, four)
+
+
+def test_level_gs_converges_to_global_solution(brs, orc):
+    P, pdim = (2, 2, 2), (12, 10, 8)
+    dims, nbr = tiling(P, pdim)
+    a = (1.0, 1.0, 1.0)
+    bg = rhs((16, 20, 24))
+    ref = orc.exact_solve(bg, a)
+    b = pack(bg, P, pdim)
+    with brs.BatchedContext(dims, a, method="gs", dtype="f64", nbr=nbr) as ctx:
+        ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
+        ctx.sweep(ut, bt, 2500)  # the oracle's lexicographic level GS needs 757 to 1e-11
+        got = to_np(ut)
+    assert rel_max_err(unpack(got, P, pdim), ref) <= 1e-10
+
+
+def test_paper_level_96_patches_of_64cubed(brs, orc):
+    """The paper's 96 x 64^3 level (a 4 x 4 x 6 array of patches), FP32, one Jacobi step."""
+    P, pdim = (4, 4, 6), (64, 64, 64)
+    dims, nbr = tiling(P, pdim)
+    n = 96 * 64 ** 3
+    u = rounded(uniform_field((n,), 35), "f32")
+    b = rounded(uniform_field((n,), 36) * (1.0 / 65) ** 2, "f32")
+    got = run_level(brs, dims, nbr, u, b, (1, 1, 1), "f32", 1)[0]
+    ref = orc.level_sweep(u, b, dims, nbr, (1, 1, 1), method="jacobi", omega=0.8)
+    assert rel_max_err(got, ref) <= TOL["f32"]

@@ -109,3 +109,18 @@ def test_params_struct_layout_matches_header(tmp_path):
     assert int(out["size"]) == ctypes.sizeof(brs.brs_params)
     for f in fields:
         assert int(out[f]) == getattr(brs.brs_params, f).offset, f
+
+
+@pytest.mark.parametrize("case", [
+    ([[4, 4, 4], [4, 4, 4]], [[-1, 1, -1, -1, -1, -1], [-1] * 6]),          # not symmetric
+    ([[4, 4, 4], [4, 5, 4]], [[-1, 1, -1, -1, -1, -1], [0, -1, -1, -1, -1, -1]]),  # faces differ
+    ([[4, 4, 1]], [[-1] * 6]),                                              # a dim below 2
+    ([[4, 4, 4]], [[2, -1, -1, -1, -1, -1]]),                               # index out of range
+    ([[4, 4, 4]], [[-2, -1, -1, -1, -1, -1]]),                              # negative index
+])
+def test_create_level_rejects_bad_tables_before_any_device_call(cuda_lib, case):
+    import paper_1208_1975_gb300 as brs
+
+    p = brs.brs_params(1, 1, 1, 1.0, 1.0, 1.0, 0, 1, 1, 0.0, 0)
+    rc, h = brs.brsmooth_create_level(case[0], case[1], p)
+    assert rc == brs.BRS_ERR_ARG and not h.value
