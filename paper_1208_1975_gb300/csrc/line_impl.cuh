@@ -253,11 +253,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
             mbar_init(&full[s], 1);
         fence_mbar_init();
     }
-    // Launched as a programmatic dependent of the previous sweep: the prologue above (the
-    // constant factor tables, barrier set-up) overlaps that sweep's tail; its grid must have
-    // completed before this one reads u or writes the output buffer.  The next sweep may be
-    // scheduled as soon as this grid's CTAs begin to retire.
-    pdl_wait_trigger();
     __syncthreads();
 
     const long long L0 = (long long)blockIdx.x * a.total / gridDim.x;
@@ -273,6 +268,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
     int p_next = 0, p_slot = 0;   // next stage to issue and its slot
     int p_seg_base = 0, p_end = 0;
     bool p_has = false;
+    int b_pre = 0;                // stages [0, b_pre) had their b rows requested early
     auto issue = [&](int limit) {
         while (true) {
             if (!p_has || p_next >= p_end) {
@@ -289,12 +285,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
             T* dst = slot_ptr(p_slot);
             uint64_t* bar = &full[p_slot];
             const bool with_b = t >= 2;
-            mbar_arrive_expect_tx(bar, ubytes + (with_b ? bbytes : 0u));
+            const bool pre = p_next < b_pre;  // b rows already requested (see below)
+            if (!pre)
+                mbar_arrive_expect_tx(bar, ubytes + (with_b ? bbytes : 0u));
             const int j0 = pit.jt * JT;
             const int ku = pit.kb - 1 + t;
             for (int pc = 0; pc < pieces; ++pc)
                 tma_load_3d(dst + (size_t)pc * ubox, &tm_u, bar, pc * bx, j0 - 1, ku);
-            if (with_b) {
+            if (with_b && !pre) {
                 T* bdst = dst + u_elems;
                 for (int pc = 0; pc < pieces; ++pc)
                     tma_load_3d(bdst + (size_t)pc * bbox, &tm_b, bar, pc * bx, j0, ku - 1);
@@ -303,6 +301,40 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
             p_slot = inc(p_slot);
         }
     };
+    // Launched as a programmatic dependent of the previous sweep: everything above (the
+    // constant factor tables, barrier set-up) overlaps that sweep's tail, and so do the
+    // b rows of the first ring stages (b is read only, for every sweep).  The previous grid
+    // must have completed before this one reads u or writes the output buffer; a stage's
+    // barrier expects its u and b bytes together, so no step starts before its u arrives.
+    // The next sweep may be scheduled as soon as this grid's CTAs begin to retire.
+    if (tid == 0) {
+        SegIter it = pit;
+        int seg_base = 0, end = 0, slot = 0;
+        bool has = false;
+        while (b_pre < NS) {
+            if (!has || b_pre >= end) {
+                if (has)
+                    seg_base = end;
+                has = it.next();
+                if (!has)
+                    break;
+                end = seg_base + it.n + 2;
+            }
+            const int t = b_pre - seg_base;
+            uint64_t* bar = &full[slot];
+            const bool with_b = t >= 2;
+            mbar_arrive_expect_tx(bar, ubytes + (with_b ? bbytes : 0u));
+            if (with_b) {
+                T* bdst = slot_ptr(slot) + u_elems;
+                for (int pc = 0; pc < pieces; ++pc)
+                    tma_load_3d(bdst + (size_t)pc * bbox, &tm_b, bar, pc * bx, it.jt * JT,
+                                it.kb - 2 + t);
+            }
+            ++b_pre;
+            slot = inc(slot);
+        }
+    }
+    pdl_wait_trigger();
     if (tid == 0)
         issue(NS);
 
