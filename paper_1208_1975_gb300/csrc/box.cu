@@ -16,6 +16,7 @@
 // cores (tcgen05.mma kind::tf32, single TF32 or split-TF32 hi*hi + hi*lo + lo*hi) through the
 // persistent product kernel of plane_tc.cuh with its EPI_BOX epilogue.
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "box.cuh"
@@ -358,8 +359,16 @@ const void* tc_kernel()
 const void* tc_kernel_for(int split, int bn)
 {
     if (split == 3)
-        return bn == 128 ? tc_kernel<3, 128>() : bn == 64 ? tc_kernel<3, 64>() : tc_kernel<3, 32>();
-    return bn == 128 ? tc_kernel<1, 128>() : bn == 64 ? tc_kernel<1, 64>() : tc_kernel<1, 32>();
+        return bn == 256 ? tc_kernel<3, 256>() : bn == 128 ? tc_kernel<3, 128>()
+             : bn == 64  ? tc_kernel<3, 64>()  : tc_kernel<3, 32>();
+    return bn == 256 ? tc_kernel<1, 256>() : bn == 128 ? tc_kernel<1, 128>()
+         : bn == 64  ? tc_kernel<1, 64>()  : tc_kernel<1, 32>();
+}
+
+int env_int(const char* name, int dflt)
+{
+    const char* v = std::getenv(name);
+    return v ? std::atoi(v) : dflt;
 }
 
 // One pass: gather the rows of `rows[0..M)` from uin, then the product and update into uout.
@@ -517,6 +526,8 @@ int box_setup(brs_ctx* c)
     B->math = math;
     B->split = math == BRS_PLANE_3XTF32 ? 3 : math == BRS_PLANE_TF32 ? 1 : 0;
     B->bn = n >= 128 ? 128 : n >= 64 ? 64 : 32;
+    if (n >= 256 && env_int("BRSMOOTH_BOX_BN", 0) == 256)
+        B->bn = 256;
     cudaError_t e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess)
         return brs_cuda_status(e);

@@ -262,6 +262,8 @@ const void* pers_kernel_for(int bn)
 {
     if (bn == 64)
         return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 64, pers_nst(SPLIT, 64)>;
+    if (bn == 256)
+        return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 256, pers_nst(SPLIT, 256)>;
     return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 128, pers_nst(SPLIT, 128)>;
 }
 
@@ -693,11 +695,13 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
     P->tc_nst = P->tc_bn == 64 ? (P->math == BRS_PLANE_3XTF32 ? 2 : 4) : 3;
     // persistent warp-specialised products (double-buffered TMEM accumulator)
     const char* penv = std::getenv("BRSMOOTH_TC_PERSISTENT");
-    // measured: split-TF32 gains from overlapping epilogues with the next tile's MMAs
-    // (37 -> 43 Gcell/s at 256^3); single TF32 is faster with two per-tile CTAs per SM
-    P->tc_persistent = penv ? std::atoi(penv) != 0 : (P->math == BRS_PLANE_3XTF32 ? 1 : 0);
+    // measured at 256^3 (x-sine form, same box): the persistent kernel, which overlaps a
+    // tile's epilogue with the next tile's MMAs, beats two per-tile CTAs per SM for split
+    // TF32 and, narrowly, for single TF32 (96.4 vs 95.0 Gcell/s).  Tiles of N = 128 beat
+    // N = 256, whose two-stage split-TF32 ring starves the MMA issue (76.0 vs 71.2).
+    P->tc_persistent = penv ? std::atoi(penv) != 0 : 1;
     const char* pbn = std::getenv("BRSMOOTH_TC_PBN");
-    P->tc_pbn = (pbn && std::atoi(pbn) == 64) ? 64 : 128;
+    P->tc_pbn = pbn ? (std::atoi(pbn) == 64 ? 64 : std::atoi(pbn) == 256 ? 256 : 128) : 128;
     cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (P->tc_persistent)
         P->tc_bn = P->tc_pbn;  // B maps' box rows follow the tile N in use

@@ -40,10 +40,11 @@ inline int upload_split(void** hi, void** lo, const std::vector<double>& src)
     return brs_cuda_status(e);
 }
 
-// Persistent products: ring stages per (split, tile N) so that the ring is 160-192 KB.
+// Persistent products: ring stages per (split, tile N) so that the ring is 160-196 KB.
 constexpr int pers_nst(int split, int bn)
 {
-    return split == 3 ? (bn == 128 ? 3 : 4) : (bn == 128 ? 6 : 8);
+    return bn == 256 ? (split == 3 ? 2 : 4)
+                     : split == 3 ? (bn == 128 ? 3 : 4) : (bn == 128 ? 6 : 8);
 }
 
 inline size_t pers_smem(int split, int bn)

@@ -126,9 +126,11 @@ def test_box_converges_fp64(brs, orc):
     assert rel_max_err(got, ref) <= 1e-10
 
 
-def test_box_full_size_one_sweep(brs, orc):
+@pytest.mark.parametrize("bn", ["0", "256"], ids=["tileN128", "tileN256"])
+def test_box_full_size_one_sweep(brs, orc, bn, monkeypatch):
     """256^3 FP32, 8^3 boxes, split-TF32, the launch the benchmark times: one Jacobi sweep
-    against the oracle over the whole grid."""
+    against the oracle over the whole grid (product tiles of 128 and of 256 local cells)."""
+    monkeypatch.setenv("BRSMOOTH_BOX_BN", bn)
     nx = ny = nz = 256
     a = (1.0, 1.0, 1.0)
     u, b = inputs((nx, ny, nz), "f32")

@@ -150,7 +150,8 @@ def test_full_size_256_sampled_planes(brs, orc, dt):
 TC_SHAPES = [(32, 32, 4), (64, 96, 3), (96, 64, 5), (256, 256, 3), (160, 128, 2)]
 
 
-@pytest.mark.parametrize("kernel", ["tile64", "tile128", "persistent128", "persistent64"])
+@pytest.mark.parametrize("kernel", ["tile64", "tile128", "persistent128", "persistent64",
+                                    "persistent256"])
 @pytest.mark.parametrize("shape", TC_SHAPES, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
 def test_plane_3xtf32_one_sweep_parity(brs, orc, shape, a, kernel, monkeypatch):
@@ -167,10 +168,12 @@ def test_plane_3xtf32_one_sweep_parity(brs, orc, shape, a, kernel, monkeypatch):
     assert rel_max_err(got, ref) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("persistent", ["0", "1"])
-@pytest.mark.parametrize("shape", [(32, 32, 4), (160, 128, 2)], ids=str)
+@pytest.mark.parametrize("persistent", ["0", "1", "256"])
+@pytest.mark.parametrize("shape", [(32, 32, 4), (160, 128, 2), (256, 256, 2)], ids=str)
 def test_plane_single_tf32_error_is_tf32_level(brs, orc, shape, persistent, monkeypatch):
-    monkeypatch.setenv("BRSMOOTH_TC_PERSISTENT", persistent)
+    monkeypatch.setenv("BRSMOOTH_TC_PERSISTENT", "0" if persistent == "0" else "1")
+    if persistent == "256":
+        monkeypatch.setenv("BRSMOOTH_TC_PBN", "256")
     """One TF32 pass per product: per-sweep error at the TF32 unit roundoff 2^-11 ~ 4.9e-4
     (not held to the FP32 bar; used inside defect correction, where FP64 decides)."""
     nx, ny, nz = shape
