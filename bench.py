@@ -469,6 +469,62 @@ def _variant_defect(brs, stream):
     return out
 
 
+STUDY_BLOCKS = [("box", (1, 1, 1)), ("box", (2, 2, 2)), ("box", (4, 2, 2)), ("box", (4, 4, 2)),
+                ("box", (4, 4, 4)), ("box", (8, 4, 4)), ("box", (8, 8, 4)), ("box", (8, 8, 8)),
+                ("line", (0, 0, 0)), ("plane", (0, 0, 0))]
+
+
+def _variant_block_study(brs, stream, n=64, i_win=5000, k_win=100):
+    """Sec. 3 block-size study on the paper's 64^3 patch, FP64, a=(1,1,1), b=0 and a random
+    initial guess: ||r_3||/||r_0||, the sliding-window factor (||r_{i+k}||/||r_i||)^(1/k) at
+    i = 5000, the time per sweep, and the time per decade of residual reduction.  For
+    Jacobi with point, x-line and xy-plane blocks the asymptotic factor has a closed form
+    (the slowest sine mode), reported beside the measurement."""
+    import math
+
+    import torch
+
+    from brs_inputs import initial_guess
+
+    a = (1.0, 1.0, 1.0)
+    u0 = torch.from_numpy(initial_guess((n, n, n))).cuda()
+    b = torch.zeros_like(u0)
+    s1 = 2 - 2 * math.cos(math.pi / (n + 1))
+    lam = 3 * s1
+    closed = {"box(1, 1, 1)": 1 - 0.8 * lam / 6, "line": 1 - 0.8 * lam / (s1 + 4),
+              "plane": 1 - 0.8 * lam / (2 * s1 + 2)}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    rows = []
+    for blk, box in STUDY_BLOCKS:
+        label = f"box{box}" if blk == "box" else blk
+        for meth in ("jacobi", "gs"):
+            with brs.Context(n, n, n, a, block=blk, method=meth, dtype="f64", box=box) as c:
+                u = u0.clone()
+                r0 = c.residual(u, b)
+                c.sweep(u, b, 3)
+                r3 = c.residual(u, b)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                c.sweep(u, b, i_win - 3)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / (i_win - 3)
+                ri = c.residual(u, b)
+                c.sweep(u, b, k_win)
+                rk = c.residual(u, b)
+                fac = (rk / ri) ** (1.0 / k_win) if ri > 0 and rk > 0 else None
+                row = {"block": label, "method": meth, "r3_over_r0": r3 / r0,
+                       "factor_at_5000": fac, "ms_per_sweep": ms,
+                       "ms_per_decade": (ms * math.log(10) / -math.log(fac)
+                                         if fac and 0 < fac < 1 else None)}
+                if meth == "jacobi" and label in closed:
+                    row["factor_closed_form"] = closed[label]
+                rows.append(row)
+    return {"workload": f"block_study {n}^3 FP64, a=(1,1,1), b=0, random initial guess",
+            "window": {"i": i_win, "k": k_win}, "results": rows}
+
+
 def _variant_adjoint(brs, stream):
     """128^3 and 384^3: 8 x-line Jacobi sweeps forward + adjoint backward (checkpoint 4)."""
     import torch
@@ -520,8 +576,12 @@ BOX_VARIANTS = {
     "box_jacobi_f32_4cubed_3xtf32": ("jacobi", "f32", (4, 4, 4), 4, 10, "3xtf32"),
     "box_gs_f64_8cubed": ("gs", "f64", (8, 8, 8), 1, 2, "auto"),
     "box_gs_f64_4cubed": ("gs", "f64", (4, 4, 4), 1, 5, "auto"),
+    # y- and z-lines as 1 x 256 x 1 and 1 x 1 x 256 boxes (blocks for other anisotropies)
+    "box_jacobi_f32_yline_3xtf32": ("jacobi", "f32", (1, 256, 1), 4, 10, "3xtf32"),
+    "box_jacobi_f32_zline_3xtf32": ("jacobi", "f32", (1, 1, 256), 4, 10, "3xtf32"),
 }
-SPECIAL = ("batched600", "level96x64", "table2_mixed", "level96x64_f64", "defect512", "adjoint")
+SPECIAL = ("batched600", "level96x64", "table2_mixed", "level96x64_f64", "defect512", "adjoint",
+           "block_study64")
 PROFILE_ONLY = ("batched600_graph",)
 
 
@@ -542,6 +602,8 @@ def _run_variant(name, brs, stream, barrier, peak, steps=None):
         return _variant_defect(brs, stream)
     if name == "adjoint":
         return _variant_adjoint(brs, stream)
+    if name == "block_study64":
+        return _variant_block_study(brs, stream)
     if name in BOX_VARIANTS:
         meth, dt, box, st, sw, math = BOX_VARIANTS[name]
         out = _variant_grid(brs, stream, barrier, peak, "box", meth, dt, COEFFS, steps or st, sw,

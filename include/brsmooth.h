@@ -186,13 +186,16 @@ int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int
  * is the physical boundary (ghost value zero; fold non-zero boundary data into b).  The
  * table must be symmetric (q = nbr[6p + f] >= 0 implies nbr[6q + (f ^ 1)] == p; q == p
  * makes that direction periodic), neighbours across an x face have equal ny and nz (and so
- * on for y and z faces), and every patch dim must be >= 2.  Each step of
- * brsmooth_sweep_batched on a level context first writes, for every boundary cell,
- *   b_eff = b + a_d * (the face neighbour's adjacent value)
- * into a context-owned array (the neighbours' values from before the step), then smooths
- * every patch against b_eff with zero values outside the patch.  The context holds one
- * more packed array (b_eff) than a batched context.  Errors: as brsmooth_create_batched;
- * BRS_ERR_ARG for a null, out-of-range, asymmetric or face-mismatched table or a dim < 2.
+ * on for y and z faces), and every patch dim must be >= 2.  Every step of
+ * brsmooth_sweep_batched on a level context smooths each patch with its ghost layer held
+ * at the face neighbours' values from before the step (zero on the physical boundary).
+ * The ghost layers live in context-owned ghost blocks (the six faces of every patch): the
+ * first step of a call gathers them from the iterate, and each later step of the same call
+ * reads the faces that the previous step wrote there as it computed them (two ghost
+ * arrays, alternating), so a call of n steps equals n calls of one step.  The context
+ * holds two ghost arrays, each of 2 (nx ny + nx nz + ny nz) elements per patch (faces
+ * rounded up to multiples of 4).  Errors: as brsmooth_create_batched; BRS_ERR_ARG for a
+ * null, out-of-range, asymmetric or face-mismatched table or a dim < 2.
  */
 int brsmooth_create_level(int npatch, const int* dims, const int* nbr,
                           const brs_params* common, brs_ctx** out);

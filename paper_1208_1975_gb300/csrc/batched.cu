@@ -62,12 +62,15 @@ struct BatchState {
     cudaStream_t cap = nullptr; // private capture stream
     std::vector<Graph> graphs;
     bool async = false;         // cp.async kernel (every patch row is 16-byte aligned)
-    // level of patches (ghost exchange between face neighbours after every step)
+    // level of patches (ghost values from the face neighbours, refreshed after every step)
     bool level = false;
     int* d_nbr = nullptr;        // 6 per patch: -x, +x, -y, +y, -z, +z neighbour or -1
     int* d_chunk_patch = nullptr; // boundary-cell chunk -> patch
     int nchunks = 0;
     void* ghost = nullptr;       // ghost blocks of every patch (neighbours' face layers)
+    void* ghost2 = nullptr;      // the second ghost buffer (written during a step, read by the next)
+    long long* d_push = nullptr; // 6 per patch: where each face goes in a ghost buffer, or -1
+    bool push = true;            // steps after a call's first write their faces themselves
     int stages = 4;             // its ring depth (z-steps of lookahead per warp)
 };
 
@@ -89,8 +92,8 @@ constexpr size_t async_ring_bytes(int stages, size_t esize, bool level)
     return (size_t)stages * kFields * 32 * kE * esize + (level ? xg_bytes(esize) : 0);
 }
 
-// Ghost block of a patch of a level (the face neighbours' adjacent layers, copied before
-// every step; zero on the physical boundary), at g0 in the ghost array: the z- and z+ faces
+// Ghost block of a patch of a level (the face neighbours' adjacent layers as they were before
+// the step; zero on the physical boundary), at g0 in a ghost array: the z- and z+ faces
 // ([j][i], nx*ny each), the y- and y+ faces ([k][i], nx*nz), the x- and x+ faces ([k][j],
 // ny*nz), each face starting on a multiple of 4 elements.
 __host__ __device__ __forceinline__ long long round4(long long v) { return (v + 3) & ~3ll; }
@@ -129,6 +132,72 @@ __device__ __forceinline__ const T* ghost_x(const PatchDesc& d, const T* ghost, 
 {
     const long long A = round4((long long)d.nx * d.ny), Bz = round4((long long)d.nx * d.nz);
     return ghost + d.g0 + 2 * A + 2 * Bz + j + (long long)d.ny * k;
+}
+
+// Level contexts, steps after the first of a call: once a work item's lines are stored, the
+// warp copies the item's cells that lie on a patch face into the ghost block of the face
+// neighbour, in the ghost buffer that the next step reads (the current step reads the other
+// one, so every patch still sees its neighbours' values of the previous step).  Every cell
+// is written once per step, so the values are final; they are re-read from the output (just
+// written by this warp, L2-resident).  push[f] is the offset of the destination face in that
+// buffer, -1 where face f has no neighbour; destination layouts: z faces [j][i], y faces
+// [k][i], x faces [k][j].  Not inlined and kept small, with nothing of it in the step loop:
+// the loop keeps its registers (changes there cost more than the copy saves); the item is
+// re-read here.
+template <typename T>
+__device__ __noinline__ void push_item(const PatchDesc* __restrict__ desc,
+                                       const long long* __restrict__ push_all, T* gnext,
+                                       const T* uout, int pq, int item, int KC)
+{
+    __syncwarp();  // the item's stores by every lane of the warp are visible to all lanes
+    const PatchDesc d = desc[pq];
+    const long long* push = push_all + 6 * pq;
+    const int local = item - d.item0;
+    const int R = 32 / (4 << d.cls);
+    const int j0 = (local % d.njb) * R, k0 = (local / d.njb) * KC;
+    const int k1 = min(d.nz, k0 + KC);
+    const T* uo = uout + d.off;
+    const int lane = threadIdx.x & 31;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const long long plane = (long long)nx * ny;
+    const int nj = min(R, ny - j0), nk = k1 - k0;
+    for (int f = 0; f < 2; ++f) {  // x faces: the item's cells at x = 0 and x = nx - 1
+        const long long o = __ldg(push + f);
+        if (o < 0)
+            continue;
+        const int xi = f ? nx - 1 : 0;
+        for (int t = lane; t < nj * nk; t += 32) {
+            const int kk = t / nj, jl = t - kk * nj;
+            const int j = j0 + jl, k = k0 + kk;
+            gnext[o + j + (long long)ny * k] = uo[k * plane + (long long)j * nx + xi];
+        }
+    }
+    for (int f = 2; f < 4; ++f) {  // y faces: line 0 or ny - 1, when the item holds it
+        const int j = f == 2 ? 0 : ny - 1;
+        if (j < j0 || j >= j0 + nj)
+            continue;
+        const long long o = __ldg(push + f);
+        if (o < 0)
+            continue;
+        for (int t = lane; t < nk * nx; t += 32) {
+            const int kk = t / nx, i = t - kk * nx;
+            const int k = k0 + kk;
+            gnext[o + (long long)k * nx + i] = uo[k * plane + (long long)j * nx + i];
+        }
+    }
+    for (int f = 4; f < 6; ++f) {  // z faces: plane 0 or nz - 1, when the item holds it
+        const int k = f == 4 ? 0 : nz - 1;
+        if (k < k0 || k >= k1)
+            continue;
+        const long long o = __ldg(push + f);
+        if (o < 0)
+            continue;
+        for (int t = lane; t < nj * nx; t += 32) {
+            const int jl = t / nx, i = t - jl * nx;
+            const int j = j0 + jl;
+            gnext[o + (long long)j * nx + i] = uo[k * plane + (long long)j * nx + i];
+        }
+    }
 }
 
 template <typename T, int G, bool GS, bool LV>
@@ -275,6 +344,13 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
                  "r"(src_bytes)
                  : "memory");
 }
+// 4-byte variant (through L1), for the staged x ghosts of a level
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -341,38 +417,61 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
             return gyp ? gyp + (long long)kk * nx : nullptr;
         return nullptr;
     };
-    auto copy_line = [&](int slot, int f, const T* src, int jj, int kk) {
-        const T* row = row_of(src, jj, kk);
+    auto copy_row = [&](int slot, int f, const T* row) {
         const bool ok = xin && row;
-        const T* p = ok ? row + x0 : src;
+        const T* p = ok ? row + x0 : ub;
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             cp_async16(ring0 + soff(slot, f, c), p + c * (16 / sizeof(T)), ok ? 16u : 0u);
     };
+    auto copy_line = [&](int slot, int f, const T* src, int jj, int kk) {
+        copy_row(slot, f, row_of(src, jj, kk));
+    };
     // x ghosts of the line (level contexts): the lanes holding x = 0 and x = nx - 1
     const bool xlo = LV && xin && jin && x0 == 0;
     const bool xhi = LV && xin && jin && x0 <= nx - 1 && nx - 1 < x0 + kE;
-    // the item's x ghosts, staged once: xg[face][k - k0][line in the warp]
+    // the item's x ghosts, staged once: xg[face][k - k0][line in the warp], copied
+    // asynchronously with the first step's inputs (zero beyond the last line)
     T* xg = reinterpret_cast<T*>(ring + (size_t)D * kFields * 32 * kE * sizeof(T));
     if (LV) {
         const long long xpo = round4((long long)ny * nz);
         const int nk = k1 - k0;
+        const uint32_t xg0 = (uint32_t)__cvta_generic_to_shared(xg);
         for (int idx = lanew; idx < 2 * nk * R; idx += 32) {
             const int face = idx / (nk * R), rem = idx - face * nk * R;
             const int kk = rem / R, jl = rem - kk * R;
             const int jj = jb * R + jl;
-            xg[(face * kMaxKC + kk) * 8 + jl] =
-                jj < ny ? ghost_x(d, ghost, jj, k0 + kk)[face ? xpo : 0] : T(0);
+            const bool ok = jj < ny;
+            const T* src = ok ? ghost_x(d, ghost, jj, k0 + kk) + (face ? xpo : 0) : ghost;
+            cp_async4(xg0 + (uint32_t)(((face * kMaxKC + kk) * 8 + jl) * sizeof(T)), src,
+                      ok ? 4u : 0u);
         }
-        __syncwarp();
     }
     auto issue = [&](int kk, int slot) {
-        copy_line(slot, 0, ub, j, kk + 1);
-        copy_line(slot, 1, bb, j, kk);
-        if (g == 0)
-            copy_line(slot, 2, ub, j - 1, kk);
-        if (g == R - 1)
-            copy_line(slot, 3, ub, j + 1, kk);
+        if constexpr (LV) {
+            // the rows this step can need outside the patch are known per field: u(k+1)
+            // crosses the z+ face on the last plane, the halo lines cross the y faces, and
+            // line ny (past the patch, in the last y-block) carries the y+ ghost row that
+            // its neighbour ny - 1 takes by shuffle
+            const T* in = ub + (long long)kk * plane + (long long)j * nx;
+            copy_row(slot, 0, kk + 1 < nz ? (jin ? in + plane
+                                                 : (j == ny && gyp ? gyp + (long long)(kk + 1) * nx
+                                                                   : nullptr))
+                                          : gzp);
+            copy_row(slot, 1, jin ? bb + (in - ub) : nullptr);
+            if (g == 0)
+                copy_row(slot, 2, j > 0 ? in - nx : (gym ? gym + (long long)kk * nx : nullptr));
+            if (g == R - 1)
+                copy_row(slot, 3, j + 1 < ny ? in + nx
+                                             : (j + 1 == ny && gyp ? gyp + (long long)kk * nx : nullptr));
+        } else {
+            copy_line(slot, 0, ub, j, kk + 1);
+            copy_line(slot, 1, bb, j, kk);
+            if (g == 0)
+                copy_line(slot, 2, ub, j - 1, kk);
+            if (g == R - 1)
+                copy_line(slot, 3, ub, j + 1, kk);
+        }
     };
     auto read = [&](int slot, int f, T (&v)[kE]) {
 #pragma unroll
@@ -402,6 +501,10 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
         if (k0 + i < k1)
             issue(k0 + i, i);
         cp_async_commit();
+    }
+    if (LV) {  // the x ghosts (first group) have landed and every lane sees them
+        cp_async_wait<D - 1>();
+        __syncwarp();
     }
     int slot = 0;
     for (int k = k0; k < k1; ++k) {
@@ -448,6 +551,7 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
             for (int c = 0; c < CH; ++c)
                 reinterpret_cast<float4*>(p)[c] = reinterpret_cast<const float4*>(v)[c];
         }
+
 #pragma unroll
         for (int q = 0; q < kE; ++q) {
             um[q] = GS ? ((xin && jin) ? v[q] : T(0)) : uc[q];
@@ -471,7 +575,9 @@ __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __r
                                                             const T* __restrict__ b,
                                                             const T* __restrict__ tab,
                                                             double ax, double ay, double az,
-                                                            double om1, const T* ghost)
+                                                            double om1, const T* ghost,
+                                                            T* gnext,
+                                                            const long long* __restrict__ push)
 {
     extern __shared__ __align__(16) unsigned char async_smem[];
     pdl_wait_trigger();
@@ -485,7 +591,8 @@ __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __r
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems)
             return;
-        const PatchDesc d = desc[item_patch[item]];
+        const int pq = item_patch[item];
+        const PatchDesc d = desc[pq];
         const int local = item - d.item0;
         const int jb = local % d.njb, kc = local / d.njb;
         switch (d.cls) {
@@ -494,6 +601,8 @@ __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __r
         case 2: batched_item_async<T, 16, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
         default: batched_item_async<T, 32, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
         }
+        if (LV && gnext)
+            push_item<T>(desc, push, gnext, uout, item_patch[item], item, KC);
     }
 }
 
@@ -563,7 +672,9 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
                                                            const T* __restrict__ b,
                                                            const T* __restrict__ tab,
                                                            double ax, double ay, double az,
-                                                           double om1, const T* ghost)
+                                                           double om1, const T* ghost,
+                                                           T* gnext,
+                                                           const long long* __restrict__ push)
 {
     pdl_wait_trigger();
     const int lanew = threadIdx.x & 31;
@@ -574,7 +685,8 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems)
             return;
-        const PatchDesc d = desc[item_patch[item]];
+        const int pq = item_patch[item];
+        const PatchDesc d = desc[pq];
         const int local = item - d.item0;
         const int jb = local % d.njb, kc = local / d.njb;
         switch (d.cls) {
@@ -583,6 +695,8 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
         case 2: batched_item<T, 16, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
         default: batched_item<T, 32, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
         }
+        if (LV && gnext)
+            push_item<T>(desc, push, gnext, uout, item_patch[item], item, KC);
     }
 }
 
@@ -679,7 +793,7 @@ int ensure_counters(BatchState* B, int n)
 }
 
 int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* counter,
-               cudaStream_t s)
+               cudaStream_t s, const void* ghost = nullptr, void* gnext = nullptr)
 {
     BatchState* B = bs(c);
     const bool gs = c->p.method == BRS_CHAOTIC_GS;
@@ -692,13 +806,16 @@ int launch_one(brs_ctx* c, const void* uin, void* uout, const void* b, int* coun
     int nitems = B->nitems, KC = B->KC;
     const void* tab = B->d_tab;
     double ax = c->p.ax, ay = c->p.ay, az = c->p.az, om1 = 1.0 - c->omega;
-    const void* ghost = B->ghost;  // null unless the context is a level
+    // ghost: the buffer this step reads (null unless the context is a level); gnext: the
+    // one its face pushes go to (null: no pushes)
+    const long long* push = B->d_push;
     void* args[] = {(void*)&desc, (void*)&ip, &nitems, &counter, &KC, (void*)&uin, &uout,
-                    (void*)&b, (void*)&tab, &ax, &ay, &az, &om1, (void*)&ghost};
+                    (void*)&b, (void*)&tab, &ax, &ay, &az, &om1, (void*)&ghost, &gnext,
+                    (void*)&push};
     return brs_cuda_status(launch_pdl_c(k, dim3(B->grid), dim3(B->warps * 32), smem, s, args));
 }
 
-int level_exchange(brs_ctx* c, const void* u, cudaStream_t s)
+int level_exchange(brs_ctx* c, const void* u, void* ghost, cudaStream_t s)
 {
     BatchState* B = bs(c);
     const PatchDesc* desc = B->d_desc;
@@ -707,10 +824,10 @@ int level_exchange(brs_ctx* c, const void* u, cudaStream_t s)
     cudaError_t e;
     if (c->p.dtype == BRS_F64)
         e = launch_pdl(level_exchange_kernel<double>, dim3(B->nchunks), dim3(256), 0, s, desc, cp,
-                       nb, static_cast<const double*>(u), static_cast<double*>(B->ghost));
+                       nb, static_cast<const double*>(u), static_cast<double*>(ghost));
     else
         e = launch_pdl(level_exchange_kernel<float>, dim3(B->nchunks), dim3(256), 0, s, desc, cp,
-                       nb, static_cast<const float*>(u), static_cast<float*>(B->ghost));
+                       nb, static_cast<const float*>(u), static_cast<float*>(ghost));
     return brs_cuda_status(e);
 }
 
@@ -726,11 +843,20 @@ int enqueue_sweeps(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t
     void* nxt = gs ? u : c->scratch;
     int rc = BRS_OK;
     for (int k = 0; k < nsweeps && rc == BRS_OK; ++k) {
-        // a level first refreshes its ghost layer from the iterate before the step
-        if (B->level)
-            rc = level_exchange(c, cur, s);
+        void* gcur = nullptr;
+        void* gnext = nullptr;
+        if (B->level) {
+            // the call's first step gathers its ghost layer from the iterate; every step
+            // but the last then writes the next step's ghosts as it computes its faces
+            // (two buffers, alternating)
+            gcur = (B->push && (k & 1)) ? B->ghost2 : B->ghost;
+            if (!B->push || k == 0)
+                rc = level_exchange(c, cur, gcur, s);
+            if (B->push && k + 1 < nsweeps)
+                gnext = (k & 1) ? B->ghost : B->ghost2;
+        }
         if (rc == BRS_OK)
-            rc = launch_one(c, cur, nxt, b, B->d_counters + k, s);
+            rc = launch_one(c, cur, nxt, b, B->d_counters + k, s, gcur, gnext);
         if (!gs)
             std::swap(cur, nxt);
     }
@@ -984,6 +1110,35 @@ int level_setup(brs_ctx* c, const int* nbr)
         e = cudaMalloc(&B->ghost, (size_t)gtotal * c->esize);
     if (e == cudaSuccess)
         e = cudaMemset(B->ghost, 0, (size_t)gtotal * c->esize);
+    // face pushes: patch p's face f lands in the opposite ghost face of neighbour q
+    // (x- -> q's x+, x+ -> q's x-, and so on); physical-boundary ghosts stay zero in both
+    // buffers because nothing writes them
+    B->push = env_int("BRSMOOTH_LEVEL_PUSH", 1) != 0 && gtotal < (1ll << 31);
+    if (B->push) {
+        std::vector<long long> push(6 * (size_t)B->npatch, -1);
+        for (int p = 0; p < B->npatch; ++p)
+            for (int f = 0; f < 6; ++f) {
+                const int q = nbr[6 * p + f];
+                if (q < 0)
+                    continue;
+                const PatchDesc& d = B->h_desc[q];
+                const long long A = round4((long long)d.nx * d.ny);
+                const long long Bz = round4((long long)d.nx * d.nz);
+                const long long C = round4((long long)d.ny * d.nz);
+                const long long face[6] = {2 * A + 2 * Bz + C, 2 * A + 2 * Bz, 2 * A + Bz,
+                                           2 * A, A, 0};
+                push[6 * (size_t)p + f] = d.g0 + face[f];
+            }
+        if (e == cudaSuccess)
+            e = cudaMalloc(&B->ghost2, (size_t)gtotal * c->esize);
+        if (e == cudaSuccess)
+            e = cudaMemset(B->ghost2, 0, (size_t)gtotal * c->esize);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&B->d_push, sizeof(long long) * push.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_push, push.data(), sizeof(long long) * push.size(),
+                           cudaMemcpyHostToDevice);
+    }
     return brs_cuda_status(e);
 }
 
@@ -995,7 +1150,8 @@ void batched_teardown(brs_ctx* c)
     for (auto& g : B->graphs)
         cudaGraphExecDestroy(g.exec);
     for (void* q : {(void*)B->d_desc, (void*)B->d_item_patch, B->d_tab, (void*)B->d_counters,
-                    (void*)B->d_nbr, (void*)B->d_chunk_patch, B->ghost})
+                    (void*)B->d_nbr, (void*)B->d_chunk_patch, B->ghost, B->ghost2,
+                    (void*)B->d_push})
         if (q)
             cudaFree(q);
     if (B->cap)

@@ -19,7 +19,9 @@ COEFFS = [(1.0, 1.0, 1.0), (1.0, 0.1, 0.01)]
 # per axis (two-colour passes of unequal size), boxes with bx not a multiple of 4
 CASES = [((40, 24, 16), (4, 4, 4)), ((64, 32, 24), (8, 8, 8)), ((64, 64, 32), (8, 4, 4)),
          ((36, 20, 12), (4, 2, 2)), ((30, 18, 10), (2, 2, 2)), ((24, 18, 15), (6, 3, 5)),
-         ((9, 7, 5), (1, 1, 1)), ((48, 8, 8), (48, 1, 1)), ((12, 12, 3), (12, 12, 1))]
+         ((9, 7, 5), (1, 1, 1)), ((48, 8, 8), (48, 1, 1)), ((12, 12, 3), (12, 12, 1)),
+         # y-lines and z-lines (the blocks for y- or z-dominant coefficients)
+         ((10, 40, 6), (1, 40, 1)), ((6, 9, 36), (1, 1, 36))]
 
 
 @pytest.fixture(scope="module")
@@ -124,6 +126,27 @@ def test_box_converges_fp64(brs, orc):
         ctx.sweep(ut, bt, 700)  # the oracle's two-colour GS reaches 1e-11 after 623
         got = to_np(ut)
     assert rel_max_err(got, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("a,box", [((0.01, 1.0, 0.01), (1, 32, 1)), ((0.01, 0.01, 1.0), (1, 1, 32))],
+                         ids=["y_dominant", "z_dominant"])
+def test_lines_along_the_strong_coupling_converge_faster(brs, orc, a, box):
+    """Strongly anisotropic coefficients: lines along the dominant direction (1 x 32 x 1 or
+    1 x 1 x 32 boxes) contract the residual far faster than x-lines, as the oracle's ten-sweep
+    ratios on the same input show; the GPU ratios match the oracle's."""
+    n = 32
+    u, b = inputs((n, n, n), "f64")
+    b = np.zeros_like(b)
+    r0 = orc.residual_norm(u, b, a)
+    ratios = {}
+    for blk in (box, (n, 1, 1)):
+        got = gpu_sweeps(brs, u, b, a, blk, dt="f64", method="jacobi", nsweeps=10)[-1]
+        ref = u
+        for _ in range(10):
+            ref = orc.sweep(ref, b, a, block="box", box=blk, method="jacobi", omega=0.8)
+        ratios[blk] = orc.residual_norm(got, b, a) / r0
+        assert abs(ratios[blk] - orc.residual_norm(ref, b, a) / r0) <= 1e-10
+    assert ratios[box] < 0.05 * ratios[(n, 1, 1)], ratios
 
 
 @pytest.mark.parametrize("bn", ["0", "256"], ids=["tileN128", "tileN256"])

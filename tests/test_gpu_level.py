@@ -70,17 +70,42 @@ def test_level_jacobi_parity(brs, orc, name, dt):
         prev = got[k]  # per-sweep parity from the device's own iterate
 
 
-def test_level_multi_sweep_call_matches_single_calls(brs):
-    dims, nbr = LAYOUTS["tiled2x2x2"]
+@pytest.mark.parametrize("name", list(LAYOUTS))
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_level_multi_sweep_call_matches_single_calls(brs, name, dt):
+    """Within one call, steps after the first take their ghosts from the faces the previous
+    step wrote directly into the second ghost buffer; across calls, from the gather of the
+    iterate.  Both give the same level Jacobi iterate, bit for bit."""
+    dims, nbr = LAYOUTS[name]
     n = int(np.prod(dims, axis=1).sum())
-    u = rounded(uniform_field((n,), 33), "f32")
-    b = rounded(uniform_field((n,), 34) * 1e-3, "f32")
-    one = run_level(brs, dims, nbr, u, b, (1, 1, 1), "f32", 4)[-1]
-    with brs.BatchedContext(dims, (1, 1, 1), method="jacobi", dtype="f32", nbr=nbr) as ctx:
-        ut, bt = to_dev(u, "f32"), to_dev(b, "f32")
+    u = rounded(uniform_field((n,), 33), dt)
+    b = rounded(uniform_field((n,), 34) * 1e-3, dt)
+    one = run_level(brs, dims, nbr, u, b, (1.0, 0.5, 0.25), dt, 4)[-1]
+    with brs.BatchedContext(dims, (1.0, 0.5, 0.25), method="jacobi", dtype=dt, nbr=nbr) as ctx:
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
         ctx.sweep(ut, bt, 4)
         four = to_np(ut)
+        assert brs.brsmooth_last_error(ctx.h) == 0
     assert np.array_equal(one, four)
+
+
+@pytest.mark.parametrize("push", ["0", "1"], ids=["gather_every_step", "face_push"])
+def test_paper_level_three_steps_per_call(brs, push, monkeypatch):
+    """The 96 x 64^3 level, FP32 Jacobi, three steps in one call (the launch sequence the
+    benchmark times, with and without the face pushes) equals three single-step calls."""
+    monkeypatch.setenv("BRSMOOTH_LEVEL_PUSH", push)
+    P, pdim = (4, 4, 6), (64, 64, 64)
+    dims, nbr = tiling(P, pdim)
+    n = 96 * 64 ** 3
+    u = rounded(uniform_field((n,), 37), "f32")
+    b = rounded(uniform_field((n,), 38) * (1.0 / 65) ** 2, "f32")
+    one = run_level(brs, dims, nbr, u, b, (1, 1, 1), "f32", 3)[-1]
+    with brs.BatchedContext(dims, (1, 1, 1), method="jacobi", dtype="f32", nbr=nbr) as ctx:
+        ut, bt = to_dev(u, "f32"), to_dev(b, "f32")
+        ctx.sweep(ut, bt, 3)
+        three = to_np(ut)
+        assert brs.brsmooth_last_error(ctx.h) == 0
+    assert np.array_equal(one, three)
 
 
 def test_level_gs_converges_to_global_solution(brs, orc):

@@ -7,7 +7,9 @@ inverse computed once as in Sec. 4.3) against what mathematics fixes independent
 * A grid that is one block: one sweep with omega = 1 is the exact solve (DST-I closed form).
 * 1x1x1 blocks: point Jacobi, whose damping of a sine mode has a closed form.
 * nx x 1 x 1 and nx x ny x 1 boxes equal the x-line and xy-plane blocks, which the oracle
-  solves by other algorithms (Thomas, banded Cholesky).
+  solves by other algorithms (Thomas, banded Cholesky); 1 x ny x 1 and 1 x 1 x nz boxes (y-
+  and z-lines, the blocks for other anisotropies) equal x-line sweeps of the grid with its
+  axes permuted and the coefficients permuted with them.
 * Convergence to A^{-1} b, and the Sec. 3 observation that a larger block lowers
   ||r_3|| / ||r_0|| from a random initial guess, over the paper's seven block sizes.
 """
@@ -158,6 +160,27 @@ def test_box_equals_line_and_plane(orc, method, a):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (box, block)
 
 
+@pytest.mark.parametrize("method", ["jacobi", "gs_lex", "gs_reverse", "gs_zebra"])
+@pytest.mark.parametrize("a", COEFFS + [(0.01, 1.0, 0.1)])
+def test_y_and_z_line_boxes_are_permuted_x_lines(orc, method, a):
+    """A 1 x ny x 1 box is an x-line of the grid with x and y exchanged; a 1 x 1 x nz box an
+    x-line of the grid whose axes (x, y, z) become (z, x, y).  Both permutations keep the
+    visiting order (block index i fastest) and the two-colour parity i + j + k."""
+    nx, ny, nz = 5, 7, 6
+    u0 = initial_guess((nz, ny, nx))
+    b = rhs((nz, ny, nx))
+    om = 0.8 if method == "jacobi" else 1.0
+    ax, ay, az = a
+    got = orc.sweep(u0, b, a, block="box", box=(1, ny, 1), method=method, omega=om)
+    ref = orc.sweep(u0.transpose(0, 2, 1).copy(), b.transpose(0, 2, 1).copy(), (ay, ax, az),
+                    block="line", method=method, omega=om).transpose(0, 2, 1)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), "y-lines"
+    got = orc.sweep(u0, b, a, block="box", box=(1, 1, nz), method=method, omega=om)
+    ref = orc.sweep(u0.transpose(1, 2, 0).copy(), b.transpose(1, 2, 0).copy(), (az, ax, ay),
+                    block="line", method=method, omega=om).transpose(2, 0, 1)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), "z-lines"
+
+
 @pytest.mark.parametrize("method,omega,sweeps", [("jacobi", 0.8, 400), ("gs_zebra", 1.0, 200)])
 def test_box_converges_to_exact(orc, method, omega, sweeps):
     n = 8
@@ -187,6 +210,30 @@ def test_larger_blocks_smooth_more(orc, method, omega):
         ratios.append(orc.residual_norm(u, b, a) / r0)
     assert all(x > y for x, y in zip(ratios, ratios[1:])), ratios
     assert ratios[0] < 0.05  # three sweeps already reduce the residual 20-fold
+
+
+@pytest.mark.parametrize("block,box", [("box", (1, 1, 1)), ("line", None), ("plane", None)])
+def test_asymptotic_factor_is_slowest_sine_mode(orc, block, box):
+    """Sec. 3's sliding-window factor (||r_{i+k}|| / ||r_i||)^(1/k) for block Jacobi
+    (omega = 0.8) with point, x-line and xy-plane blocks: every sine mode e_pqr is an
+    eigenvector, with factor 1 - omega lambda_pqr / mu (mu = the block operator's eigenvalue
+    on that mode), and the slowest one is (1,1,1); on a 10^3 grid after 600 sweeps the other
+    modes have died out to 1e-6."""
+    n, i, k = 10, 600, 50
+    a = (1.0, 1.0, 1.0)
+    s1 = 2 - 2 * np.cos(np.pi / (n + 1))
+    mu = {"box": 6.0, "line": s1 + 4, "plane": 2 * s1 + 2}[block]
+    g = 1 - 0.8 * 3 * s1 / mu
+    u = initial_guess((n, n, n))
+    b = np.zeros_like(u)
+    kw = {"box": box} if box else {}
+    for _ in range(i):
+        u = orc.sweep(u, b, a, block=block, method="jacobi", omega=0.8, **kw)
+    ri = orc.residual_norm(u, b, a)
+    for _ in range(k):
+        u = orc.sweep(u, b, a, block=block, method="jacobi", omega=0.8, **kw)
+    fac = (orc.residual_norm(u, b, a) / ri) ** (1.0 / k)
+    assert abs(fac - g) <= 1e-6, (fac, g)
 
 
 def test_box_must_tile_grid(orc):
