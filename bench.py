@@ -566,6 +566,10 @@ VARIANTS = {
     "plane_jacobi_f32_tf32": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 4, 10, "tf32"),
     "plane_jacobi_f32_simt": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 2, 10, "simt"),
     "plane_jacobi_f64": ("plane", "jacobi", "f64", (1.0, 1.0, 0.01), 1, 4, "auto"),
+    # y- and z-lines (x-line sweeps of the permuted grid; three grid passes per call)
+    "yline_jacobi_f32": ("yline", "jacobi", "f32", (0.01, 1.0, 0.01), 6, 50, "auto"),
+    "zline_jacobi_f32": ("zline", "jacobi", "f32", (0.01, 0.01, 1.0), 6, 50, "auto"),
+    "zline_gs_f32": ("zline", "gs", "f32", (0.01, 0.01, 1.0), 6, 50, "auto"),
 }
 BOX_VARIANTS = {
     # name: (method, dtype, box, steps, sweeps per step, math); a = (1, 1, 1)
@@ -576,7 +580,8 @@ BOX_VARIANTS = {
     "box_jacobi_f32_4cubed_3xtf32": ("jacobi", "f32", (4, 4, 4), 4, 10, "3xtf32"),
     "box_gs_f64_8cubed": ("gs", "f64", (8, 8, 8), 1, 2, "auto"),
     "box_gs_f64_4cubed": ("gs", "f64", (4, 4, 4), 1, 5, "auto"),
-    # y- and z-lines as 1 x 256 x 1 and 1 x 1 x 256 boxes (blocks for other anisotropies)
+    # y- and z-lines as 1 x 256 x 1 and 1 x 1 x 256 boxes (dense inverse applied per line;
+    # the line blocks themselves are the yline / zline variants)
     "box_jacobi_f32_yline_3xtf32": ("jacobi", "f32", (1, 256, 1), 4, 10, "3xtf32"),
     "box_jacobi_f32_zline_3xtf32": ("jacobi", "f32", (1, 1, 256), 4, 10, "3xtf32"),
 }

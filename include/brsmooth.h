@@ -54,6 +54,8 @@ extern "C" {
 #define BRS_XLINE 0
 #define BRS_XYPLANE 1
 #define BRS_BOX 2 /* bx*by*bz spatial blocks with one precomputed inverse (Sec. 2, Sec. 4.3) */
+#define BRS_YLINE 3 /* lines along y: the blocks for y-dominant coefficients */
+#define BRS_ZLINE 4 /* lines along z: the blocks for z-dominant coefficients */
 
 /* Update scheme between blocks. */
 #define BRS_JACOBI 0     /* damped block Jacobi, paper default omega = 0.8 (Sec. 2.1) */
@@ -74,7 +76,7 @@ typedef struct brs_ctx brs_ctx; /* opaque; owned by the library */
 typedef struct brs_params {
     int nx, ny, nz;     /* interior cells per axis, each >= 1 */
     double ax, ay, az;  /* stencil coefficients, each > 0 and finite */
-    int block;          /* BRS_XLINE, BRS_XYPLANE or BRS_BOX */
+    int block;          /* BRS_XLINE, BRS_XYPLANE, BRS_BOX, BRS_YLINE or BRS_ZLINE */
     int method;         /* BRS_JACOBI or BRS_CHAOTIC_GS */
     int dtype;          /* BRS_F64 or BRS_F32 */
     double omega;       /* relaxation weight in (0, 2); <= 0 selects the paper default */
@@ -99,6 +101,14 @@ typedef struct brs_params {
  * inverse then serves every box, Sec. 4.3).  BRS_PLANE_AUTO selects FP64 CUDA-core math
  * for BRS_F64 and, for BRS_F32, split-TF32 tensor cores when bx*by*bz is a multiple of 4
  * and >= 32, else FP32 CUDA cores.
+ * y-line and z-line blocks (BRS_YLINE, BRS_ZLINE): the full-extent lines along y or z,
+ * solved exactly.  A y-line (z-line) sweep is the x-line sweep of the grid with its axes
+ * permuted to (y, x, z) ((z, x, y)) and the coefficients permuted with them, so the
+ * context holds an x-line context of that grid and two permuted grid copies (u and b,
+ * plus the inner context's Jacobi buffer).  Each brsmooth_sweep call permutes u and b in,
+ * runs all its sweeps, and permutes u back: three grid passes per call, whatever nsweeps.
+ * Chaotic GS visits the lines in the permuted order.  Limits: the line length (ny or nz)
+ * as for x-lines, and nz <= 65535 (y-lines) or ny <= 65535 (z-lines).
  */
 int brsmooth_create(const brs_params* p, brs_ctx** out);
 

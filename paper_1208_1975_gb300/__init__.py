@@ -24,12 +24,13 @@ BRS_ERR_NOMEM = -4
 BRS_ERR_TIMEOUT = -5
 BRS_ERR_BOUNDS = -6
 
-BRS_XLINE, BRS_XYPLANE, BRS_BOX = 0, 1, 2
+BRS_XLINE, BRS_XYPLANE, BRS_BOX, BRS_YLINE, BRS_ZLINE = 0, 1, 2, 3, 4
 BRS_JACOBI, BRS_CHAOTIC_GS = 0, 1
 BRS_F64, BRS_F32 = 0, 1
 BRS_PLANE_AUTO, BRS_PLANE_SIMT, BRS_PLANE_TF32, BRS_PLANE_3XTF32 = 0, 1, 2, 3
 
-BLOCKS = {"line": BRS_XLINE, "plane": BRS_XYPLANE, "box": BRS_BOX}
+BLOCKS = {"line": BRS_XLINE, "plane": BRS_XYPLANE, "box": BRS_BOX, "yline": BRS_YLINE,
+          "zline": BRS_ZLINE}
 METHODS = {"jacobi": BRS_JACOBI, "gs": BRS_CHAOTIC_GS, "chaotic_gs": BRS_CHAOTIC_GS}
 DTYPES = {"f64": BRS_F64, "f32": BRS_F32}
 PLANE_MATH = {"auto": BRS_PLANE_AUTO, "simt": BRS_PLANE_SIMT, "tf32": BRS_PLANE_TF32,

@@ -65,6 +65,8 @@ int poll_status(brs_ctx* c)
         if (*hs != 0)
             c->sticky = *hs;
     }
+    if (c->sticky == BRS_OK && c->perm)  // the permuted grid's kernels report there
+        c->sticky = poll_status(c->perm);
     return c->sticky;
 }
 
@@ -76,7 +78,8 @@ int validate(const brs_params* p)
         return BRS_ERR_ARG;
     if (!finite_pos(p->ax) || !finite_pos(p->ay) || !finite_pos(p->az))
         return BRS_ERR_ARG;
-    if (p->block != BRS_XLINE && p->block != BRS_XYPLANE && p->block != BRS_BOX)
+    if (p->block != BRS_XLINE && p->block != BRS_XYPLANE && p->block != BRS_BOX &&
+        p->block != BRS_YLINE && p->block != BRS_ZLINE)
         return BRS_ERR_ARG;
     if (p->block == BRS_BOX &&
         (p->bx < 1 || p->by < 1 || p->bz < 1 || p->nx % p->bx || p->ny % p->by || p->nz % p->bz))
@@ -95,6 +98,74 @@ int validate(const brs_params* p)
     return BRS_OK;
 }
 
+// y-line / z-line blocks: permutation of the axes that makes them x-lines.  Axis a of the
+// permuted grid is axis ax[a] of the grid (0 = x, 1 = y, 2 = z).
+void perm_axes(int block, int ax[3])
+{
+    if (block == BRS_YLINE) {
+        ax[0] = 1, ax[1] = 0, ax[2] = 2;  // (y, x, z)
+    } else {
+        ax[0] = 2, ax[1] = 0, ax[2] = 1;  // (z, x, y)
+    }
+}
+
+// Grid -> permuted grid (forward) or back.  y-lines: per plane k, [j][i] <-> [i][j];
+// z-lines: per row j, [k][i] (plane stride) <-> [i][k] (rows of nz at j nx nz).
+int permute(brs_ctx* c, const void* src, void* dst, bool forward, cudaStream_t s)
+{
+    const long long nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const int dt = c->p.dtype;
+    if (c->p.block == BRS_YLINE) {
+        if (forward)  // (r = j, c = i) -> i * ny + j
+            return transpose_launch(dt, src, dst, (int)ny, (int)nx, (int)nz, nx, nx * ny, ny,
+                                    nx * ny, s);
+        return transpose_launch(dt, src, dst, (int)nx, (int)ny, (int)nz, ny, nx * ny, nx,
+                                nx * ny, s);
+    }
+    if (forward)  // batch j: (r = k, c = i) at k nx ny + j nx + i -> j nx nz + i nz + k
+        return transpose_launch(dt, src, dst, (int)nz, (int)nx, (int)ny, nx * ny, nx, nz,
+                                nx * nz, s);
+    // batch j: (r = i, c = k) at j nx nz + i nz + k -> k nx ny + j nx + i
+    return transpose_launch(dt, src, dst, (int)nx, (int)nz, (int)ny, nz, nx * nz, nx * ny, nx,
+                            s);
+}
+
+int perm_setup(brs_ctx* c)
+{
+    const brs_params& p = c->p;
+    int ax[3];
+    perm_axes(p.block, ax);
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const double a[3] = {p.ax, p.ay, p.az};
+    if (n[ax[2]] > 65535)
+        return BRS_ERR_UNSUPPORTED;  // the permutation's batch count
+    brs_params q = p;
+    q.block = BRS_XLINE;
+    q.nx = n[ax[0]], q.ny = n[ax[1]], q.nz = n[ax[2]];
+    q.ax = a[ax[0]], q.ay = a[ax[1]], q.az = a[ax[2]];
+    int rc = brsmooth_create(&q, &c->perm);
+    if (rc != BRS_OK)
+        return rc;
+    cudaError_t e = cudaMalloc(&c->perm_u, (size_t)c->cells * c->esize);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->perm_b, (size_t)c->cells * c->esize);
+    return brs_cuda_status(e);
+}
+
+int perm_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s)
+{
+    if (nsweeps == 0)
+        return BRS_OK;
+    int rc = permute(c, u, c->perm_u, true, s);
+    if (rc == BRS_OK)
+        rc = permute(c, b, c->perm_b, true, s);
+    if (rc == BRS_OK)
+        rc = brsmooth_sweep(c->perm, c->perm_u, c->perm_b, nsweeps, s);
+    if (rc == BRS_OK)
+        rc = permute(c, c->perm_u, u, false, s);
+    return rc;
+}
+
 void free_ctx(brs_ctx* c)
 {
     if (!c)
@@ -104,6 +175,11 @@ void free_ctx(brs_ctx* c)
     box_teardown(c);
     batched_teardown(c);
     adjoint_teardown(c);
+    free_ctx(c->perm);
+    if (c->perm_u)
+        cudaFree(c->perm_u);
+    if (c->perm_b)
+        cudaFree(c->perm_b);
     if (c->scratch)
         cudaFree(c->scratch);
     if (c->partials)
@@ -213,11 +289,13 @@ int brsmooth_create(const brs_params* p, brs_ctx** out)
         rc = line_setup(c);
     else if (p->block == BRS_XYPLANE)
         rc = plane_setup(c);
-    else
+    else if (p->block == BRS_BOX)
         rc = box_setup(c);
+    else
+        rc = perm_setup(c);
     if (rc == BRS_OK)
         rc = residual_setup(c);
-    if (rc == BRS_OK && p->method == BRS_JACOBI) {
+    if (rc == BRS_OK && p->method == BRS_JACOBI && !c->perm) {
         e = cudaMalloc(&c->scratch, (size_t)c->cells * c->esize);
         rc = brs_cuda_status(e);
     }
@@ -259,6 +337,8 @@ int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream
     c->last_stream = s;
     if (c->batch)
         return batched_sweep(c, u, b, nsweeps, s);
+    if (c->perm)
+        return perm_sweep(c, u, b, nsweeps, s);
     if (c->p.method == BRS_CHAOTIC_GS) {
         for (int k = 0; k < nsweeps && rc == BRS_OK; ++k)
             rc = sweep_one(c, u, u, b, s);

@@ -77,6 +77,11 @@ struct brs_ctx {
     float* dc_c = nullptr;
     // adjoint-sweep state (owned by adjoint.cu)
     void* adjoint = nullptr;
+    // y-line / z-line blocks (api.cu): an x-line context of the permuted grid and the
+    // permuted copies of u and b it sweeps
+    brs_ctx* perm = nullptr;
+    void* perm_u = nullptr;
+    void* perm_b = nullptr;
 };
 
 // Status helpers -------------------------------------------------------------------------
@@ -98,6 +103,11 @@ int residual_launch_f32out(brs_ctx* c, const double* u, const double* b, float* 
                            cudaStream_t s);
 // ||x||_2^2 of a grid array (context dtype) into norm_dev.
 int norm2sq_launch(brs_ctx* c, const void* x, cudaStream_t s);
+
+// Axis permutation (transpose.cu) ------------------------------------------------------------
+// dst[b * db + c * dc + r] = src[b * sb + r * sr + c] for r < R, c < C, b < batch.
+int transpose_launch(int dtype, const void* src, void* dst, int R, int C, int batch,
+                     long long sr, long long sb, long long dc, long long db, cudaStream_t s);
 
 // Adjoint (adjoint.cu) ------------------------------------------------------------------------
 void adjoint_teardown(brs_ctx* c);

@@ -69,7 +69,7 @@ def test_strerror_and_null_handling(cuda_lib):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(ny=-1), dict(nz=0), dict(ax=0.0), dict(ay=-1.0), dict(az=float("nan")),
-    dict(ax=float("inf")), dict(block=3), dict(method=5), dict(dtype=3), dict(omega=2.0),
+    dict(ax=float("inf")), dict(block=5), dict(block=-1), dict(method=5), dict(dtype=3), dict(omega=2.0),
     dict(omega=float("nan")), dict(plane_math=9), dict(block=2),
     dict(block=2, bx=2, by=2, bz=0), dict(block=2, bx=3, by=2, bz=2),
     dict(block=2, bx=2, by=16, bz=2)])
