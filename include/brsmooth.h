@@ -144,6 +144,20 @@ int brsmooth_sweep_host(brs_ctx* c, void* u_host, const void* b_host, int nsweep
                         void* stream);
 
 /*
+ * brsmooth_sweep_host without the final synchronisation: the copies in, the sweeps and the
+ * copy of u back are enqueued on `stream` and the call returns.  u_host holds the result
+ * once the stream has reached that point (synchronise the stream or an event first), and
+ * neither host array may be touched before then.  With pinned host arrays the copies run
+ * asynchronously, so a caller with independent problems can keep two contexts on two
+ * streams and overlap one problem's copies with the other's sweeps.  Calls on one context
+ * must stay on one stream (its device buffers are reused in stream order).
+ * Errors: as brsmooth_sweep_host; a device status raised by the sweeps is reported by a
+ * later call or brsmooth_last_error.
+ */
+int brsmooth_sweep_host_async(brs_ctx* c, void* u_host, const void* b_host, int nsweeps,
+                              void* stream);
+
+/*
  * Release the context and every device resource it owns.  NULL is accepted (BRS_OK).
  * Synchronises the device work the context enqueued.
  */

@@ -77,6 +77,7 @@ def lib():
     L.brsmooth_sweep.argtypes = [P, P, P, I, P]
     L.brsmooth_residual.argtypes = [P, P, P, P, ctypes.POINTER(D), P]
     L.brsmooth_sweep_host.argtypes = [P, P, P, I, P]
+    L.brsmooth_sweep_host_async.argtypes = [P, P, P, I, P]
     L.brsmooth_destroy.argtypes = [P]
     L.brsmooth_last_error.argtypes = [P]
     L.brsmooth_strerror.argtypes = [I]
@@ -97,6 +98,7 @@ def lib():
     L.brsmooth_adjoint_sweep.argtypes = [P, P, P, P, P, P, P]
     L.brsmooth_adjoint_sweep.restype = I
     for name in ("brsmooth_create", "brsmooth_sweep", "brsmooth_residual", "brsmooth_sweep_host",
+                 "brsmooth_sweep_host_async",
                  "brsmooth_destroy", "brsmooth_last_error", "brsmooth_create_batched",
                  "brsmooth_sweep_batched", "brsmooth_batched_config"):
         getattr(L, name).restype = I
@@ -160,6 +162,11 @@ def brsmooth_residual(ctx, u_ptr, b_ptr, r_ptr, want_norm: bool, stream):
 
 def brsmooth_sweep_host(ctx, u_host_ptr, b_host_ptr, nsweeps: int, stream) -> int:
     return lib().brsmooth_sweep_host(ctx, u_host_ptr, b_host_ptr, int(nsweeps), ctypes.c_void_p(stream))
+
+
+def brsmooth_sweep_host_async(ctx, u_host_ptr, b_host_ptr, nsweeps: int, stream) -> int:
+    return lib().brsmooth_sweep_host_async(ctx, u_host_ptr, b_host_ptr, int(nsweeps),
+                                           ctypes.c_void_p(stream))
 
 
 def brsmooth_destroy(ctx) -> int:
@@ -255,8 +262,10 @@ class Context:
         _check(rc, "brsmooth_residual")
         return nrm if norm else None
 
-    def sweep_host(self, u_host, b_host, nsweeps: int = 1, stream=None):
-        """Sweeps on host arrays (numpy or CPU tensors, contiguous, context dtype), in place on u."""
+    def sweep_host(self, u_host, b_host, nsweeps: int = 1, stream=None, wait: bool = True):
+        """Sweeps on host arrays (numpy or CPU tensors, contiguous, context dtype), in place on
+        u.  wait=False only enqueues the copies and sweeps on `stream` (brsmooth_sweep_host_async):
+        u is valid, and both arrays may be touched again, once the stream has reached it."""
         import numpy as np
 
         def hptr(x, name):
@@ -273,8 +282,9 @@ class Context:
         want = "float64" if self.dtype_code == BRS_F64 else "float32"
         if un != self.cells or bn != self.cells or want not in ud or want not in bd:
             raise ValueError(f"host arrays need {self.cells} {want} elements")
-        rc = brsmooth_sweep_host(self.h, up, bp, nsweeps, _stream_handle(stream))
-        _check(rc, "brsmooth_sweep_host")
+        fn = brsmooth_sweep_host if wait else brsmooth_sweep_host_async
+        rc = fn(self.h, up, bp, nsweeps, _stream_handle(stream))
+        _check(rc, fn.__name__)
         return u_host
 
     def last_error(self) -> int:

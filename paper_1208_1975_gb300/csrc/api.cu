@@ -385,7 +385,8 @@ int brsmooth_residual(brs_ctx* c, const void* u, const void* b, void* r, double*
     return BRS_OK;
 }
 
-int brsmooth_sweep_host(brs_ctx* c, void* u_host, const void* b_host, int nsweeps, void* stream)
+static int sweep_host_enqueue(brs_ctx* c, void* u_host, const void* b_host, int nsweeps,
+                              cudaStream_t s)
 {
     if (!c || !u_host || !b_host || nsweeps < 0)
         return BRS_ERR_ARG;
@@ -397,21 +398,34 @@ int brsmooth_sweep_host(brs_ctx* c, void* u_host, const void* b_host, int nsweep
         e = cudaMalloc(&c->host_b_dev, bytes);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemcpyAsync(c->host_b_dev, b_host, bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->host_u_dev, u_host, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    int rc = brsmooth_sweep(c, c->host_u_dev, c->host_b_dev, nsweeps, stream);
+    int rc = brsmooth_sweep(c, c->host_u_dev, c->host_b_dev, nsweeps, s);
     if (rc != BRS_OK)
         return rc;
-    e = cudaMemcpyAsync(u_host, c->host_u_dev, bytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(s);
+    return brs_cuda_status(
+        cudaMemcpyAsync(u_host, c->host_u_dev, bytes, cudaMemcpyDeviceToHost, s));
+}
+
+int brsmooth_sweep_host(brs_ctx* c, void* u_host, const void* b_host, int nsweeps, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = sweep_host_enqueue(c, u_host, b_host, nsweeps, s);
+    if (rc != BRS_OK)
+        return rc;
+    cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
     return poll_status(c);
+}
+
+int brsmooth_sweep_host_async(brs_ctx* c, void* u_host, const void* b_host, int nsweeps,
+                              void* stream)
+{
+    return sweep_host_enqueue(c, u_host, b_host, nsweeps, static_cast<cudaStream_t>(stream));
 }
 
 int brsmooth_destroy(brs_ctx* c)

@@ -129,6 +129,37 @@ def test_host_buffer_path_matches_device_path(brs):
     assert np.array_equal(uh, dev)
 
 
+def test_async_host_path_on_two_streams(brs):
+    """Independent problems alternating over two contexts and two streams through the
+    asynchronous host entry point (the end-to-end benchmark's pattern): each result equals
+    the synchronous call's, bit for bit."""
+    import torch
+
+    shape = (16, 24, 32)
+    b = torch.from_numpy(rhs(shape)).pin_memory()
+    us = [torch.from_numpy(initial_guess(shape)).pin_memory(),
+          torch.from_numpy(0.5 * initial_guess(shape)).pin_memory()]
+    refs = []
+    for u in us:
+        with brs.Context(32, 24, 16, (1, 0.5, 0.25)) as ctx:
+            uh = u.clone()
+            ctx.sweep_host(uh, b, 7)
+            ctx.sweep_host(uh, b, 7)
+            refs.append(uh)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ctxs = [brs.Context(32, 24, 16, (1, 0.5, 0.25)) for _ in range(2)]
+    try:
+        for q in range(4):  # two calls per problem, enqueued without waiting
+            ctxs[q % 2].sweep_host(us[q % 2], b, 7, stream=streams[q % 2], wait=False)
+        torch.cuda.synchronize()
+        for q in range(2):
+            assert ctxs[q].last_error() == 0
+            assert torch.equal(us[q], refs[q])
+    finally:
+        for cx in ctxs:
+            cx.close()
+
+
 def test_argument_errors(brs):
     import torch
 
