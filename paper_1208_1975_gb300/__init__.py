@@ -334,6 +334,23 @@ def _adjoint_step(c: "Context", lam, u_k, b, gb, ga, stream=None):
     _check(rc, "brsmooth_adjoint_sweep")
 
 
+# Contexts of recent block_smooth shapes, most recent last: creating one allocates and
+# uploads tables (synchronising), so repeated calls with the same grid, coefficients and
+# dtype reuse it.  An evicted context is destroyed once no autograd graph holds it.
+_SMOOTH_CTX = {}
+
+
+def _smooth_context(nx, ny, nz, av, dt, omega):
+    key = (nx, ny, nz, av, dt, float(omega))
+    c = _SMOOTH_CTX.pop(key, None)
+    if c is None:
+        c = Context(nx, ny, nz, av, block="line", method="jacobi", dtype=dt, omega=omega)
+    _SMOOTH_CTX[key] = c
+    while len(_SMOOTH_CTX) > 2:
+        _SMOOTH_CTX.pop(next(iter(_SMOOTH_CTX)))
+    return c
+
+
 def _block_smooth_fn():
     import torch
 
@@ -350,7 +367,7 @@ def _block_smooth_fn():
             nz, ny, nx = b.shape
             dt = "f64" if b.dtype == torch.float64 else "f32"
             av = tuple(float(x) for x in a.detach().cpu().tolist())
-            c = Context(nx, ny, nz, av, block="line", method="jacobi", dtype=dt, omega=omega)
+            c = _smooth_context(nx, ny, nz, av, dt, omega)
             b = b.detach().contiguous()
             u = u0.detach().clone().contiguous()
             ckpt = max(1, int(ckpt))

@@ -11,6 +11,10 @@
 // blocks dM/dax = Tx, dM/day = dM/daz = 2 I.
 // One call performs these updates for one sweep; the caller supplies u_k (checkpointed
 // or recomputed) and runs the calls from the last sweep to the first.
+// The gradient terms only need z_k through x_k = u_k + z_k = M^{-1}(b + N u_k), the
+// undamped line-Jacobi iterate (A = M - N), which the x-line sweep kernel produces in one
+// pass: Tx (z + u) = Tx x, 2 z + Ty u = 2 x - Sy u, 2 z + Tz u = 2 x - Sz u, with S_d the
+// sum of the two neighbours along d (T_d = 2 I - S_d).
 #include "brs_internal.cuh"
 #include "line_impl.cuh"
 
@@ -23,7 +27,7 @@ constexpr int kThreads = 256;
 template <typename T, int E, int G>
 __global__ void __launch_bounds__(kThreads) line_minv_kernel(const T* in, T* out,
                                                              const T* __restrict__ tab, int nx,
-                                                             int ny, int nz)
+                                                             int ny, int nz, bool vec)
 {
     const int groups = blockDim.x / G;
     const long long line = (long long)blockIdx.x * groups + threadIdx.x / G;
@@ -35,57 +39,196 @@ __global__ void __launch_bounds__(kThreads) line_minv_kernel(const T* in, T* out
     constexpr int LG = brs::Log2<G>::value;
     const T* ptab = tab + 3 * NP + 2 * LG * G;
     const size_t base = (size_t)(active ? line : 0) * nx;
+    // VEC: full lines (nx = E G) with 16-byte aligned rows and E a whole number of 16-byte
+    // vectors: each lane moves its E cells as vectors of the element type
+    using V = typename brs::Vec16<T>::type;
+    constexpr int NV = (int)(E * sizeof(T) / 16);
+    constexpr bool CAN_VEC = (E * sizeof(T)) % 16 == 0;
     T r[E];
+    if (CAN_VEC && vec) {
+        const V* src = reinterpret_cast<const V*>(in + base + lane * E);
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-        const int x = lane * E + q;
-        r[q] = (active && x < nx) ? in[base + x] : T(0);
+        for (int m = 0; m < NV; ++m)
+            reinterpret_cast<V*>(r)[m] = active ? src[m] : V{};
+    } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int x = lane * E + q;
+            r[q] = (active && x < nx) ? in[base + x] : T(0);
+        }
     }
     brs::line_solve<T, E, G>(r, tb, lane);
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-        const int x = lane * E + q;
-        if (active && x < nx)
-            out[base + x] = ptab[lane * E + q] * r[q];
+    for (int q = 0; q < E; ++q)
+        r[q] = ptab[lane * E + q] * r[q];
+    if (CAN_VEC && vec) {
+        if (active) {
+            V* dst = reinterpret_cast<V*>(out + base + lane * E);
+#pragma unroll
+            for (int m = 0; m < NV; ++m)
+                dst[m] = reinterpret_cast<const V*>(r)[m];
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int x = lane * E + q;
+            if (active && x < nx)
+                out[base + x] = r[q];
+        }
+    }
+}
+
+// Four consecutive cells of a row (rem = cells left in the row); VEC: 16-byte vectors.
+template <typename T>
+__device__ __forceinline__ void ld4(T (&v)[4], const T* p, int rem, bool vec)
+{
+    if (vec) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 f = *reinterpret_cast<const float4*>(p);
+            v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+        } else {
+            const double2 f0 = reinterpret_cast<const double2*>(p)[0];
+            const double2 f1 = reinterpret_cast<const double2*>(p)[1];
+            v[0] = f0.x, v[1] = f0.y, v[2] = f1.x, v[3] = f1.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            v[q] = q < rem ? p[q] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4], int rem, bool vec)
+{
+    if (vec) {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+            reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < rem)
+                p[q] = v[q];
+    }
+}
+
+// Second-difference neighbour sums of four cells of row `row` (at p, j, k): x (within the
+// row), y and z.
+template <typename T>
+struct Nb4 {
+    T c[4], sx[4], sy[4], sz[4];
+};
+
+template <typename T>
+__device__ __forceinline__ void neighbours4(Nb4<T>& o, const T* p, int i0, int rem, int j,
+                                            int k, int nx, int ny, int nz, long long plane,
+                                            bool vec, bool xs, bool yz)
+{
+    ld4(o.c, p, rem, vec);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        o.sx[q] = o.sy[q] = o.sz[q] = T(0);
+    if (xs) {
+        const T left = i0 > 0 ? p[-1] : T(0);
+        const T right = rem > 4 ? p[4] : T(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o.sx[q] = (q == 0 ? left : o.c[q - 1]) +
+                      (q == 3 ? right : (q + 1 < rem ? o.c[q + 1] : T(0)));
+    }
+    if (!yz)
+        return;
+    T a[4];
+    if (j > 0) {
+        ld4(a, p - nx, rem, vec);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o.sy[q] += a[q];
+    }
+    if (j + 1 < ny) {
+        ld4(a, p + nx, rem, vec);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o.sy[q] += a[q];
+    }
+    if (k > 0) {
+        ld4(a, p - plane, rem, vec);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o.sz[q] += a[q];
+    }
+    if (k + 1 < nz) {
+        ld4(a, p + plane, rem, vec);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o.sz[q] += a[q];
     }
 }
 
 // lambda <- lambda - omega A mu; gb += omega mu; per-CTA partial sums of the three
-// coefficient-gradient terms.  z = M^{-1}(b - A u_k), u = u_k.
+// coefficient-gradient terms mu.(Tx x), mu.(2x - Sy u), mu.(2x - Sz u) with x = M^{-1}(b +
+// N u_k), u = u_k.  One warp per grid row at a time (grid-stride over rows with a fixed
+// grid, so the partial sums are reproducible), four cells per lane.  FP32 contexts sum a
+// lane's products over a row in FP32 before the FP64 sums (the FP64 pipe is the narrow one).
+// Latency bound (ncu: long-scoreboard stalls, 16 resident warps at 120 registers): the FP32
+// build is held to 3 CTAs per SM (78 registers, no spills); FP64 would spill, so it keeps 2.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) adjoint_update_kernel(
-    T* __restrict__ lam, const T* __restrict__ mu, const T* __restrict__ z,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) adjoint_update_kernel(
+    T* __restrict__ lam, const T* __restrict__ mu, const T* __restrict__ x,
     const T* __restrict__ u, T* __restrict__ gb, int nx, int ny, int nz, double ax, double ay,
-    double az, double omega, double* partials)
+    double az, double omega, double* partials, bool vec)
 {
-    const long long n = (long long)nx * ny * nz;
     const long long plane = (long long)nx * ny;
+    const long long nrows = (long long)ny * nz;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const T cx = (T)ax, cy = (T)ay, cz = (T)az, dg = (T)(2.0 * (ax + ay + az)), om = (T)omega;
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % nx);
-        const long long jk = t / nx;
-        const int j = (int)(jk % ny);
-        const int k = (int)(jk / ny);
-        const bool xm = i > 0, xp = i + 1 < nx, ym = j > 0, yp = j + 1 < ny, zm = k > 0,
-                   zp = k + 1 < nz;
-        auto sum_x = [&](const T* a) { return (xm ? a[t - 1] : T(0)) + (xp ? a[t + 1] : T(0)); };
-        auto sum_y = [&](const T* a) { return (ym ? a[t - nx] : T(0)) + (yp ? a[t + nx] : T(0)); };
-        auto sum_z = [&](const T* a) {
-            return (zm ? a[t - plane] : T(0)) + (zp ? a[t + plane] : T(0));
-        };
-        const T m = mu[t];
-        const T Amu = dg * m - cx * sum_x(mu) - cy * sum_y(mu) - cz * sum_z(mu);
-        lam[t] = lam[t] - om * Amu;
-        gb[t] += om * m;
-        const T zt = z[t], ut = u[t];
-        const T Txz_u = (T(2) * (zt + ut)) - sum_x(z) - sum_x(u);  // Tx (z + u)
-        const T Tyu = T(2) * ut - sum_y(u);
-        const T Tzu = T(2) * ut - sum_z(u);
-        g0 += (double)m * (double)Txz_u;
-        g1 += (double)m * (double)(T(2) * zt + Tyu);
-        g2 += (double)m * (double)(T(2) * zt + Tzu);
+    for (long long row = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); row < nrows;
+         row += (long long)gridDim.x * wpb) {
+        const int k = (int)(row / ny), j = (int)(row - (long long)k * ny);
+        const long long base = row * nx;
+        T h0 = T(0), h1 = T(0), h2 = T(0);
+        for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+            const int rem = nx - i0;
+            const long long t = base + i0;
+            Nb4<T> m, xx, uu;
+            neighbours4(m, mu + t, i0, rem, j, k, nx, ny, nz, plane, vec, true, true);
+            neighbours4(xx, x + t, i0, rem, j, k, nx, ny, nz, plane, vec, true, false);
+            neighbours4(uu, u + t, i0, rem, j, k, nx, ny, nz, plane, vec, false, true);
+            T lv[4], gv[4];
+            ld4(lv, lam + t, rem, vec);
+            ld4(gv, gb + t, rem, vec);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T mq = m.c[q];
+                const T Amu = dg * mq - cx * m.sx[q] - cy * m.sy[q] - cz * m.sz[q];
+                lv[q] = lv[q] - om * Amu;
+                gv[q] += om * mq;
+                const T x2 = T(2) * xx.c[q];
+                if (q < rem) {
+                    if constexpr (sizeof(T) == 4) {
+                        h0 = fma(mq, x2 - xx.sx[q], h0);
+                        h1 = fma(mq, x2 - uu.sy[q], h1);
+                        h2 = fma(mq, x2 - uu.sz[q], h2);
+                    } else {
+                        g0 = fma(mq, x2 - xx.sx[q], g0);
+                        g1 = fma(mq, x2 - uu.sy[q], g1);
+                        g2 = fma(mq, x2 - uu.sz[q], g2);
+                    }
+                }
+            }
+            st4(lam + t, lv, rem, vec);
+            st4(gb + t, gv, rem, vec);
+        }
+        if constexpr (sizeof(T) == 4) {
+            g0 += (double)h0;
+            g1 += (double)h1;
+            g2 += (double)h2;
+        }
     }
     __shared__ double red[3][kThreads / 32];
     double v[3] = {g0, g1, g2};
@@ -142,9 +285,11 @@ cudaError_t launch_minv(const brs_ctx* c, const T* in, T* out, cudaStream_t s)
     const unsigned blocks = (unsigned)((nlines + groups - 1) / groups);
     const T* tab = static_cast<const T*>(c->line_tab);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    const bool vec = nx == L.E * L.G && (nx * sizeof(T)) % 16 == 0 && a16(in) && a16(out);
 #define BRS_MINV_CASE(EE, GG)                                                          \
     if (L.E == EE && L.G == GG) {                                                      \
-        line_minv_kernel<T, EE, GG><<<blocks, kThreads, 0, s>>>(in, out, tab, nx, ny, nz); \
+        line_minv_kernel<T, EE, GG><<<blocks, kThreads, 0, s>>>(in, out, tab, nx, ny, nz, vec); \
         return cudaGetLastError();                                                     \
     }
     BRS_MINV_CASE(4, 4)
@@ -162,26 +307,28 @@ struct AdjState {
     void* mu = nullptr;
     double* partials = nullptr;
     int nblocks = 0;
+    brs_ctx* xctx = nullptr;  // x-line Jacobi with omega = 1: x = M^{-1}(b + N u) in one pass
+    int* xstatus = nullptr;   // xctx's own status word (its kernels report to the owner's)
 };
 
 template <typename T>
 int adjoint_run(brs_ctx* c, T* lam, const T* u, const T* b, T* gb, double* ga, cudaStream_t s)
 {
     AdjState* A = static_cast<AdjState*>(c->adjoint);
-    T* z = static_cast<T*>(c->scratch);
+    T* x = static_cast<T*>(c->scratch);
     T* mu = static_cast<T*>(A->mu);
-    // z = M^{-1}(b - A u_k)
-    int rc = residual_launch(c, u, b, z, false, s);
+    // x = M^{-1}(b + N u_k): one undamped x-line Jacobi sweep from u_k
+    int rc = line_sweep_launch(A->xctx, u, x, b, s);
     if (rc != BRS_OK)
         return rc;
-    cudaError_t e = launch_minv<T>(c, z, z, s);
-    if (e == cudaSuccess)
-        e = launch_minv<T>(c, lam, mu, s);  // mu = M^{-1} lambda
+    cudaError_t e = launch_minv<T>(c, lam, mu, s);  // mu = M^{-1} lambda
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    adjoint_update_kernel<T><<<A->nblocks, kThreads, 0, s>>>(lam, mu, z, u, gb, c->p.nx, c->p.ny,
+    auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    const bool vec = c->p.nx % 4 == 0 && a16(lam) && a16(mu) && a16(x) && a16(u) && a16(gb);
+    adjoint_update_kernel<T><<<A->nblocks, kThreads, 0, s>>>(lam, mu, x, u, gb, c->p.nx, c->p.ny,
                                                              c->p.nz, c->p.ax, c->p.ay, c->p.az,
-                                                             c->omega, A->partials);
+                                                             c->omega, A->partials, vec);
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return brs_cuda_status(e);
@@ -200,6 +347,10 @@ void adjoint_teardown(brs_ctx* c)
         cudaFree(A->mu);
     if (A->partials)
         cudaFree(A->partials);
+    if (A->xctx) {
+        A->xctx->dev_status = A->xstatus;
+        brsmooth_destroy(A->xctx);
+    }
     delete A;
     c->adjoint = nullptr;
 }
@@ -218,15 +369,28 @@ extern "C" int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, co
         c->adjoint = A;
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-        const long long need = (c->cells + kThreads - 1) / kThreads;
+        const long long need = ((long long)c->p.ny * c->p.nz + kThreads / 32 - 1) / (kThreads / 32);
         A->nblocks = (int)(need < (long long)sms * 8 ? need : (long long)sms * 8);
         if (A->nblocks < 1)
             A->nblocks = 1;
         cudaError_t e = cudaMalloc(&A->mu, (size_t)c->cells * c->esize);
         if (e == cudaSuccess)
             e = cudaMalloc(&A->partials, sizeof(double) * 3 * A->nblocks);
-        if (e != cudaSuccess)
-            return brs_cuda_status(e);
+        int rc = brs_cuda_status(e);
+        if (rc == BRS_OK) {
+            brs_params q = c->p;
+            q.omega = 1.0;
+            rc = brsmooth_create(&q, &A->xctx);
+        }
+        if (rc != BRS_OK) {
+            adjoint_teardown(c);
+            return rc;
+        }
+        // only its line kernel is used: no Jacobi buffer, and faults land in this context
+        cudaFree(A->xctx->scratch);
+        A->xctx->scratch = nullptr;
+        A->xstatus = A->xctx->dev_status;
+        A->xctx->dev_status = c->dev_status;
     }
     c->last_stream = s;
     if (c->p.dtype == BRS_F64)
