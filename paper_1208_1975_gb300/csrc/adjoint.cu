@@ -15,6 +15,8 @@
 // undamped line-Jacobi iterate (A = M - N), which the x-line sweep kernel produces in one
 // pass: Tx (z + u) = Tx x, 2 z + Ty u = 2 x - Sy u, 2 z + Tz u = 2 x - Sz u, with S_d the
 // sum of the two neighbours along d (T_d = 2 I - S_d).
+#include <cstdlib>
+
 #include "brs_internal.cuh"
 #include "line_impl.cuh"
 
@@ -250,6 +252,151 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) adjoint_upda
     }
 }
 
+// FP32 form of the same update as a z-march: a warp owns 128 cells of row j (four per lane)
+// over a chunk of kMarchKC planes, keeps mu and u of planes k-1, k, k+1 in registers, and
+// loads the next plane's inputs before computing the current one (more loads in flight per
+// warp, and the z neighbours are not loaded twice).  Items (j, x-chunk, z-chunk) go to warps
+// in a fixed grid-stride order, so the partial sums are reproducible.
+constexpr int kMarchKC = 16;
+
+template <int N>
+__device__ __forceinline__ void zero4(float (&v)[N])
+{
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+        v[q] = 0.0f;
+}
+
+struct MarchIn {  // one plane's loads for the lanes' four cells
+    float mup[4], up[4], muym[4], muyp[4], uym[4], uyp[4], xc[4], lam[4], gb[4];
+    float mul, mur, xl, xr;
+};
+
+__global__ void __launch_bounds__(kThreads, 2) adjoint_update_march(
+    float* __restrict__ lam, const float* __restrict__ mu, const float* __restrict__ x,
+    const float* __restrict__ u, float* __restrict__ gb, int nx, int ny, int nz, double ax,
+    double ay, double az, double omega, double* partials, bool vec)
+{
+    const long long plane = (long long)nx * ny;
+    const int ncx = (nx + 127) / 128, nkc = (nz + kMarchKC - 1) / kMarchKC;
+    const long long nitems = (long long)ny * ncx * nkc;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const float cx = (float)ax, cy = (float)ay, cz = (float)az;
+    const float dg = (float)(2.0 * (ax + ay + az)), om = (float)omega;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (long long it = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); it < nitems;
+         it += (long long)gridDim.x * wpb) {
+        const int kc = (int)(it % nkc);
+        const long long rest = it / nkc;
+        const int xc = (int)(rest % ncx), j = (int)(rest / ncx);
+        const int i0 = xc * 128 + 4 * lane, rem = nx - i0;
+        const bool act = rem > 0;
+        const int k0 = kc * kMarchKC, k1 = min(nz, k0 + kMarchKC);
+        const long long row = (long long)j * nx + i0;
+        auto at = [&](const float* a, int k) { return a + (long long)k * plane + row; };
+        // plane k's loads (zeros outside the grid or for lanes past the row)
+        auto load = [&](MarchIn& P, int k) {
+            zero4(P.mup), zero4(P.up), zero4(P.muym), zero4(P.muyp), zero4(P.uym), zero4(P.uyp);
+            zero4(P.xc), zero4(P.lam), zero4(P.gb);
+            P.mul = P.mur = P.xl = P.xr = 0.0f;
+            if (!act)
+                return;
+            if (k + 1 < nz) {
+                ld4(P.mup, at(mu, k + 1), rem, vec);
+                ld4(P.up, at(u, k + 1), rem, vec);
+            }
+            if (j > 0) {
+                ld4(P.muym, at(mu, k) - nx, rem, vec);
+                ld4(P.uym, at(u, k) - nx, rem, vec);
+            }
+            if (j + 1 < ny) {
+                ld4(P.muyp, at(mu, k) + nx, rem, vec);
+                ld4(P.uyp, at(u, k) + nx, rem, vec);
+            }
+            const float* px = at(x, k);
+            const float* pm = at(mu, k);
+            ld4(P.xc, px, rem, vec);
+            ld4(P.lam, at(lam, k), rem, vec);
+            ld4(P.gb, at(gb, k), rem, vec);
+            if (i0 > 0) {
+                P.mul = pm[-1];
+                P.xl = px[-1];
+            }
+            if (rem > 4) {
+                P.mur = pm[4];
+                P.xr = px[4];
+            }
+        };
+        float mum[4], muc[4], um[4], uc[4];
+        zero4(mum), zero4(muc), zero4(um), zero4(uc);
+        if (act) {
+            if (k0 > 0) {
+                ld4(mum, at(mu, k0 - 1), rem, vec);
+                ld4(um, at(u, k0 - 1), rem, vec);
+            }
+            ld4(muc, at(mu, k0), rem, vec);
+            ld4(uc, at(u, k0), rem, vec);
+        }
+        MarchIn nxt;
+        load(nxt, k0);
+        float h0 = 0.0f, h1 = 0.0f, h2 = 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            const MarchIn cur = nxt;
+            if (k + 1 < k1)
+                load(nxt, k + 1);
+            float lv[4], gv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float mq = muc[q];
+                const float sxm = (q == 0 ? cur.mul : muc[q - 1]) +
+                                  (q == 3 ? cur.mur : (q + 1 < rem ? muc[q + 1] : 0.0f));
+                const float sym = cur.muym[q] + cur.muyp[q], szm = mum[q] + cur.mup[q];
+                const float Amu = dg * mq - cx * sxm - cy * sym - cz * szm;
+                lv[q] = cur.lam[q] - om * Amu;
+                gv[q] = cur.gb[q] + om * mq;
+                const float x2 = 2.0f * cur.xc[q];
+                const float sxx = (q == 0 ? cur.xl : cur.xc[q - 1]) +
+                                  (q == 3 ? cur.xr : (q + 1 < rem ? cur.xc[q + 1] : 0.0f));
+                if (q < rem) {
+                    h0 = fmaf(mq, x2 - sxx, h0);
+                    h1 = fmaf(mq, x2 - (cur.uym[q] + cur.uyp[q]), h1);
+                    h2 = fmaf(mq, x2 - (um[q] + cur.up[q]), h2);
+                }
+            }
+            if (act) {
+                st4(lam + (long long)k * plane + row, lv, rem, vec);
+                st4(gb + (long long)k * plane + row, gv, rem, vec);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                mum[q] = muc[q], muc[q] = cur.mup[q];
+                um[q] = uc[q], uc[q] = cur.up[q];
+            }
+        }
+        g0 += (double)h0;
+        g1 += (double)h1;
+        g2 += (double)h2;
+    }
+    __shared__ double red[3][kThreads / 32];
+    double v[3] = {g0, g1, g2};
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1)
+            v[d] += __shfl_down_sync(0xffffffffu, v[d], o);
+        if ((threadIdx.x & 31) == 0)
+            red[d][threadIdx.x >> 5] = v[d];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int d = 0; d < 3; ++d) {
+            double w = threadIdx.x < kThreads / 32 ? red[d][threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1)
+                w += __shfl_down_sync(0xffffffffu, w, o);
+            if (threadIdx.x == 0)
+                partials[3 * blockIdx.x + d] = w;
+        }
+    }
+}
+
 // grad_a[d] += -omega * sum of the partials, in a fixed order.
 __global__ void adjoint_reduce_kernel(const double* partials, int nblocks, double omega,
                                       double* grad_a)
@@ -303,6 +450,13 @@ cudaError_t launch_minv(const brs_ctx* c, const T* in, T* out, cudaStream_t s)
     return cudaErrorInvalidConfiguration;
 }
 
+// BRSMOOTH_ADJ_MARCH=0 selects the row form of the FP32 update (A/B measurements)
+bool env_march()
+{
+    const char* v = std::getenv("BRSMOOTH_ADJ_MARCH");
+    return !(v && v[0] == '0');
+}
+
 struct AdjState {
     void* mu = nullptr;
     double* partials = nullptr;
@@ -326,6 +480,16 @@ int adjoint_run(brs_ctx* c, T* lam, const T* u, const T* b, T* gb, double* ga, c
         return brs_cuda_status(e);
     auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
     const bool vec = c->p.nx % 4 == 0 && a16(lam) && a16(mu) && a16(x) && a16(u) && a16(gb);
+    if constexpr (sizeof(T) == 4) {
+        if (env_march())
+            adjoint_update_march<<<A->nblocks, kThreads, 0, s>>>(
+                lam, mu, x, u, gb, c->p.nx, c->p.ny, c->p.nz, c->p.ax, c->p.ay, c->p.az,
+                c->omega, A->partials, vec);
+        else
+            adjoint_update_kernel<T><<<A->nblocks, kThreads, 0, s>>>(
+                lam, mu, x, u, gb, c->p.nx, c->p.ny, c->p.nz, c->p.ax, c->p.ay, c->p.az,
+                c->omega, A->partials, vec);
+    } else
     adjoint_update_kernel<T><<<A->nblocks, kThreads, 0, s>>>(lam, mu, x, u, gb, c->p.nx, c->p.ny,
                                                              c->p.nz, c->p.ax, c->p.ay, c->p.az,
                                                              c->omega, A->partials, vec);
