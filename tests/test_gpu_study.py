@@ -9,6 +9,9 @@ guess): ||r_3|| / ||r_0|| and the sliding-window factor (||r_{i+k}|| / ||r_i||)^
   the larger block keeping fewer couplings in N, so Varga's comparison theorem orders the
   spectral radii of M^{-1} N; with omega = 0.8 the slowest mode sets the factor because the
   most negative eigenvalue of the damped iteration is above -0.6.
+* Two-colour block GS contracts with the square of the undamped block-Jacobi factor (Young:
+  the two-colour block matrix is 2-cyclic and consistently ordered), which the GPU's GS and
+  damped-Jacobi factors satisfy for every paper size.
 """
 import math
 
@@ -82,3 +85,11 @@ def test_asymptotic_jacobi_factor_falls_with_block_size(brs):
     facs = [window_factor(brs, "box", box, "jacobi", 2000, 100) for box in PAPER_SIZES]
     assert all(0 < f < 1 for f in facs), facs
     assert all(x > y for x, y in zip(facs, facs[1:])), facs
+
+
+@pytest.mark.parametrize("box", PAPER_SIZES, ids=lambda s: "x".join(map(str, s)))
+def test_two_colour_gs_factor_is_square_of_jacobi(brs, box):
+    gj = window_factor(brs, "box", box, "jacobi", 2000, 100)
+    gg = window_factor(brs, "box", box, "gs", 1000, 100)
+    rho = 1 - (1 - gj) / 0.8
+    assert abs(gg - rho * rho) <= 2e-5, (gj, gg, rho * rho)

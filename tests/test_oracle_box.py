@@ -236,6 +236,31 @@ def test_asymptotic_factor_is_slowest_sine_mode(orc, block, box):
     assert abs(fac - g) <= 1e-6, (fac, g)
 
 
+@pytest.mark.parametrize("box", [(1, 1, 1), (2, 2, 2), (4, 2, 2), (2, 2, 4)])
+def test_two_colour_gs_factor_is_square_of_jacobi(orc, box):
+    """Young's theorem: with the blocks coloured by the parity of bi + bj + bk, the block
+    matrix is 2-cyclic and consistently ordered, so two-colour block GS (omega = 1) contracts
+    with rho_J^2, rho_J the undamped block-Jacobi factor; damped Jacobi (omega = 0.8) has
+    1 - 0.8 (1 - rho_J).  Both measured as sliding-window factors from a random guess, b = 0."""
+    n, i, k = 8, 300, 40
+    a = (1.0, 1.0, 1.0)
+    u0 = initial_guess((n, n, n))
+    b = np.zeros_like(u0)
+
+    def factor(method, omega):
+        u = u0
+        for _ in range(i):
+            u = orc.sweep(u, b, a, block="box", box=box, method=method, omega=omega)
+        ri = orc.residual_norm(u, b, a)
+        for _ in range(k):
+            u = orc.sweep(u, b, a, block="box", box=box, method=method, omega=omega)
+        return (orc.residual_norm(u, b, a) / ri) ** (1.0 / k)
+
+    gj = factor("jacobi", 0.8)
+    rho = 1 - (1 - gj) / 0.8
+    assert abs(factor("gs_zebra", 1.0) - rho * rho) <= 1e-6, (gj, rho)
+
+
 def test_box_must_tile_grid(orc):
     u = np.zeros((4, 4, 6))
     with pytest.raises(ValueError):
