@@ -24,58 +24,78 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// out = M_line^{-1} in, one line group per (j,k); in-place safe (a group reads its whole
-// line before writing it).
+// out = M_line^{-1} in, one line group per (j,k) at a time; in-place safe (a group reads
+// its whole line, and its next one, before writing it).
 template <typename T, int E, int G>
 __global__ void __launch_bounds__(kThreads) line_minv_kernel(const T* in, T* out,
                                                              const T* __restrict__ tab, int nx,
                                                              int ny, int nz, bool vec)
 {
+    // Grid-stride over lines, the next line's cells loaded before the current one is solved
+    // (the load latency overlaps the solve).  Every group of a warp runs the same number of
+    // iterations, because the solve shuffles across the warp; groups past the last line
+    // solve zeros.
     const int groups = blockDim.x / G;
-    const long long line = (long long)blockIdx.x * groups + threadIdx.x / G;
+    const long long nlines = (long long)ny * nz;
+    const long long stride = (long long)gridDim.x * groups;
     const int lane = threadIdx.x % G;
-    const bool active = line < (long long)ny * nz;
+    const long long warp_line0 = (long long)blockIdx.x * groups + (threadIdx.x & ~31) / G;
+    const long long iters = warp_line0 < nlines ? (nlines - warp_line0 + stride - 1) / stride : 0;
     brs::LineTables<T, E, G> tb;
     tb.load(tab, lane);
     constexpr int NP = G * E;
     constexpr int LG = brs::Log2<G>::value;
     const T* ptab = tab + 3 * NP + 2 * LG * G;
-    const size_t base = (size_t)(active ? line : 0) * nx;
     // VEC: full lines (nx = E G) with 16-byte aligned rows and E a whole number of 16-byte
     // vectors: each lane moves its E cells as vectors of the element type
     using V = typename brs::Vec16<T>::type;
     constexpr int NV = (int)(E * sizeof(T) / 16);
     constexpr bool CAN_VEC = (E * sizeof(T)) % 16 == 0;
-    T r[E];
-    if (CAN_VEC && vec) {
-        const V* src = reinterpret_cast<const V*>(in + base + lane * E);
-#pragma unroll
-        for (int m = 0; m < NV; ++m)
-            reinterpret_cast<V*>(r)[m] = active ? src[m] : V{};
-    } else {
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            const int x = lane * E + q;
-            r[q] = (active && x < nx) ? in[base + x] : T(0);
-        }
-    }
-    brs::line_solve<T, E, G>(r, tb, lane);
-#pragma unroll
-    for (int q = 0; q < E; ++q)
-        r[q] = ptab[lane * E + q] * r[q];
-    if (CAN_VEC && vec) {
-        if (active) {
-            V* dst = reinterpret_cast<V*>(out + base + lane * E);
+    auto load = [&](long long line, T (&r)[E]) {
+        const bool active = line < nlines;
+        const size_t base = (size_t)(active ? line : 0) * nx;
+        if (CAN_VEC && vec) {
+            const V* src = reinterpret_cast<const V*>(in + base + lane * E);
 #pragma unroll
             for (int m = 0; m < NV; ++m)
-                dst[m] = reinterpret_cast<const V*>(r)[m];
-        }
-    } else {
+                reinterpret_cast<V*>(r)[m] = active ? src[m] : V{};
+        } else {
 #pragma unroll
-        for (int q = 0; q < E; ++q) {
-            const int x = lane * E + q;
-            if (active && x < nx)
-                out[base + x] = r[q];
+            for (int q = 0; q < E; ++q) {
+                const int x = lane * E + q;
+                r[q] = (active && x < nx) ? in[base + x] : T(0);
+            }
+        }
+    };
+    long long line = (long long)blockIdx.x * groups + threadIdx.x / G;
+    T nxt[E];
+    load(line, nxt);
+    for (long long it = 0; it < iters; ++it, line += stride) {
+        T r[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            r[q] = nxt[q];
+        if (it + 1 < iters)
+            load(line + stride, nxt);
+        brs::line_solve<T, E, G>(r, tb, lane);
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            r[q] = ptab[lane * E + q] * r[q];
+        if (line < nlines) {
+            const size_t base = (size_t)line * nx;
+            if (CAN_VEC && vec) {
+                V* dst = reinterpret_cast<V*>(out + base + lane * E);
+#pragma unroll
+                for (int m = 0; m < NV; ++m)
+                    dst[m] = reinterpret_cast<const V*>(r)[m];
+            } else {
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    const int x = lane * E + q;
+                    if (x < nx)
+                        out[base + x] = r[q];
+                }
+            }
         }
     }
 }
@@ -429,13 +449,20 @@ cudaError_t launch_minv(const brs_ctx* c, const T* in, T* out, cudaStream_t s)
     const LineCfg& L = c->lcfg;
     const int groups = kThreads / L.G;
     const long long nlines = (long long)c->p.ny * c->p.nz;
-    const unsigned blocks = (unsigned)((nlines + groups - 1) / groups);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const long long need = (nlines + groups - 1) / groups;
     const T* tab = static_cast<const T*>(c->line_tab);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
     const bool vec = nx == L.E * L.G && (nx * sizeof(T)) % 16 == 0 && a16(in) && a16(out);
 #define BRS_MINV_CASE(EE, GG)                                                          \
     if (L.E == EE && L.G == GG) {                                                      \
+        int per_sm = 1; /* one resident wave: the kernel strides over the lines */      \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, line_minv_kernel<T, EE, GG>, \
+                                                      kThreads, 0);                    \
+        const long long cap = (long long)sms * (per_sm > 0 ? per_sm : 1);               \
+        const unsigned blocks = (unsigned)(need < cap ? need : cap);                    \
         line_minv_kernel<T, EE, GG><<<blocks, kThreads, 0, s>>>(in, out, tab, nx, ny, nz, vec); \
         return cudaGetLastError();                                                     \
     }
