@@ -95,7 +95,11 @@ int line_setup(brs_ctx* c)
             (L.bx * es) % 16 == 0 && L.bx % L.E == 0 && L.bx <= 256 &&
             env_int("BRSMOOTH_LINE_PLAIN", 0) == 0;
     const int groups_per_warp = 32 / L.G;
-    int jt_default = (c->p.dtype == BRS_F64 && L.E >= 8) ? 4 : 256 / L.G;
+    // Wide lines (E >= 12 cells per lane, 168+ registers) fit one 256-thread CTA per SM; at
+    // 4 lines per tile and a 4-stage ring three (nx = 384) or two (512) CTAs fit, which
+    // measured 409 -> 471 Gcell/s at 384^3 and 321 -> 336 at 512^3 (same box, FP32 Jacobi).
+    const bool wide = c->p.dtype == BRS_F32 && L.E >= 12;
+    int jt_default = (c->p.dtype == BRS_F64 && L.E >= 8) ? 4 : wide ? 128 / L.G : 256 / L.G;
     int jt = env_int("BRSMOOTH_LINE_JT", jt_default);
     const int ny_round = ((p.ny + groups_per_warp - 1) / groups_per_warp) * groups_per_warp;
     if (jt > ny_round)
@@ -105,7 +109,7 @@ int line_setup(brs_ctx* c)
         jt = 256 / L.G;
     L.JT = jt;
     // ring depth: stages s..s+2 are being read, the rest are loads in flight
-    L.NS = env_int("BRSMOOTH_LINE_NS", p.dtype == BRS_F64 ? 4 : 6);
+    L.NS = env_int("BRSMOOTH_LINE_NS", (p.dtype == BRS_F64 || wide) ? 4 : 6);
     if (L.NS < 3)
         L.NS = 3;
     while (L.NS > 3 && (size_t)L.NS * (tma_slot_bytes(L, es) + 8) > 227u * 1024u)
