@@ -261,6 +261,28 @@ def test_two_colour_gs_factor_is_square_of_jacobi(orc, box):
     assert abs(factor("gs_zebra", 1.0) - rho * rho) <= 1e-6, (gj, rho)
 
 
+@pytest.mark.parametrize("block", ["line", "plane"])
+def test_zebra_line_and_plane_gs_factor_is_square_of_jacobi(orc, block):
+    """The same relation for full-extent lines (colour = parity of j + k) and planes (parity of
+    k): two colours make the block matrix 2-cyclic and consistently ordered."""
+    n, i, k = 8, 200, 40
+    a = (1.0, 0.5, 0.25)
+    u0 = initial_guess((n, n, n))
+    b = np.zeros_like(u0)
+
+    def factor(method, omega):
+        u = u0
+        for _ in range(i):
+            u = orc.sweep(u, b, a, block=block, method=method, omega=omega)
+        ri = orc.residual_norm(u, b, a)
+        for _ in range(k):
+            u = orc.sweep(u, b, a, block=block, method=method, omega=omega)
+        return (orc.residual_norm(u, b, a) / ri) ** (1.0 / k)
+
+    rho = 1 - (1 - factor("jacobi", 0.8)) / 0.8
+    assert abs(factor("gs_zebra", 1.0) - rho * rho) <= 1e-6, rho
+
+
 def test_box_must_tile_grid(orc):
     u = np.zeros((4, 4, 6))
     with pytest.raises(ValueError):
