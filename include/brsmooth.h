@@ -11,7 +11,8 @@
  *
  * One sweep (Sec. 2, Eq. blockiteration2):  u <- u + omega * M^{-1} (b - A u)
  * with M the block diagonal of A for full x-line blocks (M_line = tridiag(-ax,
- * 2(ax+ay+az), -ax), one block per (j,k)) or full xy-plane blocks (M_plane = ax Tx (x) I
+ * 2(ax+ay+az), -ax), one block per (j,k)), full y-line or z-line blocks (the same with the
+ * axes exchanged), full xy-plane blocks (M_plane = ax Tx (x) I
  * + ay I (x) Ty + 2 az I, one block per k) or bx*by*bz boxes (the spatial blocks of
  * Sec. 2 and Sec. 3: M_box = the stencil restricted to the box's cells, inverted once
  * (Sec. 4.3) and applied as a dense product, Alg. 2 step 2).  Every block is solved
@@ -50,7 +51,8 @@ extern "C" {
 #define BRS_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out */
 #define BRS_ERR_BOUNDS (-6)      /* a device-side index check failed */
 
-/* Block shape: full x-lines or full xy-planes (Sec. 2, block partition of A). */
+/* Block shape (Sec. 2, block partition of A): full lines along x, y or z, full xy-planes,
+ * or bx*by*bz boxes. */
 #define BRS_XLINE 0
 #define BRS_XYPLANE 1
 #define BRS_BOX 2 /* bx*by*bz spatial blocks with one precomputed inverse (Sec. 2, Sec. 4.3) */
