@@ -1113,7 +1113,7 @@ int level_setup(brs_ctx* c, const int* nbr)
     // face pushes: patch p's face f lands in the opposite ghost face of neighbour q
     // (x- -> q's x+, x+ -> q's x-, and so on); physical-boundary ghosts stay zero in both
     // buffers because nothing writes them
-    B->push = env_int("BRSMOOTH_LEVEL_PUSH", 1) != 0 && gtotal < (1ll << 31);
+    B->push = env_int("BRSMOOTH_LEVEL_PUSH", 1) != 0;
     if (B->push) {
         std::vector<long long> push(6 * (size_t)B->npatch, -1);
         for (int p = 0; p < B->npatch; ++p)
