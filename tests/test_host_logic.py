@@ -62,6 +62,8 @@ def test_strerror_and_null_handling(cuda_lib):
         assert isinstance(brs.brsmooth_strerror(code), str) and brs.brsmooth_strerror(code)
     assert brs.brsmooth_destroy(None) == brs.BRS_OK
     assert brs.brsmooth_sweep(None, None, None, 1, 0) == brs.BRS_ERR_ARG
+    assert brs.brsmooth_sweep_host(None, None, None, 1, 0) == brs.BRS_ERR_ARG
+    assert brs.brsmooth_sweep_host_async(None, None, None, 1, 0) == brs.BRS_ERR_ARG
     assert brs.brsmooth_residual(None, None, None, None, True, 0)[0] == brs.BRS_ERR_ARG
     assert brs.brsmooth_last_error(None) == brs.BRS_ERR_ARG
     assert brs.brsmooth_cells(None) == 0
