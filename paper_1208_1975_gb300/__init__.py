@@ -340,8 +340,8 @@ def _adjoint_step(c: "Context", lam, u_k, b, gb, ga, stream=None):
 _SMOOTH_CTX = {}
 
 
-def _smooth_context(nx, ny, nz, av, dt, omega):
-    key = (nx, ny, nz, av, dt, float(omega))
+def _smooth_context(nx, ny, nz, av, dt, omega, device=None):
+    key = (nx, ny, nz, av, dt, float(omega), device)
     c = _SMOOTH_CTX.pop(key, None)
     if c is None:
         c = Context(nx, ny, nz, av, block="line", method="jacobi", dtype=dt, omega=omega)
@@ -367,7 +367,7 @@ def _block_smooth_fn():
             nz, ny, nx = b.shape
             dt = "f64" if b.dtype == torch.float64 else "f32"
             av = tuple(float(x) for x in a.detach().cpu().tolist())
-            c = _smooth_context(nx, ny, nz, av, dt, omega)
+            c = _smooth_context(nx, ny, nz, av, dt, omega, b.device.index)
             b = b.detach().contiguous()
             u = u0.detach().clone().contiguous()
             ckpt = max(1, int(ckpt))
