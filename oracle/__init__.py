@@ -14,8 +14,16 @@ the pieces whose plain definition is a library primitive or a closed form:
   line/plane block diagonal, and the exact per-sweep damping of one sine mode.
 * :func:`adjoint_gradients` -- reverse-mode gradients of L = 0.5 ||u_K - u_t||^2 through K
   block-Jacobi sweeps (Eq. blockiteration2), stepping lambda_k = G^T lambda_{k+1}.
+* :func:`sweep` with ``block="box"`` and :func:`box_inverse` -- bx*by*bz blocks whose
+  inverse comes from a dense Cholesky factorisation (Sec. 4.3 inverts once per block
+  shape); the visiting orders of block GS (Eq. sm:blockm) as lexicographic, reverse and
+  two-colour.
+* :func:`level_sweep` -- a level of patches whose ghost layers hold the face neighbours'
+  values from before the step (Sec. 2), one x-line sweep per patch.
 
-Parity status: every function here is pinned by a CPU test (``tests/test_oracle_*.py``).
+Parity status: every function here is pinned by a CPU test (``tests/test_oracle_*.py``):
+closed forms, dense solves, equalities between independently built block forms (box = line
+= plane = permuted line), Varga's and Young's relations between the block iterations.
 """
 from __future__ import annotations
 
