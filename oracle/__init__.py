@@ -23,7 +23,7 @@ the pieces whose plain definition is a library primitive or a closed form:
 
 Parity status: every function here is pinned by a CPU test (``tests/test_oracle_*.py``):
 closed forms, dense solves, equalities between independently built block forms (box = line
-= plane = permuted line), Varga's and Young's relations between the block iterations.
+= plane = permuted line), Young's relation between block Jacobi and two-colour block GS.
 """
 from __future__ import annotations
 
