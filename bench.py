@@ -1,19 +1,22 @@
 """Benchmark: Gcell-updates/s of block-relaxation sweeps on a 256^3 grid (one GB300 per rank).
 
 Headline workload: 256^3 interior cells, a = (1,1,1), x-line block Jacobi (omega = 0.8),
-FP32, b = h^2 f and u0 from seeded U[-1,1] draws; one step = 50 sweeps.  With N ranks
-(torchrun) every rank sweeps its own replica (no data-path collective: the grids are
-independent), so `value` is N x cells x sweeps / (max-over-ranks time).
+FP64 (the paper's precision), b = h^2 f and u0 from seeded U[-1,1] draws; one step = one
+library call of 50 sweeps.  With N ranks (torchrun) every rank sweeps its own replica (no
+data-path collective: the grids are independent), so `value` is N x cells x sweeps /
+(max-over-ranks time).
 
 Also reported on the same JSON line:
-  roofline     -- the sweep kernel's algorithmic HBM bytes (u read, b read, u' written:
-                  3 words per cell) per launch / average launch time, against the measured
-                  HBM copy bandwidth;
+  roofline     -- the binding roof of the FP64 sweep kernel: FP64 pipe operations (7 per
+                  cell: gather 4, elimination 1 each way, update 1) per launch / average
+                  launch time, against the FP64 FMA rate measured in the same run;
+  roofline_hbm -- the same kernel against the HBM roof (24 algorithmic bytes per cell);
   e2e          -- the same metric through the host-buffer C-ABI entry point, with the H2D
                   copies of u and b and the D2H copy of u inside the timed region;
   cpu_baseline -- the FP64 CPU oracle on the host cores on a bounded slab of the grid;
   clocks       -- nvidia-smi samples taken during the timed region;
-  variants     -- other method / dtype / coefficient combinations of the 256^3 workload.
+  variants     -- other method / dtype / coefficient / block combinations, each with its
+                  error against the FP64 oracle and, where timed, the oracle's own rate.
 
 `--impl reference` times the FP64 CPU oracle instead (rank 0 only), on the same metric.
 """
@@ -237,26 +240,94 @@ def run_reference(args):
     return 0
 
 
-def _traffic_record():
-    """Per-launch DRAM bytes of the headline kernel from the committed ncu summary, if current."""
+def _traffic_record(profile: str, sources):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if still current:
+    the summary records a hash of the kernel's sources, and a changed kernel gives None."""
     import hashlib
     import re
 
-    rec = ROOT / "profiles" / "line_tma_f32_256cubed.md"
+    rec = ROOT / "profiles" / profile
     if not rec.exists():
         return None
     text = rec.read_text()
     m_b = re.search(r"^traffic_per_launch_bytes:\s*(\d+)", text, re.M)
     m_h = re.search(r"^source_sha256_16:\s*([0-9a-f]+)", text, re.M)
-    src = ROOT / "paper_1208_1975_gb300" / "csrc" / "line_impl.cuh"
-    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
-    if not (m_b and m_h) or m_h.group(1) != h:
+    h = hashlib.sha256()
+    for src in sources:
+        h.update((ROOT / "paper_1208_1975_gb300" / "csrc" / src).read_bytes())
+    if not (m_b and m_h) or m_h.group(1) != h.hexdigest()[:16]:
         return None  # the kernel changed since the counters were taken
     return int(m_b.group(1))
 
 
+def _live_fp64_fma_rate(brs, stream):
+    """FP64 FMAs per second on this GPU right now: the library's FMA-bound probe kernel
+    (8 independent chains per thread, every SM full), best of 5 CUDA-event timings."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = sms * 8, 2048
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    h = _stream_int(stream)
+    for _ in range(2):
+        if brs.brsmooth_probe_fp64_fma(out.data_ptr(), blocks, iters, h) != 0:
+            raise RuntimeError("FP64 FMA probe failed to launch")
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        brs.brsmooth_probe_fp64_fma(out.data_ptr(), blocks, iters, h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return blocks * 256 * iters * 8 / (best / 1e3)
+
+
+def _stream_int(stream):
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+
+
+def _launch_ms(ctx, u, b, stream, k=50, reps=5):
+    """Average duration of one sweep launch inside a call, as the timed steps run them
+    (back-to-back dependent launches): (T(k+1 sweeps) - T(1 sweep)) / k per call, median
+    of `reps`, CUDA events on the launching stream.  Both calls pay the same per-call
+    copies, so the difference is k sweep launches."""
+    import torch
+
+    def one(ns):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.sweep(u, b, ns, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    one(1), one(k + 1)
+    d = sorted(one(k + 1) - one(1) for _ in range(reps))
+    return d[len(d) // 2] / k
+
+
 def _rate(cells, sweeps, ms):
     return cells * sweeps / (ms / 1e3) / 1e9
+
+
+_FMA = {}
+
+
+def _fma_rate(brs, stream):
+    """FP64 FMAs per second, measured once per run by the probe kernel."""
+    if "rate" not in _FMA:
+        _FMA["rate"] = _live_fp64_fma_rate(brs, stream)
+    return _FMA["rate"]
+
+
+def _plane_form(ny):
+    """The plane solve the library runs: 1 = x sine transform + y tridiagonal solves (two
+    dense n x n contractions per plane), 2 = 2D sine basis (four)."""
+    return 1 if os.environ.get("BRSMOOTH_PLANE_FORM", "1") == "1" and ny <= 512 else 2
 
 
 def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, math="auto",
@@ -271,6 +342,7 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
     rate = _rate(N ** 3, sweeps * steps, vms)
     out = {"workload": "grid256", "block": blk, "method": meth, "dtype": dt, "coeffs": a,
            "value": rate, "unit": UNIT, "hbm_frac": rate * 3 * es / peak}
+    fma = _fma_rate(brs, stream) / 1e9 if dt == "f64" else None
     if blk == "box":
         # the dense block product: n multiply-adds per cell, n = bx by bz (Alg. 2 step 2)
         nb = box[0] * box[1] * box[2]
@@ -284,11 +356,16 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
             out["tensor_frac_of_tf32_peak"] = out["tensor_tflops"] / tf32_peak
             out["tf32_peak_tflops"] = tf32_peak
         if dt == "f64":
-            out["alu_frac_of_fp64_fma_peak"] = rate * nb / 626.9
+            out["alu_frac_of_fp64_fma_rate"] = rate * nb / fma
     if blk == "plane":
-        flops = 8.0 * N * N ** 3  # four n x n contractions per plane: 4 (nx + ny) per cell
+        # dense contractions per plane: form 1 (x sine transform + y tridiagonal solves) runs
+        # the forward and inverse x transforms, nx multiply-adds per cell each; form 2 (2D
+        # sine basis) runs four, 2 (nx + ny) multiply-adds per cell in all
+        form = _plane_form(N)
+        flops_per_cell = 4.0 * N if form == 1 else 4.0 * (N + N)
+        out["plane_form"] = form
         out["plane_math"] = math
-        out["tflops"] = flops * sweeps * steps / (vms / 1e3) / 1e12
+        out["tflops"] = flops_per_cell * rate / 1e3
         if math in ("tf32", "3xtf32"):
             # tensor work: one TF32 product per contraction, three for split-TF32; the TF32
             # dense peak is taken as half the measured BF16 GEMM rate (nominal 1:2 ratio)
@@ -297,9 +374,16 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
             out["tensor_tflops"] = out["tflops"] * passes
             out["tensor_frac_of_tf32_peak"] = out["tensor_tflops"] / tf32_peak
             out["tf32_peak_tflops"] = tf32_peak
+        if dt == "f64":
+            out["alu_frac_of_fp64_fma_rate"] = out["tflops"] / 2 * 1e3 / fma
     if blk == "line" and dt == "f64":
-        # ALU roof: 8 FP64 operations per cell for the sequential gather/Thomas/update
-        out["alu_frac_of_fp64_fma_peak"] = rate * 8 / 626.9
+        # FP64 pipe roof: 7 operations per cell (6 for Gauss-Seidel with omega = 1, whose
+        # update is the solve itself)
+        ops = 6 if meth == "gs" else 7
+        out["fp64_ops_per_cell"] = ops
+        out["alu_frac_of_fp64_fma_rate"] = rate * ops / fma
+    if dt == "f64":
+        out["fp64_fma_rate_g"] = fma
     return out
 
 
@@ -557,10 +641,11 @@ def _variant_adjoint(brs, stream):
 
 VARIANTS = {
     # name: (block, method, dtype, coeffs, steps, sweeps per step, plane math)
+    "line_jacobi_f32": ("line", "jacobi", "f32", COEFFS, 6, 50, "auto"),
     "line_gs_f32": ("line", "gs", "f32", COEFFS, 6, 50, "auto"),
     "line_jacobi_f32_aniso": ("line", "jacobi", "f32", (1.0, 1.0, 0.01), 6, 50, "auto"),
-    "line_jacobi_f64": ("line", "jacobi", "f64", COEFFS, 4, 50, "auto"),
-    "line_gs_f64": ("line", "gs", "f64", COEFFS, 4, 50, "auto"),
+    "line_jacobi_f64_aniso": ("line", "jacobi", "f64", (1.0, 1.0, 0.01), 2, 50, "auto"),
+    "line_gs_f64": ("line", "gs", "f64", COEFFS, 2, 50, "auto"),
     "plane_jacobi_f32_3xtf32": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 4, 10, "3xtf32"),
     "plane_gs_f32_3xtf32": ("plane", "gs", "f32", (1.0, 1.0, 0.01), 4, 10, "3xtf32"),
     "plane_jacobi_f32_tf32": ("plane", "jacobi", "f32", (1.0, 1.0, 0.01), 4, 10, "tf32"),
@@ -676,11 +761,10 @@ def main():
 
     stream = torch.cuda.current_stream()
     cells = N * N * N
-    u0, b_h = _inputs("f32")
+    u0, b_h = _inputs("f64")
     u = u0.cuda()
     b = b_h.cuda()
-    ctx = brs.Context(N, N, N, COEFFS, block="line", method="jacobi", dtype="f32")
-    cfg = brs.lib()  # noqa: F841  (library loaded)
+    ctx = brs.Context(N, N, N, COEFFS, block="line", method="jacobi", dtype="f64")
 
     sampler = ClockSampler(local)
     ms = _time_sweeps(ctx, u, b, args.steps, args.warmup, SWEEPS_PER_STEP, stream, barrier)
@@ -688,16 +772,31 @@ def main():
     ms = max_over_ranks(ms, ws)
     sweeps_total = args.steps * SWEEPS_PER_STEP
     value = whole_job_rate(cells, sweeps_total, ms / 1e3, ws)
-    launch_s = ms / 1e3 / sweeps_total  # one kernel launch per sweep, back to back
-    alg_bytes = 3 * 4 * cells
+
+    # roofs of the sweep kernel: FP64 pipe operations (binding) and HBM bytes
+    launch_ms = _launch_ms(ctx, u, b, stream)
+    fma_rate = _live_fp64_fma_rate(brs, stream)
+    ops_per_cell = 7  # gather 2 adds + 2 FMAs, one FMA per elimination direction, update FMA
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    smax = clocks.get("sm_max_mhz") or 2070.0
+    alu_achieved = ops_per_cell * cells / (launch_ms / 1e3) / 1e9
+    kernel = "xline_twist_kernel<false> (FP64 x-line Jacobi, omega = 0.8)"
+    traffic = _traffic_record("line_twist_f64_256cubed.md", ["line_seq.cu", "brs_internal.cuh"])
+    roofline = {"bound": "alu", "achieved": alu_achieved, "peak": fma_rate / 1e9,
+                "unit": "GFP64op/s", "frac": alu_achieved / (fma_rate / 1e9),
+                "traffic": traffic, "kernel": kernel, "ops_per_cell": ops_per_cell,
+                "op": "one FP64 pipe instruction (FMA or ADD)",
+                "launch_ms": launch_ms, "launches_per_step": SWEEPS_PER_STEP,
+                "peak_source": "FP64 FMA probe kernel timed in this run (CUDA events)",
+                "peak_derived": 2 * sm * smax / 1e3,
+                "peak_derived_note": "2 FP64 FMA per clock per SM x SMs x max SM clock (GHz)"}
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / launch_s / 1e9
+    hbm_achieved = 3 * 8 * cells / (launch_ms / 1e3) / 1e9
     live = _live_copy_gbs()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _traffic_record(),
-                "live_copy_gbs": live, "frac_of_live_copy": achieved / live,
-                "kernel": "line_tma_kernel<float,8,32,Jacobi>",
-                "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} hbm_gbs"}
+    roofline_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
+                    "frac": hbm_achieved / peak, "traffic": traffic, "kernel": kernel,
+                    "alg_bytes_per_launch": 3 * 8 * cells, "live_copy_gbs": live,
+                    "peak_source": f"{peak_kind} hbm_gbs"}
 
     # end to end through the host-buffer entry point (pinned host arrays): every step copies
     # its u and b in, sweeps, and copies u back.  Steps are independent problems, so they
@@ -707,7 +806,7 @@ def main():
     bh = b_h.pin_memory()
     uhs = [u0.pin_memory(), u0.clone().pin_memory()]
     streams = [stream, torch.cuda.Stream()]
-    ctx2 = brs.Context(N, N, N, COEFFS, block="line", method="jacobi", dtype="f32")
+    ctx2 = brs.Context(N, N, N, COEFFS, block="line", method="jacobi", dtype="f64")
     ctxs = [ctx, ctx2]
     e2e_steps = max(4, min(args.steps, 40))
     for q in range(4):
@@ -728,7 +827,7 @@ def main():
             raise RuntimeError("device status raised during the end-to-end steps")
     e2e_s = max_over_ranks(e2e_s, ws)
     e2e = {"value": whole_job_rate(cells, SWEEPS_PER_STEP * e2e_steps, e2e_s, ws), "unit": UNIT,
-           "h2d_bytes_per_step": 2 * 4 * cells, "d2h_bytes_per_step": 4 * cells,
+           "h2d_bytes_per_step": 2 * 8 * cells, "d2h_bytes_per_step": 8 * cells,
            "steps": e2e_steps,
            "timer": "host wall clock; steps alternate over two contexts and streams "
                     "(brsmooth_sweep_host_async), clock stopped after both streams drain"}
@@ -744,15 +843,18 @@ def main():
     cpu = None if args.no_cpu else _cpu_baseline()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "grid256_iso: 256^3 x-line block Jacobi, a=(1,1,1), omega=0.8, "
-                                   "FP32, b=h^2 f, f,u0 ~ U[-1,1] seeded",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "grid256_iso_f64: 256^3 x-line block Jacobi, a=(1,1,1), "
+                                   "omega=0.8, FP64, b=h^2 f, f,u0 ~ U[-1,1] seeded",
                        "nx": N, "ny": N, "nz": N, "sweeps_per_step": SWEEPS_PER_STEP,
                        "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2: u, b and the Jacobi buffer are 192 MB "
-                             "per sweep vs the 129 MB L2"},
-            "gpu_launches": sweeps_total, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "variants": variants}
+                       "l2": "inputs larger than L2: u, b and the line-major copies are "
+                             "134 MB each (FP64) vs the 129 MB L2"},
+            "gpu_launches": args.steps * (SWEEPS_PER_STEP + 3),
+            "gpu_launches_note": "per step: 2 copies into the line-major layout, 50 sweeps, "
+                                 "1 copy back",
+            "roofline": roofline, "roofline_hbm": roofline_hbm, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks, "variants": variants}
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -111,6 +111,15 @@ typedef struct brs_params {
  * runs all its sweeps, and permutes u back: three grid passes per call, whatever nsweeps.
  * Chaotic GS visits the lines in the permuted order.  Limits: the line length (ny or nz)
  * as for x-lines, and nz <= 65535 (y-lines) or ny <= 65535 (z-lines).
+ * FP64 x-line blocks: the sweeps run on line-major copies of u and b (cell index i
+ * outermost, the lines of each row k split by colour (j+k) mod 2), so the context holds
+ * three more buffers of nx*nz*2*ceil(ny/2) doubles and each brsmooth_sweep call copies u
+ * and b in and u back (three grid passes per call).  Each line is eliminated from both ends
+ * by two threads with pivots factored once (Sec. 2 / Sec. 4.3: invert once, reuse).
+ * Chaotic GS on these contexts visits the lines in two colours, j+k even then odd, each
+ * colour reading the other colour's newest values: the red-black line order, one
+ * admissible order of the chaotic scheme, deterministic.  BRSMOOTH_LINE_SEQ=0 in the
+ * environment at creation selects the lane-scan kernel of the FP32 path instead.
  */
 int brsmooth_create(const brs_params* p, brs_ctx** out);
 
@@ -303,6 +312,16 @@ int brsmooth_line_jacobi_noalloc(int nx, int ny, int nz, double ax, double ay, d
  * Errors: BRS_ERR_ARG (null context or limit out of range), BRS_ERR_CUDA.
  */
 int brsmooth_selftest_wait(brs_ctx* c, long long limit_ns, void* stream);
+
+/*
+ * Measurement helper (no counterpart in the paper): enqueues `blocks` CTAs of 256 threads,
+ * each thread running `iters` iterations of 8 independent FP64 fused multiply-adds, and
+ * writes one double per thread to the device array `out` (blocks * 256 elements, caller
+ * owned).  blocks * 256 * iters * 8 FMAs in total: timed with events on `stream`, this is
+ * the FP64 FMA rate of the GPU, the roof of the FP64 x-line sweeps.
+ * Errors: BRS_ERR_ARG (null out, blocks < 1, iters < 1), BRS_ERR_CUDA.
+ */
+int brsmooth_probe_fp64_fma(double* out, int blocks, int iters, void* stream);
 
 /* Number of cell updates one sweep performs (nx*ny*nz summed over patches). */
 long long brsmooth_cells(const brs_ctx* c);

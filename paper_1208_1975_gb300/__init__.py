@@ -494,3 +494,11 @@ def brsmooth_selftest_wait(ctx, limit_ns: int, stream) -> int:
     fn.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
     fn.restype = ctypes.c_int
     return fn(ctx, int(limit_ns), ctypes.c_void_p(stream))
+
+
+def brsmooth_probe_fp64_fma(out_ptr, blocks: int, iters: int, stream) -> int:
+    """FP64 FMA-bound measurement kernel (see the C header): blocks*256*iters*8 FMAs."""
+    fn = lib().brsmooth_probe_fp64_fma
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    return fn(out_ptr, int(blocks), int(iters), ctypes.c_void_p(stream))

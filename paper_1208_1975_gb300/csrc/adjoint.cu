@@ -577,9 +577,11 @@ extern "C" int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, co
             adjoint_teardown(c);
             return rc;
         }
-        // only its line kernel is used: no Jacobi buffer, and faults land in this context
+        // only its line kernel is used: no Jacobi buffer or line-major copies, and faults
+        // land in this context
         cudaFree(A->xctx->scratch);
         A->xctx->scratch = nullptr;
+        line_seq_teardown(A->xctx);
         A->xstatus = A->xctx->dev_status;
         A->xctx->dev_status = c->dev_status;
     }

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -171,6 +172,7 @@ void free_ctx(brs_ctx* c)
     if (!c)
         return;
     line_teardown(c);
+    line_seq_teardown(c);
     plane_teardown(c);
     box_teardown(c);
     batched_teardown(c);
@@ -285,9 +287,13 @@ int brsmooth_create(const brs_params* p, brs_ctx** out)
         return brs_cuda_status(e);
     }
     *c->dev_status = 0;
-    if (p->block == BRS_XLINE)
+    if (p->block == BRS_XLINE) {
         rc = line_setup(c);
-    else if (p->block == BRS_XYPLANE)
+        // FP64 lines: the twisted-elimination path (BRSMOOTH_LINE_SEQ=0: the lane-scan kernel)
+        const char* ev = std::getenv("BRSMOOTH_LINE_SEQ");
+        if (rc == BRS_OK && p->dtype == BRS_F64 && !(ev && ev[0] == '0'))
+            rc = line_seq_setup(c);
+    } else if (p->block == BRS_XYPLANE)
         rc = plane_setup(c);
     else if (p->block == BRS_BOX)
         rc = box_setup(c);
@@ -339,6 +345,8 @@ int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream
         return batched_sweep(c, u, b, nsweeps, s);
     if (c->perm)
         return perm_sweep(c, u, b, nsweeps, s);
+    if (c->lseq)
+        return line_seq_sweep(c, u, b, nsweeps, s);
     if (c->p.method == BRS_CHAOTIC_GS) {
         for (int k = 0; k < nsweeps && rc == BRS_OK; ++k)
             rc = sweep_one(c, u, u, b, s);

@@ -77,6 +77,8 @@ struct brs_ctx {
     float* dc_c = nullptr;
     // adjoint-sweep state (owned by adjoint.cu)
     void* adjoint = nullptr;
+    // FP64 x-line sweeps on the line-major copy (owned by line_seq.cu); null otherwise
+    void* lseq = nullptr;
     // y-line / z-line blocks (api.cu): an x-line context of the permuted grid and the
     // permuted copies of u and b it sweeps
     brs_ctx* perm = nullptr;
@@ -93,6 +95,12 @@ int line_setup(brs_ctx* c);
 void line_teardown(brs_ctx* c);
 // One sweep from `uin` into `uout` (Jacobi) or in place (GS: uin == uout).
 int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s);
+
+// FP64 x-line path (line_seq.cu): one thread per half line, elimination from both ends,
+// on a line-major colour-split copy of u and b made by each call.
+int line_seq_setup(brs_ctx* c);
+void line_seq_teardown(brs_ctx* c);
+int line_seq_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s);
 
 // Residual (residual.cu) -------------------------------------------------------------------
 int residual_setup(brs_ctx* c);

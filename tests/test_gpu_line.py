@@ -2,8 +2,10 @@
 
 Block Jacobi is deterministic: one GPU sweep from a given iterate is compared element by
 element with the oracle's sweep from the same iterate (relative max-norm <= 1e-12 FP64,
-<= 1e-5 FP32).  Chaotic block Gauss-Seidel is not reproducible; it is judged by the
-componentwise Perron bound, a residual bracket and convergence to the exact solution.
+<= 1e-5 FP32).  FP64 chaotic Gauss-Seidel visits the lines in the red-black order (j+k even,
+then odd), which the oracle's zebra order reproduces element by element.  FP32 chaotic
+Gauss-Seidel is not reproducible; it is judged by the componentwise Perron bound, a
+residual bracket and convergence to the exact solution.
 """
 import numpy as np
 import pytest
@@ -49,6 +51,34 @@ def test_jacobi_one_sweep_parity(brs, orc, dt, shape, a):
     ref = orc.sweep(u, b, a, block="line", method="jacobi", omega=0.8)
     got = gpu_sweep(brs, u, b, a, dt=dt)
     assert rel_max_err(got, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("shape", [(24, 13, 7), (33, 17, 9), (1, 5, 3), (4, 1, 1), (256, 9, 6),
+                                   (512, 3, 3), (7, 32, 5)], ids=str)
+@pytest.mark.parametrize("omega", [1.0, 0.7])
+@pytest.mark.parametrize("a", [(1.0, 1.0, 1.0), (1.0, 0.1, 0.01)], ids=["iso", "aniso_yz"])
+def test_gs_f64_red_black_equals_oracle_zebra(brs, orc, shape, omega, a):
+    """FP64 x-line GS = the oracle's zebra order (j+k even lines, then odd), 3 sweeps."""
+    nx, ny, nz = shape
+    u, b = initial_guess((nz, ny, nx)), rhs((nz, ny, nx))
+    ref = u
+    for _ in range(3):
+        ref = orc.sweep(ref, b, a, block="line", method="gs_zebra", omega=omega)
+    got = gpu_sweep(brs, u, b, a, dt="f64", method="gs", omega=omega, nsweeps=3)
+    assert rel_max_err(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 9), (256, 9, 6), (100, 7, 5)], ids=str)
+def test_f64_lane_scan_kernel_still_matches(brs, orc, shape, monkeypatch):
+    """BRSMOOTH_LINE_SEQ=0 selects the lane-scan kernel for FP64 (also what the adjoint's
+    undamped sweeps run); it stays within 1e-12 of the oracle."""
+    monkeypatch.setenv("BRSMOOTH_LINE_SEQ", "0")
+    nx, ny, nz = shape
+    a = (1.0, 1.0, 0.01)
+    u, b = initial_guess((nz, ny, nx)), rhs((nz, ny, nx))
+    ref = orc.sweep(orc.sweep(u, b, a, block="line", omega=0.8), b, a, block="line", omega=0.8)
+    got = gpu_sweep(brs, u, b, a, dt="f64", nsweeps=2)
+    assert rel_max_err(got, ref) <= 1e-12
 
 
 @pytest.mark.parametrize("omega", [0.5, 1.0, 1.3])
@@ -289,3 +319,50 @@ def test_full_size_256_sampled_lines(brs, orc, dt, a):
     lines = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (7, 8), (8, 7), (128, 129)]
     lines += [tuple(x) for x in rng.integers(0, n, size=(50, 2))]
     assert _sampled_lines(orc, u, b, a, got, lines) <= TOL[dt]
+
+
+def _sampled_lines_after(orc, u, b, a, got, lines, nsweeps, omega=0.8):
+    """Oracle Jacobi after `nsweeps` sweeps for selected lines, each from the sub-grid of
+    lines within distance `nsweeps` in j and k (a line's value after s sweeps depends only
+    on the lines within distance s; cut edges that are not grid boundaries corrupt lines at
+    most s-1 away from them, never the centre)."""
+    nz, ny, nx = u.shape
+    worst = 0.0
+    for (j, k) in lines:
+        j0, j1 = max(0, j - nsweeps), min(ny, j + nsweeps + 1)
+        k0, k1 = max(0, k - nsweeps), min(nz, k + nsweeps + 1)
+        sub_u, sub_b = u[k0:k1, j0:j1], b[k0:k1, j0:j1]
+        for _ in range(nsweeps):
+            sub_u = orc.sweep(sub_u, sub_b, a, block="line", method="jacobi", omega=omega)
+        worst = max(worst, rel_max_err(got[k, j], sub_u[k - k0, j - j0]))
+    return worst
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_full_size_256_five_sweeps_in_one_call(brs, orc, dt):
+    """256^3 x-line Jacobi in the benchmark's launch configuration, 5 sweeps in one call
+    (back-to-back dependent launches): bitwise equal to 5 one-sweep calls, and sampled lines
+    equal to the oracle after 5 sweeps."""
+    import torch
+
+    n, K = 256, 5
+    a = (1.0, 1.0, 1.0)
+    td = torch.float64 if dt == "f64" else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(11)
+    u0 = (torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1).to(td)
+    bt = ((torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1)
+          / (n + 1) ** 2).to(td)
+    with brs.Context(n, n, n, a, dtype=dt) as ctx:
+        one = u0.clone()
+        ctx.sweep(one, bt, K)
+        many = u0.clone()
+        for _ in range(K):
+            ctx.sweep(many, bt, 1)
+        torch.cuda.synchronize()
+        assert ctx.last_error() == 0
+    assert torch.equal(one, many)
+    u, b, got = to_np(u0), to_np(bt), to_np(one)
+    rng = np.random.default_rng(5)
+    lines = [(0, 0), (n - 1, n - 1), (3, n - 2), (128, 129)]
+    lines += [tuple(x) for x in rng.integers(0, n, size=(12, 2))]
+    assert _sampled_lines_after(orc, u, b, a, got, lines, K) <= TOL[dt]
