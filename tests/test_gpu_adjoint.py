@@ -77,6 +77,24 @@ def test_adjoint_128_fp64_vs_oracle(brs, orc):
     np.testing.assert_allclose(ga, gar, rtol=1e-9)
 
 
+@pytest.mark.parametrize("n", [128, 384])
+def test_adjoint_fp32_bench_sizes_vs_oracle(brs, orc, n):
+    """The FP32 differentiation workloads (8 sweeps, checkpoint every 4) in the benchmark's
+    kernels (z-march update, one-wave line M^-1), element by element against the oracle's
+    FP64 reverse-mode gradients."""
+    shape = (n, n, n)
+    a = (1.0, 1.0, 1.0)
+    u0 = initial_guess(shape).astype(np.float32).astype(np.float64)
+    b = rhs(shape).astype(np.float32).astype(np.float64)
+    ut = uniform_field(shape, SEED_TARGET)
+    L, gu, gb, ga = gpu_grads(brs, b, u0, ut, a, 8, 4, "f32")
+    Lr, gur, gbr, gar = orc.adjoint_gradients(u0, b, a, 8, ut, block="line", omega=0.8)
+    assert abs(L - Lr) <= 1e-5 * abs(Lr)
+    assert rel_max_err(gu, gur) <= 2e-5
+    assert rel_max_err(gb, gbr) <= 2e-5
+    np.testing.assert_allclose(ga, gar, rtol=1e-4)
+
+
 def _loss(brs, b, u0, ut, a, K, dt="f64"):
     import torch
 

@@ -115,6 +115,28 @@ def test_600_patch_workload_sampled(brs, orc):
             assert rel_max_err(bc.patch(got, q), ref) <= TOL["f32"], q
 
 
+def test_600_patch_gs_perron_bound_20_sweep_graph_calls(brs, orc):
+    """The 600-patch set, FP32 chaotic line GS, 20 sweeps per call as the benchmark runs it
+    (one persistent launch per sweep, the call replayed as a CUDA graph), two calls: with
+    b = 0 and the positive (1,1,1) mode in every patch, 0 <= u_k <= g^k u_0 componentwise
+    after 20 and 40 sweeps (g: the undamped x-line Jacobi factor of each patch's mode)."""
+    dims = batched_patch_dims(600)
+    a = (1.0, 1.0, 1.0)
+    u0 = np.concatenate([sine_mode(nx, ny, nz, 1, 1, 1).ravel() for nx, ny, nz in dims])
+    g = np.array([orc.mode_factor(nx, ny, nz, a, "line", 1.0)[0, 0, 0] for nx, ny, nz in dims])
+    sizes = dims.prod(axis=1)
+    with brs.BatchedContext(dims, a, method="gs", dtype="f32") as bc:
+        ut, bt = to_dev(u0, "f32"), to_dev(np.zeros_like(u0), "f32")
+        u0r = to_np(ut)
+        for done in (20, 40):
+            bc.sweep(ut, bt, 20)
+            got = to_np(ut)
+            slack = 2e-6 * (1 + done)
+            assert np.all(got >= -slack)
+            assert np.all(got <= np.repeat(g ** done, sizes) * u0r + slack)
+        assert bc.last_error() == 0
+
+
 def test_batched_argument_errors(brs):
     p = brs.brs_params(1, 1, 1, 1.0, 1.0, 1.0, brs.BRS_XLINE, brs.BRS_CHAOTIC_GS, brs.BRS_F32, 0.0, 0)
     assert brs.brsmooth_create_batched([(16, 16, 0)], p)[0] == brs.BRS_ERR_ARG

@@ -2,7 +2,9 @@
 
 The oracle solves each plane block with a once-factored banded Cholesky, so the two
 paths share nothing but the definition of the block.  Jacobi: element-wise per-sweep
-parity; chaotic GS: Perron bound, residual bracket and convergence to A^{-1} b.
+parity.  Gauss-Seidel on the GPU visits the even planes, then the odd ones: element-wise
+parity with the oracle's zebra order, plus the Perron bound, the residual bracket and
+convergence to A^{-1} b.
 """
 import numpy as np
 import pytest
@@ -253,3 +255,98 @@ def test_plane_xdst_form_ragged_simt(brs, orc, shape, monkeypatch):
         ut, bt = to_dev(u, "f64"), to_dev(b, "f64")
         c.sweep(ut, bt, 200)
         assert c.residual(ut, bt) < orc.residual_norm(u, b, a)
+
+
+# ----------------------------------------------------------------- GS order, bench sizes
+
+@pytest.mark.parametrize("dt,math", [("f64", "simt"), ("f32", "3xtf32"), ("f32", "simt")])
+@pytest.mark.parametrize("shape", [(32, 32, 7), (64, 96, 6), (33, 17, 5)], ids=str)
+@pytest.mark.parametrize("omega", [1.0, 0.7])
+def test_plane_gs_equals_oracle_zebra(brs, orc, dt, math, shape, omega):
+    """Plane Gauss-Seidel on the GPU updates the even planes, then the odd planes from the
+    new even ones: the oracle's zebra order, element by element (3 sweeps)."""
+    nx, ny, nz = shape
+    if math == "3xtf32" and (nx % 32 or ny % 32):
+        pytest.skip("tensor-core plane products need nx, ny multiples of 32")
+    a = (1.0, 1.0, 0.01)
+    u = rounded(initial_guess((nz, ny, nx)), dt)
+    b = rounded(rhs((nz, ny, nx)), dt)
+    ref = u
+    for _ in range(3):
+        ref = orc.sweep(ref, b, a, block="plane", method="gs_zebra", omega=omega)
+    got = gpu_run(brs, u, b, a, dt=dt, method="gs", nsweeps=3, math=math, omega=omega)
+    assert rel_max_err(got, ref) <= TOL[dt]
+
+
+@pytest.fixture(scope="module")
+def plane512(orc):
+    """512 x 512 x 3, a = (1, 0.1, 0.01) (the 512^3 defect-correction coefficients): inputs
+    representable in FP32 (one input for every arithmetic) and the oracle's Jacobi sweep,
+    whose banded Cholesky of the 512^2 plane block is factored once."""
+    n, nz = 512, 3
+    a = (1.0, 0.1, 0.01)
+    u = rounded(initial_guess((nz, n, n)), "f32")
+    b = rounded(rhs((nz, n, n)), "f32")
+    return u, b, a, orc.sweep(u, b, a, block="plane", method="jacobi", omega=0.8)
+
+
+@pytest.mark.parametrize("dt,math", [("f32", "3xtf32"), ("f32", "tf32"), ("f64", "simt")])
+def test_plane_512_jacobi_vs_banded_cholesky(brs, plane512, dt, math):
+    """The 512-wide plane solve that the 512^3 workload runs, every plane against the
+    oracle's banded Cholesky."""
+    u, b, a, ref = plane512
+    got = gpu_run(brs, u, b, a, dt=dt, math=math)
+    assert rel_max_err(got, ref) <= (2.0 ** -11 if math == "tf32" else TOL[dt])
+
+
+@pytest.mark.parametrize("dt,math", [("f32", "3xtf32"), ("f32", "tf32"), ("f64", "simt")])
+def test_plane_512_single_mode_damping(brs, orc, dt, math):
+    """512 x 512 x 4: a sine mode is scaled by the closed-form g = 1 - omega lambda/mu."""
+    nx = ny = 512
+    nz = 4
+    a = (1.0, 0.1, 0.01)
+    g = orc.mode_factor(nx, ny, nz, a, "plane", 0.8)
+    tol = 2.0 ** -10 if math == "tf32" else 4 * TOL[dt]
+    with brs.Context(nx, ny, nz, a, block="plane", method="jacobi", dtype=dt,
+                     plane_math=math) as ctx:
+        for (p, q, r) in [(1, 1, 1), (512, 512, 4), (37, 301, 2)]:
+            m = rounded(sine_mode(nx, ny, nz, p, q, r), dt)
+            ut, bt = to_dev(m, dt), to_dev(np.zeros_like(m), dt)
+            ctx.sweep(ut, bt, 1)
+            got = to_np(ut)
+            err = np.max(np.abs(got - g[r - 1, q - 1, p - 1] * m)) / np.max(np.abs(m))
+            assert err <= tol, (p, q, r, err)
+        assert ctx.last_error() == 0
+
+
+@pytest.mark.parametrize("dt,math", [("f32", "3xtf32"), ("f64", "simt")])
+def test_full_size_256_plane_three_sweeps_in_one_call(brs, orc, dt, math):
+    """256^3 plane Jacobi (a = (1, 1, 0.01)) in the benchmark's launch configuration:
+    3 sweeps in one call equal 3 one-sweep calls bit for bit, and sampled planes equal the
+    oracle after 3 sweeps (a plane after s sweeps depends only on planes within s of it)."""
+    import torch
+
+    n, K = 256, 3
+    a = (1.0, 1.0, 0.01)
+    td = torch.float64 if dt == "f64" else torch.float32
+    gen = torch.Generator(device="cuda").manual_seed(13)
+    u0 = (torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen) * 2 - 1).to(td)
+    bt = ((torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen) * 2 - 1)
+          / (n + 1) ** 2).to(td)
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype=dt,
+                     plane_math=math) as ctx:
+        one = u0.clone()
+        ctx.sweep(one, bt, K)
+        many = u0.clone()
+        for _ in range(K):
+            ctx.sweep(many, bt, 1)
+        torch.cuda.synchronize()
+        assert ctx.last_error() == 0
+    assert torch.equal(one, many)
+    u, b, got = to_np(u0), to_np(bt), to_np(one)
+    for k in (0, 131, n - 1):
+        k0, k1 = max(0, k - K), min(n, k + K + 1)
+        sub = u[k0:k1]
+        for _ in range(K):
+            sub = orc.sweep(sub, b[k0:k1], a, block="plane", method="jacobi", omega=0.8)
+        assert rel_max_err(got[k], sub[k - k0]) <= TOL[dt]

@@ -87,9 +87,13 @@ def test_asymptotic_jacobi_factor_falls_with_block_size(brs):
     assert all(x > y for x, y in zip(facs, facs[1:])), facs
 
 
-@pytest.mark.parametrize("box", PAPER_SIZES, ids=lambda s: "x".join(map(str, s)))
-def test_two_colour_gs_factor_is_square_of_jacobi(brs, box):
-    gj = window_factor(brs, "box", box, "jacobi", 2000, 100)
-    gg = window_factor(brs, "box", box, "gs", 1000, 100)
+@pytest.mark.parametrize("block,box", [("box", b) for b in PAPER_SIZES]
+                         + [("line", (0, 0, 0)), ("plane", (0, 0, 0))],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else v)
+def test_two_colour_gs_factor_is_square_of_jacobi(brs, block, box):
+    """Also for FP64 x-lines (red-black lines, j+k even then odd) and xy-planes (even, then
+    odd planes): both block partitions are 2-cyclic in those colours."""
+    gj = window_factor(brs, block, box, "jacobi", 2000, 100)
+    gg = window_factor(brs, block, box, "gs", 1000, 100)
     rho = 1 - (1 - gj) / 0.8
     assert abs(gg - rho * rho) <= 2e-5, (gj, gg, rho * rho)
