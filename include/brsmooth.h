@@ -287,16 +287,20 @@ int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, const void* b
  * and allocates nothing: the second vector and the line factor tables live in fixed
  * file-scope device arrays of the library, sized for BRSMOOTH_NOALLOC_MAX_CELLS cells
  * (8 MiB plus 32 KiB, held by every GPU that loads the library until the process exits).
- * It computes exactly what brsmooth_sweep computes for a BRS_XLINE / BRS_JACOBI context
- * with the same dims, coefficients, omega (<= 0 selects 0.8) and dtype: `nsweeps` sweeps on
- * device grid `u` (in/out) with right-hand side `b`, the result left in `u`.
+ * The factor tables are built on the device by a one-thread kernel from the coefficients,
+ * so the call copies nothing from the host and only enqueues work on `stream`.
+ * It computes what brsmooth_sweep computes for a BRS_XLINE / BRS_JACOBI context with the
+ * same dims, coefficients, omega (<= 0 selects 0.8) and dtype, with the lane-scan line
+ * kernel: `nsweeps` sweeps on device grid `u` (in/out) with right-hand side `b`, the
+ * result left in `u`.
  * The first call on each device looks up the arrays' device addresses (with that device
  * current); make that first call before any stream capture.  All calls share the arrays
  * and each call rewrites what it uses (tables and second vector are fully overwritten, so
  * nothing carries over); calls whose GPU work overlaps (different streams or threads)
  * race on them.  Errors: BRS_ERR_ARG (dims < 1, null, misaligned or aliased arrays,
- * nsweeps < 0, bad coefficients or dtype), BRS_ERR_UNSUPPORTED (nx*ny*nz greater than
- * BRSMOOTH_NOALLOC_MAX_CELLS, or nx > 512), BRS_ERR_CUDA.
+ * nsweeps < 0, non-positive or non-finite coefficients, non-finite omega or omega >= 2,
+ * bad dtype), BRS_ERR_UNSUPPORTED (nx*ny*nz greater than BRSMOOTH_NOALLOC_MAX_CELLS, or
+ * nx > 512), BRS_ERR_CUDA.
  */
 #define BRSMOOTH_NOALLOC_MAX_CELLS (1 << 20)
 int brsmooth_line_jacobi_noalloc(int nx, int ny, int nz, double ax, double ay, double az,

@@ -8,21 +8,6 @@
 
 namespace {
 
-// Lanes per line and cells per lane for a line of nx cells (G*E >= nx, E*esize a whole
-// number of 16-byte vectors).
-bool pick_EG(int nx, int* E, int* G)
-{
-    if (nx <= 16) { *G = 4; *E = 4; }
-    else if (nx <= 32) { *G = 8; *E = 4; }
-    else if (nx <= 64) { *G = 16; *E = 4; }
-    else if (nx <= 128) { *G = 32; *E = 4; }
-    else if (nx <= 256) { *G = 32; *E = 8; }
-    else if (nx <= 384) { *G = 32; *E = 12; }
-    else if (nx <= 512) { *G = 32; *E = 16; }
-    else return false;
-    return true;
-}
-
 int env_int(const char* name, int dflt)
 {
     const char* v = std::getenv(name);
@@ -85,7 +70,7 @@ int line_setup(brs_ctx* c)
 {
     const brs_params& p = c->p;
     LineCfg L;
-    if (!pick_EG(p.nx, &L.E, &L.G))
+    if (!scan_lanes(p.nx, &L.E, &L.G))
         return BRS_ERR_UNSUPPORTED;
     const size_t es = c->esize;
     // TMA path: rows 16-byte aligned, whole lane chunks, boxes of <= 256 elements

@@ -11,9 +11,11 @@
 // In host code the arrays' names are host-side stand-ins, not device addresses, so each
 // device's addresses come from cudaGetSymbolAddress (called once per device, with that
 // device current) and are passed to the kernel as plain pointers.
+#include <cmath>
 #include <mutex>
 
 #include "line_impl.cuh"
+#include "thomas_tables.h"
 
 // Fixed scratch: the second vector of block Jacobi (sized for FP64, reused for FP32) and
 // the line factor tables (at most 4*512 + 2*5*32 entries).
@@ -62,67 +64,15 @@ int device_scratch(DevScratch* out)
     return BRS_OK;
 }
 
-bool lanes_for(int nx, int* E, int* G)
-{
-    if (nx <= 16) { *G = 4; *E = 4; }
-    else if (nx <= 32) { *G = 8; *E = 4; }
-    else if (nx <= 64) { *G = 16; *E = 4; }
-    else if (nx <= 128) { *G = 32; *E = 4; }
-    else if (nx <= 256) { *G = 32; *E = 8; }
-    else if (nx <= 384) { *G = 32; *E = 12; }
-    else if (nx <= 512) { *G = 32; *E = 16; }
-    else return false;
-    return true;
-}
-
-// Factor tables of M_line = tridiag(-ax, 2(ax+ay+az), -ax) in the layout the line kernels
-// read (forward/backward multipliers, omega*p, scan multipliers), into a caller array.
+// The line factor tables built on the device by one thread, from the coefficients passed
+// as kernel arguments: no host buffer and no host-to-device copy, so the call only
+// enqueues work.  The routine is the one the context set-up runs on the host.
 template <typename T>
-int fill_tables(T* tab, int cap, int nx, double ax, double ay, double az, double omega, int E,
-                int G)
+__global__ void noalloc_tables_kernel(T* tab, int cap, int nx, double ax, double ay, double az,
+                                      double omega, int E, int G)
 {
-    const int NP = G * E;
-    int LG = 0;
-    while ((1 << LG) < G)
-        ++LG;
-    const int n = 3 * NP + 2 * LG * G;
-    if (n > cap)
-        return -1;
-    const double d = 2.0 * (ax + ay + az);
-    double p[512], c[512], e[512];
-    for (int i = 0; i < NP; ++i)
-        p[i] = c[i] = e[i] = 0.0;
-    p[0] = 1.0 / d;
-    for (int i = 1; i < nx; ++i)
-        p[i] = 1.0 / (d - ax * ax * p[i - 1]);
-    for (int i = 1; i < nx; ++i)
-        c[i] = ax * p[i - 1];
-    for (int i = 0; i + 1 < nx; ++i)
-        e[i] = ax * p[i + 1];
-    double Af[32], Ab[32];
-    for (int l = 0; l < G; ++l) {
-        Af[l] = Ab[l] = 1.0;
-        for (int q = 0; q < E; ++q) {
-            Af[l] *= c[l * E + q];
-            Ab[l] *= e[l * E + q];
-        }
-    }
-    for (int i = 0; i < NP; ++i) {
-        tab[i] = (T)c[i];
-        tab[NP + i] = (T)e[i];
-        tab[2 * NP + i] = (T)(i < nx ? omega * p[i] : 0.0);
-    }
-    for (int t = 0; t < LG; ++t)
-        for (int l = 0; l < G; ++l) {
-            double f = 1.0, bb = 1.0;
-            for (int m = (l - (1 << t) + 1 > 0 ? l - (1 << t) + 1 : 0); m <= l; ++m)
-                f *= Af[m];
-            for (int m = l; m < G && m < l + (1 << t); ++m)
-                bb *= Ab[m];
-            tab[3 * NP + t * G + l] = (T)f;
-            tab[3 * NP + LG * G + t * G + l] = (T)bb;
-        }
-    return n;
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        scan_thomas_fill<T>(tab, cap, nx, ax, 2.0 * (ax + ay + az), omega, E, G, false);
 }
 
 template <typename T>
@@ -147,14 +97,15 @@ int run(int nx, int ny, int nz, double ax, double ay, double az, double omega, T
         const T* b, int nsweeps, cudaStream_t s, const DevScratch& scr)
 {
     int E = 0, G = 0;
-    if (!lanes_for(nx, &E, &G))
+    if (!scan_lanes(nx, &E, &G))
         return BRS_ERR_UNSUPPORTED;
-    // tables are rewritten on every call (the array keeps the previous call's contents)
-    T htab[4096];
-    const int ntab = fill_tables<T>(htab, 4096, nx, ax, ay, az, omega, E, G);
-    if (ntab < 0)
+    const int cap = (int)(sizeof(g_noalloc_tab) / sizeof(T));
+    if (scan_table_len(E, G, false) > cap)
         return BRS_ERR_UNSUPPORTED;
-    cudaError_t e = cudaMemcpyAsync(scr.tab, htab, sizeof(T) * ntab, cudaMemcpyHostToDevice, s);
+    // the tables are rewritten on every call (the array keeps the previous call's contents)
+    noalloc_tables_kernel<T><<<1, 1, 0, s>>>(static_cast<T*>(scr.tab), cap, nx, ax, ay, az,
+                                             omega, E, G);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return brs_cuda_status(e);
     const void* k = plain_kernel<T>(E, G);
@@ -201,8 +152,8 @@ extern "C" int brsmooth_line_jacobi_noalloc(int nx, int ny, int nz, double ax, d
     cudaGetLastError();  // start from a clean launch-error state
     if (nx < 1 || ny < 1 || nz < 1 || !u || !b || nsweeps < 0 || u == b)
         return BRS_ERR_ARG;
-    if (!(ax > 0.0) || !(ay > 0.0) || !(az > 0.0) || !(ax < 1e300) || !(ay < 1e300) ||
-        !(az < 1e300) || !(omega < 2.0) || omega != omega)
+    if (!(ax > 0.0) || !(ay > 0.0) || !(az > 0.0) || !std::isfinite(ax) || !std::isfinite(ay) ||
+        !std::isfinite(az) || !std::isfinite(omega) || omega >= 2.0)
         return BRS_ERR_ARG;
     if (dtype != BRS_F64 && dtype != BRS_F32)
         return BRS_ERR_ARG;

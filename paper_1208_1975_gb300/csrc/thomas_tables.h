@@ -1,4 +1,4 @@
-// Host construction of the factor tables used by the cross-lane scan Thomas solve
+// Construction of the factor tables used by the cross-lane scan Thomas solve
 // (line_solve in line_impl.cuh) for a constant symmetric tridiagonal block
 //   M = tridiag(-off, diag, -off) of size n.
 // The LU pivots are the same for every system with this (n, off, diag), so they are
@@ -10,51 +10,101 @@
 //   [3NP, 3NP+G LG)        forward scan multipliers, step t at [t G + lane]
 //   [3NP+G LG, 3NP+2G LG)  backward scan multipliers
 //   [3NP+2G LG, 4NP+2G LG) p_i (only when with_p)
+// One routine serves the host (context set-up) and the device (the allocation-free entry
+// point builds its tables in a one-thread kernel), so both paths use the same arithmetic.
 #pragma once
 
-#include <algorithm>
 #include <vector>
 
+#ifdef __CUDACC__
+#define BRS_HD __host__ __device__
+#else
+#define BRS_HD
+#endif
+
+// Largest G*E of any lane layout (32 lanes x 16 cells).
+constexpr int kScanMaxNP = 512;
+
+// Lanes per line G and cells per lane E for a line of n cells (G E >= n; E a whole number
+// of 16-byte vectors for both FP32 and FP64).  False beyond 512 cells.
+BRS_HD inline bool scan_lanes(int n, int* E, int* G)
+{
+    if (n <= 16) { *G = 4; *E = 4; }
+    else if (n <= 32) { *G = 8; *E = 4; }
+    else if (n <= 64) { *G = 16; *E = 4; }
+    else if (n <= 128) { *G = 32; *E = 4; }
+    else if (n <= 256) { *G = 32; *E = 8; }
+    else if (n <= 384) { *G = 32; *E = 12; }
+    else if (n <= 512) { *G = 32; *E = 16; }
+    else return false;
+    return true;
+}
+
+// Number of table entries for the layout (E, G).
+BRS_HD inline int scan_table_len(int E, int G, bool with_p)
+{
+    int LG = 0;
+    while ((1 << LG) < G)
+        ++LG;
+    return (with_p ? 4 : 3) * G * E + 2 * LG * G;
+}
+
+// Write the tables into tab[0 .. scan_table_len) (caller storage); -1 if the layout is
+// larger than kScanMaxNP cells or cap entries, else the entry count.
 template <typename T>
-std::vector<T> scan_thomas_tables(int n, double off, double diag, double omega, int E, int G,
-                                  bool with_p)
+BRS_HD int scan_thomas_fill(T* tab, int cap, int n, double off, double diag, double omega, int E,
+                            int G, bool with_p)
 {
     const int NP = G * E;
     int LG = 0;
     while ((1 << LG) < G)
         ++LG;
-    std::vector<double> p(NP, 0.0), c(NP, 0.0), e(NP, 0.0);
-    p[0] = 1.0 / diag;
-    for (int i = 1; i < n; ++i)
-        p[i] = 1.0 / (diag - off * off * p[i - 1]);
-    for (int i = 1; i < n; ++i)
-        c[i] = off * p[i - 1];
-    for (int i = 0; i + 1 < n; ++i)
-        e[i] = off * p[i + 1];
-    std::vector<double> Af(G, 1.0), Ab(G, 1.0);
+    const int len = scan_table_len(E, G, with_p);
+    if (NP > kScanMaxNP || G > 32 || len > cap)
+        return -1;
+    // one pass over the cells with the pivots p_{i-1}, p_i, p_{i+1} live: the only arrays
+    // are the per-lane products (a few hundred bytes of stack, so a one-thread device
+    // launch needs no larger stack than the default)
+    double Af[32], Ab[32];
     for (int l = 0; l < G; ++l)
-        for (int q = 0; q < E; ++q) {
-            Af[l] *= c[l * E + q];
-            Ab[l] *= e[l * E + q];
-        }
-    std::vector<T> tab((with_p ? 4 : 3) * NP + 2 * LG * G);
+        Af[l] = Ab[l] = 1.0;
+    double pprev = 0.0, pcur = 1.0 / diag;  // p_{i-1}, p_i (p_0 = 1/diag)
     for (int i = 0; i < NP; ++i) {
-        tab[i] = (T)c[i];
-        tab[NP + i] = (T)e[i];
-        tab[2 * NP + i] = (T)(i < n ? omega * p[i] : 0.0);
+        const double pi = i < n ? pcur : 0.0;
+        const double pnext = i + 1 < n ? 1.0 / (diag - off * off * pi) : 0.0;
+        const double ci = (i >= 1 && i < n) ? off * pprev : 0.0;  // c_i = off p_{i-1}
+        const double ei = i + 1 < n ? off * pnext : 0.0;          // e_i = off p_{i+1}
+        tab[i] = (T)ci;
+        tab[NP + i] = (T)ei;
+        tab[2 * NP + i] = (T)(omega * pi);
+        if (with_p)
+            tab[3 * NP + 2 * LG * G + i] = (T)pi;
+        Af[i / E] *= ci;
+        Ab[i / E] *= ei;
+        pprev = pi;
+        pcur = pnext;
     }
     for (int t = 0; t < LG; ++t)
         for (int l = 0; l < G; ++l) {
             double f = 1.0, b = 1.0;
-            for (int m = std::max(0, l - (1 << t) + 1); m <= l; ++m)
+            const int m0 = l - (1 << t) + 1;
+            for (int m = m0 > 0 ? m0 : 0; m <= l; ++m)
                 f *= Af[m];
             for (int m = l; m < G && m < l + (1 << t); ++m)
                 b *= Ab[m];
             tab[3 * NP + t * G + l] = (T)f;
             tab[3 * NP + LG * G + t * G + l] = (T)b;
         }
-    if (with_p)
-        for (int i = 0; i < NP; ++i)
-            tab[3 * NP + 2 * LG * G + i] = (T)(i < n ? p[i] : 0.0);
+    return len;
+}
+
+// Host convenience: the tables as a vector (empty if the layout is too large).
+template <typename T>
+std::vector<T> scan_thomas_tables(int n, double off, double diag, double omega, int E, int G,
+                                  bool with_p)
+{
+    std::vector<T> tab(scan_table_len(E, G, with_p));
+    if (scan_thomas_fill<T>(tab.data(), (int)tab.size(), n, off, diag, omega, E, G, with_p) < 0)
+        tab.clear();
     return tab;
 }
