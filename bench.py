@@ -725,7 +725,9 @@ def _variant_batched(brs, stream, barrier, per_patch=True):
     out["per_patch_launches_value"] = per_patch_rate
     out["speedup_vs_per_patch"] = graph_rate / per_patch_rate
     out["vs_plain_fp64_equal_sweeps"] = _batched_vs_fp64(brs, stream, dims, u0_np, b_np)
-    out["err_vs_oracle"], out["cpu_baseline"] = _batched_cpu_leg(brs, stream, dims, u0_np, b_np)
+    if not _NO_CPU_LEGS["on"]:
+        out["err_vs_oracle"], out["cpu_baseline"] = _batched_cpu_leg(brs, stream, dims, u0_np,
+                                                                     b_np)
     return out
 
 
@@ -819,8 +821,9 @@ def _variant_level(brs, stream, barrier, which, dt="f32"):
            "unit": UNIT, "hbm_frac": rate * 3 * es / _peaks()[0],
            "without_exchange_value": _rate(cells, 3 * steps, ms0),
            "ghost_exchange_share": max(0.0, (ms - ms0) / ms)}
-    out["err_vs_oracle"], out["cpu_baseline"] = _level_cpu_leg(brs, stream, dims, nbr, u0_np,
-                                                               b_np, dt)
+    if not _NO_CPU_LEGS["on"]:
+        out["err_vs_oracle"], out["cpu_baseline"] = _level_cpu_leg(brs, stream, dims, nbr,
+                                                                   u0_np, b_np, dt)
     return out
 
 
@@ -1115,8 +1118,9 @@ def _variant_adjoint(brs, stream):
         row = {"n": n, "dtype": str(dt).replace("torch.", ""), "sweeps": 8, "ckpt": 4,
                "fwd_bwd_s": best, "value": n ** 3 * 8 / best / 1e9,
                "unit": "Gcell-updates/s (fwd+bwd)"}
-        row["err_vs_oracle"], row["cpu_baseline"] = _adjoint_cpu_leg(n, row["dtype"], bn, u0n,
-                                                                     utn, grads)
+        if not _NO_CPU_LEGS["on"]:
+            row["err_vs_oracle"], row["cpu_baseline"] = _adjoint_cpu_leg(n, row["dtype"], bn,
+                                                                         u0n, utn, grads)
         res.append(row)
         del b, u0, ut
         torch.cuda.empty_cache()
