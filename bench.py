@@ -541,6 +541,8 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
             out["tf32_peak_tflops"] = tf32_peak
         if dt == "f64":
             out["alu_frac_of_fp64_fma_rate"] = rate * nb / fma
+    if blk == "plane" and math == "auto":
+        math = "3xtf32" if dt == "f32" and N % 32 == 0 else "simt"  # the library's choice
     if blk == "plane":
         # dense contractions per plane: form 1 (x sine transform + y tridiagonal solves) runs
         # the forward and inverse x transforms, nx multiply-adds per cell each; form 2 (2D

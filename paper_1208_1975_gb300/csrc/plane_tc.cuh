@@ -568,75 +568,96 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
             if constexpr (EPI == EPI_BOX) {
                 box_epilogue<BN>(g, trow, m0 + q * 32 + lane, n0);
             } else {
-            // EPI_UPDATE: the old values of the next 32-column chunk are loaded while the
-            // current chunk is processed
-            const int mrow0 = m0 + q * 32;
-            float unext[32];
-            auto load_u = [&](int c, float (&dst)[32]) {
-                const int n = n0 + c * 32 + lane;
-                const long long ob = (long long)plane * g.plane + (long long)mrow0 * g.N + n;
+            // Row-direct epilogue: this thread's TMEM lane is output row mrow; a 32-column
+            // chunk of it is 128 contiguous bytes, written (and, for the update, the old u
+            // read) as eight 16-byte vectors.  N is a multiple of 32 on this path, so a chunk
+            // lies inside the row or wholly past it.  The old u of the next chunk is loaded
+            // while the current one is processed.
+            const int mrow = m0 + q * 32 + lane;
+            const bool mok = mrow < g.M;
+            const long long rbase = (long long)plane * g.plane + (long long)mrow * g.N;
+            float4 unext[8];
+            auto load_u = [&](int c, float4 (&dst)[8]) {
+                const int n = n0 + c * 32;
+                if (mok && n < g.N) {
+                    const float4* src = reinterpret_cast<const float4*>(g.u + rbase + n);
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    dst[i] = (n < g.N && mrow0 + i < g.M) ? g.u[ob + (long long)i * g.N] : 0.0f;
+                    for (int v = 0; v < 8; ++v)
+                        dst[v] = src[v];
+                }
             };
             if (EPI == EPI_UPDATE)
                 load_u(0, unext);
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
-                float ucur[32];
+                float4 ucur[8];
                 if (EPI == EPI_UPDATE) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        ucur[i] = unext[i];
+                    for (int v = 0; v < 8; ++v)
+                        ucur[v] = unext[v];
                     if (c + 1 < BN / 32)
                         load_u(c + 1, unext);
                 }
                 uint32_t r[32];
-                tmem_ld32(trow + (uint32_t)(c * 32), r);
-#pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    tile[lane * 33 + i] = __uint_as_float(r[i]);
-                __syncwarp();
-                const int n = n0 + c * 32 + lane;
-                const bool nok = n < g.N;
-                const int mrow = m0 + q * 32;
-                const long long obase = (long long)plane * g.plane + (long long)mrow * g.N + n;
-                float v[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    v[i] = tile[i * 33 + lane];
-                if (EPI == EPI_SCALE_SPLIT) {
-                    float sc[32];
+                tmem_ld32(trow + (uint32_t)(c * 32), r);  // warp-collective: every lane
+                const int n = n0 + c * 32;
+                if (mok && n < g.N) {
+                    const long long o = rbase + n;
+                    float v[32];
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        sc[i] = (nok && mrow + i < g.M)
-                                    ? __ldg(g.scale + (long long)(mrow + i) * g.N + n)
-                                    : 0.0f;
+                        v[i] = __uint_as_float(r[i]);
+                    if (EPI == EPI_SCALE_SPLIT) {
+                        const float4* sc4 =
+                            reinterpret_cast<const float4*>(g.scale + (long long)mrow * g.N + n);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        v[i] *= sc[i];
-                }
-                if (EPI == EPI_UPDATE) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (nok && mrow + i < g.M)
-                            g.uout[obase + (long long)i * g.N] =
-                                fmaf(g.omega, v[i], (1.0f - g.omega) * ucur[i]);
-                } else if (g.out_plain) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (nok && mrow + i < g.M)
-                            g.out_hi[obase + (long long)i * g.N] = v[i];
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (nok && mrow + i < g.M) {
-                            const uint32_t hi = tf32_rn(v[i]);
-                            g.out_hi[obase + (long long)i * g.N] = __uint_as_float(hi);
-                            if (SPLIT == 3)
-                                g.out_lo[obase + (long long)i * g.N] =
-                                    __uint_as_float(tf32_rn(v[i] - __uint_as_float(hi)));
+                        for (int w = 0; w < 8; ++w) {
+                            const float4 sc = __ldg(sc4 + w);
+                            v[4 * w + 0] *= sc.x;
+                            v[4 * w + 1] *= sc.y;
+                            v[4 * w + 2] *= sc.z;
+                            v[4 * w + 3] *= sc.w;
                         }
+                    }
+                    if (EPI == EPI_UPDATE) {
+                        const float om = g.omega, om1 = 1.0f - g.omega;
+                        float4* dst = reinterpret_cast<float4*>(g.uout + o);
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            float4 out;
+                            out.x = fmaf(om, v[4 * w + 0], om1 * ucur[w].x);
+                            out.y = fmaf(om, v[4 * w + 1], om1 * ucur[w].y);
+                            out.z = fmaf(om, v[4 * w + 2], om1 * ucur[w].z);
+                            out.w = fmaf(om, v[4 * w + 3], om1 * ucur[w].w);
+                            dst[w] = out;
+                        }
+                    } else if (g.out_plain) {
+                        float4* dst = reinterpret_cast<float4*>(g.out_hi + o);
+#pragma unroll
+                        for (int w = 0; w < 8; ++w)
+                            dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2],
+                                                 v[4 * w + 3]);
+                    } else {
+                        float hi[32], lo[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t hb = tf32_rn(v[i]);
+                            hi[i] = __uint_as_float(hb);
+                            lo[i] = __uint_as_float(tf32_rn(v[i] - hi[i]));
+                        }
+                        float4* dh = reinterpret_cast<float4*>(g.out_hi + o);
+#pragma unroll
+                        for (int w = 0; w < 8; ++w)
+                            dh[w] = make_float4(hi[4 * w], hi[4 * w + 1], hi[4 * w + 2],
+                                                hi[4 * w + 3]);
+                        if (SPLIT == 3) {
+                            float4* dl = reinterpret_cast<float4*>(g.out_lo + o);
+#pragma unroll
+                            for (int w = 0; w < 8; ++w)
+                                dl[w] = make_float4(lo[4 * w], lo[4 * w + 1], lo[4 * w + 2],
+                                                    lo[4 * w + 3]);
+                        }
+                    }
                 }
                 __syncwarp();
             }
