@@ -1177,7 +1177,7 @@ BOX_VARIANTS = {
 }
 SPECIAL = ("batched600", "level96x64", "table2_mixed", "level96x64_f64", "defect512", "adjoint",
            "block_study64")
-PROFILE_ONLY = ("batched600_graph",)
+PROFILE_ONLY = ("batched600_graph", "plane512_f32")
 
 
 # the headline workload as a named variant, for profiling runs (`--only`)
@@ -1185,11 +1185,32 @@ PROFILE_GRID = {"line_jacobi_f64_iso": ("line", "jacobi", "f64", ISO, 4, 50, "au
 _NO_CPU_LEGS = {"on": False}
 
 
+def _variant_plane512(brs, stream, barrier, steps):
+    """Plane Jacobi sweeps at 512^3, a = (1, 0.1, 0.01), FP32 split-TF32: the inner sweep of
+    the 512^3 defect correction, timed alone (for profiling)."""
+    import torch
+
+    from brs_inputs import initial_guess, rhs
+
+    n = 512
+    a = (1.0, 0.1, 0.01)
+    u = torch.from_numpy(initial_guess((n, n, n))).float().cuda()
+    b = torch.from_numpy(rhs((n, n, n))).float().cuda()
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f32") as c:
+        ms = _time_sweeps(c, u, b, steps, 1, 2, stream, barrier)
+    rate = _rate(n ** 3, 2 * steps, ms)
+    return {"workload": "grid512_aniso plane Jacobi", "dtype": "f32", "plane_math": "3xtf32",
+            "value": rate, "unit": UNIT, "ms_per_sweep": ms / (2 * steps),
+            "tensor_frac_of_tf32_peak": rate * 4.0 * n * 3 / 1e3 / (_bf16_peak() / 2)}
+
+
 def _run_variant(name, brs, stream, barrier, peak, steps=None):
     if name == "batched600":
         return _variant_batched(brs, stream, barrier)
     if name == "batched600_graph":
         return _variant_batched(brs, stream, barrier, per_patch=False)
+    if name == "plane512_f32":
+        return _variant_plane512(brs, stream, barrier, steps or 3)
     if name in ("level96x64", "table2_mixed"):
         out = _variant_level(brs, stream, barrier, name)
         out["name"] = name

@@ -414,7 +414,6 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* staging = reinterpret_cast<float*>(base + NST * STAGE);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE + STAGING);
     uint64_t* empty = full + NST;
     uint64_t* accf = empty + NST;  // accumulator a holds a finished tile
@@ -552,7 +551,6 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
     } else if (warp >= 2) {
         // epilogue: this warp reads TMEM lanes 32*(warp % 4) .. +31 = tile rows
         const int q = warp & 3;
-        float* tile = staging + (warp - 2) * (32 * 33);
         int ti = 0;
         for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
             const int a = ti & 1;
