@@ -357,8 +357,11 @@ __host__ __device__ inline int ythomas_stride(int ny)
     return s0 + (((4 - s0) % 32) + 32) % 32;
 }
 
+// FP32: at most 80 registers for lanes of <= 8 cells (3 CTAs per SM), 128 for 12-16 (2 CTAs
+// per SM: ny = 512 went from one CTA at 167 registers to two at 128 without spills, and the
+// 512^3 split-TF32 plane sweep from 60.4 to 65.5 Gcell/s on the same box).
 template <typename T, int E, int SPLIT>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 3 : 1) plane_ythomas_kernel(const T* __restrict__ cin_hi,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (E <= 8 ? 3 : 2) : 1) plane_ythomas_kernel(const T* __restrict__ cin_hi,
                                                                const T* __restrict__ cin_lo,
                                                                T* __restrict__ w_hi,
                                                                T* __restrict__ w_lo,
