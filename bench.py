@@ -830,8 +830,9 @@ def _variant_level(brs, stream, barrier, which, dt="f32"):
 
 
 def _variant_defect(brs, stream):
-    """512^3, a=(1,0.1,0.01): FP32 plane sweeps inside FP64 defect correction vs FP64 plane
-    Jacobi.  The inner sweep count per outer step m is chosen by timed full solves on 64^3
+    """512^3, a=(1,0.1,0.01): FP32 plane sweeps inside FP64 defect correction vs plain FP64
+    plane Jacobi.  The inner sweeps (block Jacobi, omega = 0.8, or two-colour block GS,
+    omega = 1) and their count per outer step m are chosen by timed full solves on 64^3
     (where the plain FP64 solve is measured too); the 512^3 mixed solve then runs to
     ||r||/||b|| <= 1e-10 and is compared with the oracle's exact solution; the plain FP64
     solve at 512^3 (about 14 000 sweeps) is a projection from timed sweeps."""
@@ -843,24 +844,26 @@ def _variant_defect(brs, stream):
     out = {"workload": "grid512_aniso defect correction", "coeffs": a, "rtol": 1e-10}
     n = 64
     b = torch.from_numpy(rhs((n, n, n))).cuda()
-    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64, \
-            brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f32") as i32:
-        # inner sweeps per outer step m in {8, 32, 128}: full solves to 1e-10, the fastest
-        # m is kept (a measured choice) and used for the 512^3 segment below
-        per_m = {}
-        for m in (8, 32, 128):
-            u = torch.zeros_like(b)
-            brs.defect_correction(o64, i32, u, b, rtol=1e-10, inner_sweeps=m, max_outer=500)
-            u.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            d_m, r_m, _ = brs.defect_correction(o64, i32, u, b, rtol=1e-10, inner_sweeps=m,
-                                                max_outer=500)
-            per_m[m] = {"outer": d_m, "inner_sweeps": d_m * m, "rel_residual": r_m,
-                        "s": time.perf_counter() - t0}
-        best_m = min(per_m, key=lambda m: per_m[m]["s"])
-        done, rel = per_m[best_m]["outer"], per_m[best_m]["rel_residual"]
-        t_mixed = per_m[best_m]["s"]
+    per = {}
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64:
+        for meth in ("jacobi", "gs"):
+            with brs.Context(n, n, n, a, block="plane", method=meth, dtype="f32") as i32:
+                # full solves to 1e-10 for m in {8, 32, 128}; the fastest (method, m) is kept
+                # (a measured choice) and used at 512^3 below
+                for m in (8, 32, 128):
+                    u = torch.zeros_like(b)
+                    brs.defect_correction(o64, i32, u, b, rtol=1e-10, inner_sweeps=m,
+                                          max_outer=500)
+                    u.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    d_m, r_m, _ = brs.defect_correction(o64, i32, u, b, rtol=1e-10,
+                                                        inner_sweeps=m, max_outer=500)
+                    per[f"{meth}_m{m}"] = {"inner": meth, "m": m, "outer": d_m,
+                                           "inner_sweeps": d_m * m, "rel_residual": r_m,
+                                           "s": time.perf_counter() - t0, "u": u.clone()}
+        best = min(per, key=lambda k: per[k]["s"])
+        best_meth, best_m = per[best]["inner"], per[best]["m"]
         u64 = torch.zeros_like(b)
         sweeps, r = 0, 1.0
         nb = float(torch.linalg.norm(b))
@@ -871,23 +874,25 @@ def _variant_defect(brs, stream):
             sweeps += 16
             r = o64.residual(u64, b) / nb
         t_f64 = time.perf_counter() - t0
-        u_mixed = torch.zeros_like(b)
-        brs.defect_correction(o64, i32, u_mixed, b, rtol=1e-10, inner_sweeps=best_m,
-                              max_outer=500)
-        ustar = _orc().exact_solve(b.cpu().numpy(), a)
-        errs = {nm: _rel_err(x.cpu().numpy(), ustar) for nm, x in
-                (("mixed", u_mixed), ("fp64", u64))}
-    out["grid64_full_solve"] = {"err_vs_oracle_exact_rel_max": errs,"inner_sweeps_m": best_m, "per_m": per_m,
-                                "mixed_outer": done, "mixed_inner_sweeps": done * best_m,
-                                "mixed_rel_residual": rel, "mixed_s": t_mixed,
-                                "fp64_sweeps": sweeps, "fp64_rel_residual": r, "fp64_s": t_f64}
+    ustar = _orc().exact_solve(b.cpu().numpy(), a)
+    errs = {"mixed": _rel_err(per[best]["u"].cpu().numpy(), ustar),
+            "fp64": _rel_err(u64.cpu().numpy(), ustar)}
+    for v in per.values():
+        del v["u"]
+    out["grid64_full_solve"] = {"err_vs_oracle_exact_rel_max": errs, "inner": best_meth,
+                                "inner_sweeps_m": best_m, "per_choice": per,
+                                "mixed_outer": per[best]["outer"],
+                                "mixed_inner_sweeps": per[best]["inner_sweeps"],
+                                "mixed_rel_residual": per[best]["rel_residual"],
+                                "mixed_s": per[best]["s"], "fp64_sweeps": sweeps,
+                                "fp64_rel_residual": r, "fp64_s": t_f64}
     # 512^3: the mixed solve run to ||r|| / ||b|| <= 1e-10 (measured), compared with the
     # oracle's exact solution; plain FP64 plane Jacobi timed on a segment and projected
     n = 512
     b_np = rhs((n, n, n))
     b = torch.from_numpy(b_np).cuda()
     with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64, \
-            brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f32") as i32:
+            brs.Context(n, n, n, a, block="plane", method=best_meth, dtype="f32") as i32:
         u = torch.zeros_like(b)
         brs.defect_correction(o64, i32, u, b, rtol=0.0, inner_sweeps=best_m, max_outer=1)
         u.zero_()
@@ -918,7 +923,7 @@ def _variant_defect(brs, stream):
     mu = a[0] * s1 + a[1] * s1 + 2 * a[2]
     g = 1 - 0.8 * lam / mu
     sweeps_needed = math.log(1e-10) / math.log(g)
-    out["grid512"] = {"inner_sweeps_m": best_m, "mixed_s_measured": t_mixed,
+    out["grid512"] = {"inner": best_meth, "inner_sweeps_m": best_m, "mixed_s_measured": t_mixed,
                       "mixed_outer": done, "mixed_inner_sweeps": done * best_m,
                       "mixed_rel_residual": rel,
                       "ms_per_fp64_plane_jacobi_sweep": ms_f64,

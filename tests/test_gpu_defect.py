@@ -43,6 +43,26 @@ def test_defect_correction_reaches_fp64_residual(brs, orc, block, method, n, a, 
     assert rel_max_err(u, orc.exact_solve(b, a)) <= 1e-7
 
 
+@pytest.mark.parametrize("method", ["jacobi", "gs"])
+def test_defect_correction_512_wide_planes(brs, orc, method):
+    """The 512 x 512 plane solve of the 512^3 workload (a = (1, 0.1, 0.01)) inside the
+    defect-correction loop, on a 512 x 512 x 6 slab: FP64 residual 1e-10, recomputed by the
+    oracle, and the distance to the exact DST solution."""
+    nx = ny = 512
+    nz = 6
+    a = (1.0, 0.1, 0.01)
+    b = rhs((nz, ny, nx))
+    with brs.Context(nx, ny, nz, a, block="plane", method="jacobi", dtype="f64") as outer, \
+            brs.Context(nx, ny, nz, a, block="plane", method=method, dtype="f32") as inner:
+        ut, bt = to_dev(np.zeros_like(b), "f64"), to_dev(b, "f64")
+        done, rel, _ = brs.defect_correction(outer, inner, ut, bt, rtol=1e-10, inner_sweeps=32,
+                                             max_outer=4000)
+        u = to_np(ut)
+    assert rel <= 1e-10 and done >= 1
+    assert orc.residual_norm(u, b, a) <= 1.05e-10 * np.linalg.norm(b)
+    assert rel_max_err(u, orc.exact_solve(b, a)) <= 1e-7
+
+
 def test_defect_correction_argument_errors(brs):
     import torch
 
