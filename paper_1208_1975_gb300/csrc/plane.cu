@@ -62,6 +62,11 @@ struct PlaneState {
     int ytab_len = 0;      // table entries per x-mode
     void* ytab = nullptr;  // [nx][ytab_len], context dtype (FP32 on the tensor path)
     CUtensorMap m_W2_hi, m_W2_lo;
+    // fused x-DST + y-Thomas product (tensor path, ny <= 256): tile N = fbn covers a whole
+    // y line, the epilogue eliminates along it; ym[y][p] are the reciprocal pivots
+    int fused = 0, fbn = 0;
+    void* ym = nullptr;
+    CUtensorMap m_Rf_hi, m_Rf_lo;  // t2 as [k][y][x], box rows fbn (B of the fused product)
 };
 
 // Tile shapes of the tensor-core products (N per CTA, ring stages): 128 x 128 tiles with a
@@ -265,6 +270,17 @@ const void* pers_kernel_for(int bn)
     if (bn == 256)
         return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 256, pers_nst(SPLIT, 256)>;
     return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 128, pers_nst(SPLIT, 128)>;
+}
+
+template <int SPLIT>
+const void* fused_kernel_for(int bn)
+{
+    using brs_tc::EPI_YTHOMAS;
+    if (bn == 64)
+        return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 64, pers_nst(SPLIT, 64)>;
+    if (bn == 128)
+        return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 128, pers_nst(SPLIT, 128)>;
+    return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 256, pers_nst(SPLIT, 256)>;
 }
 
 template <int SPLIT, int EPI>
@@ -516,6 +532,30 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
     g.kstep = kstep;
     g.plane = plane;
     g.status = c->dev_status;
+    if (P->fused) {
+        // P1 with the y-Thomas in its epilogue: t1 <- W[k][y][p] (split)
+        g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
+        g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo;
+        g.ym = (const float*)P->ym; g.ay = (float)c->p.ay;
+        int tn = 1, tm = (nx + brs_tc::BM - 1) / brs_tc::BM, nb = nbatch;
+        const long long ntiles = (long long)tm * nb;
+        const int grid = (int)(ntiles < P->sms ? ntiles : P->sms);
+        CUtensorMap a0 = P->m_sx_hi, a1 = P->m_sx_lo, b0 = P->m_Rf_hi, b1 = P->m_Rf_lo;
+        brs_tc::TcArgs gg = g;
+        void* args[] = {&a0, &a1, &b0, &b1, &gg, &tn, &tm, &nb};
+        cudaError_t e = launch_pdl_c(fused_kernel_for<SPLIT>(P->fbn), dim3(grid), dim3(192),
+                                     pers_smem(SPLIT, P->fbn), s, args);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        g.ym = nullptr;
+        // P4: X[y][x] = sum_p W[y][p] Sx[x][p]; u_k <- (1-omega) u_k + omega X
+        g.M = ny; g.N = nx; g.K = nx; g.a_batched = 1; g.b_batched = 0;
+        g.out_hi = nullptr; g.out_lo = nullptr; g.u = uin; g.uout = uout;
+        g.omega = (float)c->omega;
+        e = launch_tc<SPLIT, brs_tc::EPI_UPDATE>(P, P->m_W_hi, P->m_W_lo, P->m_sxB_hi,
+                                                 P->m_sxB_lo, g, nbatch, s);
+        return brs_cuda_status(e);
+    }
     // P1: C1[p][y] = sum_x Sx[p][x] R[y][x]  -> t1, plain FP32 (the y solve is not a
     // tensor-core operand, so it needs no TF32 split)
     g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
@@ -771,6 +811,52 @@ int tc_setup(brs_ctx* c, const std::vector<double>& sx, const std::vector<double
     return BRS_OK;
 }
 
+// Fused x-DST + y-Thomas product: on for the persistent tensor path when one tile's N (64,
+// 128 or 256) holds a whole y line.  Reciprocal pivots of tridiag(-ay, d_p, -ay), d_p =
+// ax s_p + 2 ay + 2 az, factored in FP64: m_0 = 1 / d_p, m_y = 1 / (d_p - ay^2 m_{y-1}).
+int fused_setup(brs_ctx* c)
+{
+    PlaneState* P = ps(c);
+    const brs_params& p = c->p;
+    const char* env = std::getenv("BRSMOOTH_PLANE_FUSE");
+    const bool want = env ? std::atoi(env) != 0 : true;
+    if (!want || !P->tc_persistent || p.ny > 256)
+        return BRS_OK;
+    P->fbn = p.ny <= 64 ? 64 : p.ny <= 128 ? 128 : 256;
+    std::vector<float> m((size_t)p.ny * p.nx);
+    for (int q = 0; q < p.nx; ++q) {
+        const double sp = 2.0 - 2.0 * std::cos(M_PI * (q + 1) / (p.nx + 1));
+        const double d = p.ax * sp + 2.0 * p.ay + 2.0 * p.az;
+        double piv = 1.0 / d;
+        for (int y = 0; y < p.ny; ++y) {
+            if (y > 0)
+                piv = 1.0 / (d - p.ay * p.ay * piv);
+            m[(size_t)y * p.nx + q] = (float)piv;
+        }
+    }
+    cudaError_t e = cudaMalloc(&P->ym, m.size() * 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->ym, m.data(), m.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    int rc = encode_map(&P->m_Rf_hi, P->t2, p.nx, p.ny, p.nz, P->fbn);
+    if (rc == BRS_OK)
+        rc = encode_map(&P->m_Rf_lo, P->t2_lo, p.nx, p.ny, p.nz, P->fbn);
+    if (rc != BRS_OK)
+        return rc;
+    const int split = P->math == BRS_PLANE_3XTF32 ? 3 : 1;
+    const void* k = split == 3 ? fused_kernel_for<3>(P->fbn) : fused_kernel_for<1>(P->fbn);
+    const size_t need = pers_smem(split, P->fbn);
+    cudaFuncAttributes fa{};
+    cudaError_t ce = cudaFuncGetAttributes(&fa, k);
+    if (ce == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < need)
+        ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (ce != cudaSuccess)
+        return brs_cuda_status(ce);
+    P->fused = 1;
+    return BRS_OK;
+}
+
 }  // namespace
 
 int plane_setup(brs_ctx* c)
@@ -817,6 +903,8 @@ int plane_setup(brs_ctx* c)
             rc = tc_setup(c, sx, sy);
         if (rc == BRS_OK && P->form == 1)
             rc = ythomas_setup<float>(c);
+        if (rc == BRS_OK && P->form == 1)
+            rc = fused_setup(c);
         return rc;
     }
     if (p.dtype == BRS_F64)
@@ -843,7 +931,7 @@ void plane_teardown(brs_ctx* c)
     if (!P)
         return;
     for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo,
-                    P->ytab})
+                    P->ytab, P->ym})
         if (q)
             cudaFree(q);
     delete P;

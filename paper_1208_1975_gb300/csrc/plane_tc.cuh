@@ -22,7 +22,7 @@ namespace brs_tc {
 constexpr int BM = 128;  // MMA M (one TMEM lane per output row)
 constexpr int BK = 32;   // K per ring stage: 32 FP32 = one 128-byte swizzle row
 
-enum Epi { EPI_SPLIT = 0, EPI_SCALE_SPLIT = 1, EPI_UPDATE = 2, EPI_BOX = 3 };
+enum Epi { EPI_SPLIT = 0, EPI_SCALE_SPLIT = 1, EPI_UPDATE = 2, EPI_BOX = 3, EPI_YTHOMAS = 4 };
 
 struct TcArgs {
     int M, N, K;        // per-plane product sizes
@@ -45,6 +45,12 @@ struct TcArgs {
     const int* box_off;
     int box_bx, box_by, box_bz, box_nx, box_ny;
     int box_vec4;  // bx and nx multiples of 4: 4 consecutive local cells are 16 aligned bytes
+    // EPI_YTHOMAS (persistent kernel only): row m of the tile is x-mode p = m, its columns
+    // are y = 0 .. N-1, and the epilogue solves tridiag(-ay, d_p, -ay) w = row along the
+    // columns.  ym[y * M + p] = 1 / (d_p + ay c_{y-1}) are the elimination's reciprocal
+    // pivots; w is written to out_hi (/ out_lo) as [plane][y][p], split for the next product.
+    const float* ym;
+    float ay;
 };
 
 #ifdef __CUDACC__
@@ -130,6 +136,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+        "%27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 template <int SPLIT, int EPI, int BN, int NST>
@@ -395,6 +420,84 @@ __device__ __forceinline__ void box_epilogue(const TcArgs& g, uint32_t trow, int
     }
 }
 
+// EPI_YTHOMAS epilogue of one accumulator tile, run by one warp for its 32 TMEM lanes: lane
+// = x-mode p, its N columns = the right-hand side along y.  Thomas elimination in place:
+//   z_y = m_y (r_y + ay z_{y-1})            (forward; z written back to the TMEM columns)
+//   w_y = z_y + ay m_y w_{y+1}              (back substitution, y = N-1 .. 0)
+// with the per-mode reciprocal pivots m_y from g.ym.  A warp's stores of one y are 32
+// consecutive modes (128 bytes).  Every lane runs the loops (tcgen05.ld / st are
+// warp-collective); lanes past the last mode neither load tables nor store.
+template <int BN, int SPLIT>
+__device__ __forceinline__ void ythomas_epilogue(const TcArgs& g, uint32_t trow, int p, int plane)
+{
+    constexpr int NC = BN / 32;
+    const bool pok = p < g.M;
+    const int pc = pok ? p : 0;
+    const int ncs = g.N / 32;  // chunks holding rows of the system (N is a multiple of 32)
+    const float ay = g.ay;
+    const float* tab = g.ym + pc;
+    const long long M = g.M;
+    auto load_piv = [&](int c, float (&dst)[32]) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            dst[i] = __ldg(tab + (long long)(c * 32 + i) * M);
+    };
+    float mn[32];
+    load_piv(0, mn);
+    float z = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        if (c >= ncs)
+            break;  // uniform: N is the same for every lane
+        float m[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            m[i] = mn[i];
+        if (c + 1 < ncs)
+            load_piv(c + 1, mn);
+        uint32_t r[32];
+        tmem_ld32(trow + (uint32_t)(c * 32), r);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            z = m[i] * fmaf(ay, z, __uint_as_float(r[i]));
+            r[i] = __float_as_uint(z);
+        }
+        tmem_st32(trow + (uint32_t)(c * 32), r);
+    }
+    tmem_wait_st();
+    load_piv(ncs - 1, mn);
+    float w = 0.0f;
+    const long long obase = (long long)plane * g.plane + p;
+#pragma unroll 1
+    for (int c = ncs - 1; c >= 0; --c) {
+        float m[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            m[i] = mn[i];
+        if (c > 0)
+            load_piv(c - 1, mn);
+        uint32_t r[32];
+        tmem_ld32(trow + (uint32_t)(c * 32), r);
+        float wv[32];
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+            w = fmaf(ay * m[i], w, __uint_as_float(r[i]));
+            wv[i] = w;
+        }
+        if (pok) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const long long o = obase + (long long)(c * 32 + i) * M;
+                const uint32_t hb = tf32_rn(wv[i]);
+                g.out_hi[o] = __uint_as_float(hb);
+                if (SPLIT == 3)
+                    g.out_lo[o] = __uint_as_float(tf32_rn(wv[i] - __uint_as_float(hb)));
+            }
+        }
+        __syncwarp();  // the next tcgen05.ld is warp-collective
+    }
+}
+
 // Persistent variant: one CTA per SM walks tiles t = blockIdx.x, +gridDim.x, ... of the
 // (n-tile, m-tile, plane) space.  Warp 0 streams K-blocks of every tile through the TMA
 // ring, warp 1 issues the MMAs into one of two TMEM accumulators, warps 2-5 drain the other
@@ -410,11 +513,10 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
     constexpr uint32_t B_BYTES = BN * BK * 4;
     constexpr uint32_t STAGE = (SPLIT == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
     constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulators
-    constexpr uint32_t STAGING = 4 * 32 * 33 * 4;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE + STAGING);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE);
     uint64_t* empty = full + NST;
     uint64_t* accf = empty + NST;  // accumulator a holds a finished tile
     uint64_t* acce = accf + 2;     // accumulator a has been read out
@@ -565,6 +667,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
             const uint32_t trow = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
             if constexpr (EPI == EPI_BOX) {
                 box_epilogue<BN>(g, trow, m0 + q * 32 + lane, n0);
+            } else if constexpr (EPI == EPI_YTHOMAS) {
+                ythomas_epilogue<BN, SPLIT>(g, trow, m0 + q * 32 + lane, plane);
             } else {
             // Row-direct epilogue: this thread's TMEM lane is output row mrow; a 32-column
             // chunk of it is 128 contiguous bytes, written (and, for the update, the old u

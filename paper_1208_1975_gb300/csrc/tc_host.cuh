@@ -51,7 +51,7 @@ inline size_t pers_smem(int split, int bn)
 {
     const int nst = pers_nst(split, bn);
     const size_t stage = (size_t)(split == 3 ? 2 : 1) * (BM + bn) * BK * 4;
-    return 1024 + nst * stage + 4 * 32 * 33 * 4 + (2 * nst + 5) * 8 + 16;
+    return 1024 + nst * stage + (2 * nst + 5) * 8 + 16;
 }
 
 // FP32 map with the K axis innermost, box (32, box_rows[, 1]), 128-byte swizzle; rank 3

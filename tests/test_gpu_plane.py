@@ -242,6 +242,36 @@ def test_plane_xdst_ythomas_form_parity(brs, orc, dt, math, shape, a, monkeypatc
     assert rel_max_err(got, ref) <= tol
 
 
+FUSED_SHAPES = [(32, 32, 4), (64, 96, 3), (96, 64, 5), (160, 128, 2), (256, 256, 3),
+                (128, 224, 3)]
+
+
+@pytest.mark.parametrize("math", ["3xtf32", "tf32"])
+@pytest.mark.parametrize("method", ["jacobi", "gs"])
+@pytest.mark.parametrize("shape", FUSED_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
+def test_plane_fused_xdst_ythomas_product(brs, orc, shape, a, method, math, monkeypatch):
+    """x-DST product with the y elimination in its epilogue (tile N = 64/128/256 holding a
+    whole y line, partial mode tiles, y lines shorter than the tile): one sweep against the
+    oracle, Jacobi and the even/odd plane order of GS."""
+    monkeypatch.setenv("BRSMOOTH_PLANE_FORM", "1")
+    monkeypatch.setenv("BRSMOOTH_TC_PERSISTENT", "1")
+    monkeypatch.setenv("BRSMOOTH_PLANE_FUSE", "1")
+    nx, ny, nz = shape
+    u = rounded(initial_guess((nz, ny, nx)), "f32")
+    b = rounded(rhs((nz, ny, nx)), "f32")
+    if method == "jacobi":
+        ref = orc.sweep(u, b, a, block="plane", method="jacobi", omega=0.8)
+        got = gpu_run(brs, u, b, a, dt="f32", math=math, omega=0.8)
+    else:
+        ref = orc.sweep(u, b, a, block="plane", method="gs_zebra", omega=1.0)
+        got = gpu_run(brs, u, b, a, dt="f32", math=math, method="gs", omega=1.0)
+    # one TF32 pass per product: 2^-11 per solve; under GS the odd planes solve with the even
+    # planes' new values, so two solves' errors add
+    tol = (2.0 ** -11 if method == "jacobi" else 2.0 ** -10) if math == "tf32" else TOL["f32"]
+    assert rel_max_err(got, ref) <= tol
+
+
 @pytest.mark.parametrize("shape", [(33, 17, 4), (5, 70, 3), (1, 9, 2), (100, 3, 3)], ids=str)
 def test_plane_xdst_form_ragged_simt(brs, orc, shape, monkeypatch):
     monkeypatch.setenv("BRSMOOTH_PLANE_FORM", "1")
