@@ -64,9 +64,10 @@ struct PlaneState {
     CUtensorMap m_W2_hi, m_W2_lo;
     // fused x-DST + y-Thomas product (tensor path, ny <= 256): tile N = fbn covers a whole
     // y line, the epilogue eliminates along it; ym[y][p] are the reciprocal pivots
-    int fused = 0, fbn = 0;
+    int fused = 0, fbn = 0, fbk = 16;  // tile N, K block (16: 64-byte swizzle, deeper ring)
     void* ym = nullptr;
-    CUtensorMap m_Rf_hi, m_Rf_lo;  // t2 as [k][y][x], box rows fbn (B of the fused product)
+    CUtensorMap m_Rf_hi, m_Rf_lo;    // t2 as [k][y][x], box (fbk, fbn) (B of the fused product)
+    CUtensorMap m_sxf_hi, m_sxf_lo;  // Sx, box (fbk, 128) (A of the fused product)
 };
 
 // Tile shapes of the tensor-core products (N per CTA, ring stages): 128 x 128 tiles with a
@@ -272,15 +273,33 @@ const void* pers_kernel_for(int bn)
     return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI, 128, pers_nst(SPLIT, 128)>;
 }
 
-template <int SPLIT>
-const void* fused_kernel_for(int bn)
+using brs_tc::ring_nst;
+
+template <int SPLIT, int BKT>
+const void* fused_kernel_bk(int bn)
 {
     using brs_tc::EPI_YTHOMAS;
     if (bn == 64)
-        return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 64, pers_nst(SPLIT, 64)>;
+        return (const void*)
+            brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 64, ring_nst(SPLIT, 64, BKT), BKT>;
     if (bn == 128)
-        return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 128, pers_nst(SPLIT, 128)>;
-    return (const void*)brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 256, pers_nst(SPLIT, 256)>;
+        return (const void*)
+            brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 128, ring_nst(SPLIT, 128, BKT), BKT>;
+    return (const void*)
+        brs_tc::tc_gemm_persistent<SPLIT, EPI_YTHOMAS, 256, ring_nst(SPLIT, 256, BKT), BKT>;
+}
+
+template <int SPLIT>
+const void* fused_kernel_for(int bn, int bk)
+{
+    return bk == 16 ? fused_kernel_bk<SPLIT, 16>(bn) : fused_kernel_bk<SPLIT, 32>(bn);
+}
+
+size_t fused_smem(int split, int bn, int bk)
+{
+    const int nst = split == 3 ? (bk == 16 ? ring_nst(3, bn, 16) : ring_nst(3, bn, 32))
+                               : (bk == 16 ? ring_nst(1, bn, 16) : ring_nst(1, bn, 32));
+    return pers_smem(split, bn, nst, bk) + brs_tc::kTwistExtra;
 }
 
 template <int SPLIT, int EPI>
@@ -540,11 +559,12 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
         int tn = 1, tm = (nx + brs_tc::BM - 1) / brs_tc::BM, nb = nbatch;
         const long long ntiles = (long long)tm * nb;
         const int grid = (int)(ntiles < P->sms ? ntiles : P->sms);
-        CUtensorMap a0 = P->m_sx_hi, a1 = P->m_sx_lo, b0 = P->m_Rf_hi, b1 = P->m_Rf_lo;
+        CUtensorMap a0 = P->m_sxf_hi, a1 = P->m_sxf_lo, b0 = P->m_Rf_hi, b1 = P->m_Rf_lo;
         brs_tc::TcArgs gg = g;
         void* args[] = {&a0, &a1, &b0, &b1, &gg, &tn, &tm, &nb};
-        cudaError_t e = launch_pdl_c(fused_kernel_for<SPLIT>(P->fbn), dim3(grid), dim3(192),
-                                     pers_smem(SPLIT, P->fbn), s, args);
+        cudaError_t e = launch_pdl_c(fused_kernel_for<SPLIT>(P->fbn, P->fbk), dim3(grid),
+                                     dim3(brs_tc::pers_threads<brs_tc::EPI_YTHOMAS>()),
+                                     fused_smem(SPLIT, P->fbn, P->fbk), s, args);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
         g.ym = nullptr;
@@ -839,14 +859,21 @@ int fused_setup(brs_ctx* c)
         e = cudaMemcpy(P->ym, m.data(), m.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
         return brs_cuda_status(e);
-    int rc = encode_map(&P->m_Rf_hi, P->t2, p.nx, p.ny, p.nz, P->fbn);
+    const char* kenv = std::getenv("BRSMOOTH_PLANE_FUSE_BK");
+    P->fbk = (kenv && std::atoi(kenv) == 32) ? 32 : 16;
+    int rc = encode_map(&P->m_Rf_hi, P->t2, p.nx, p.ny, p.nz, P->fbn, P->fbk);
     if (rc == BRS_OK)
-        rc = encode_map(&P->m_Rf_lo, P->t2_lo, p.nx, p.ny, p.nz, P->fbn);
+        rc = encode_map(&P->m_Rf_lo, P->t2_lo, p.nx, p.ny, p.nz, P->fbn, P->fbk);
+    if (rc == BRS_OK)
+        rc = encode_map(&P->m_sxf_hi, P->sx, p.nx, p.nx, 0, brs_tc::BM, P->fbk);
+    if (rc == BRS_OK)
+        rc = encode_map(&P->m_sxf_lo, P->sx_lo, p.nx, p.nx, 0, brs_tc::BM, P->fbk);
     if (rc != BRS_OK)
         return rc;
     const int split = P->math == BRS_PLANE_3XTF32 ? 3 : 1;
-    const void* k = split == 3 ? fused_kernel_for<3>(P->fbn) : fused_kernel_for<1>(P->fbn);
-    const size_t need = pers_smem(split, P->fbn);
+    const void* k = split == 3 ? fused_kernel_for<3>(P->fbn, P->fbk)
+                               : fused_kernel_for<1>(P->fbn, P->fbk);
+    const size_t need = fused_smem(split, P->fbn, P->fbk);
     cudaFuncAttributes fa{};
     cudaError_t ce = cudaFuncGetAttributes(&fa, k);
     if (ce == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < need)

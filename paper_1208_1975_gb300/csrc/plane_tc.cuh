@@ -86,6 +86,25 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* tile)
     return d;
 }
 
+// Descriptor of a K-major tile written by TMA with a swizzle as wide as its rows: BKT = 32
+// FP32 (128-byte rows, SWIZZLE_128B, 8-row groups 1024 bytes apart) or BKT = 16 (64-byte
+// rows, SWIZZLE_64B, 8-row groups 512 bytes apart).
+template <int BKT>
+__device__ __forceinline__ uint64_t smem_desc_kmajor(const void* tile)
+{
+    static_assert(BKT == 32 || BKT == 16, "K block of 16 or 32 FP32");
+    if constexpr (BKT == 32)
+        return smem_desc_sw128(tile);
+    const uint64_t addr = smem_u32(tile);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFFull) >> 4;          // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512 >> 4) << 32;         // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                  // fixed constant 0b001
+    d |= (uint64_t)4 << 61;                  // swizzle: 64-byte
+    return d;
+}
+
 // Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n)
 {
@@ -155,6 +174,29 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 __device__ __forceinline__ void tmem_wait_st()
 {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
+        : "memory");
 }
 
 template <int SPLIT, int EPI, int BN, int NST>
@@ -420,97 +462,157 @@ __device__ __forceinline__ void box_epilogue(const TcArgs& g, uint32_t trow, int
     }
 }
 
-// EPI_YTHOMAS epilogue of one accumulator tile, run by one warp for its 32 TMEM lanes: lane
-// = x-mode p, its N columns = the right-hand side along y.  Thomas elimination in place:
-//   z_y = m_y (r_y + ay z_{y-1})            (forward; z written back to the TMEM columns)
-//   w_y = z_y + ay m_y w_{y+1}              (back substitution, y = N-1 .. 0)
-// with the per-mode reciprocal pivots m_y from g.ym.  A warp's stores of one y are 32
-// consecutive modes (128 bytes).  Every lane runs the loops (tcgen05.ld / st are
-// warp-collective); lanes past the last mode neither load tables nor store.
-template <int BN, int SPLIT>
-__device__ __forceinline__ void ythomas_epilogue(const TcArgs& g, uint32_t trow, int p, int plane)
+// EPI_YTHOMAS epilogue of one accumulator tile: TMEM lane = x-mode p, its N = n columns =
+// the right-hand side r along y of tridiag(-ay, d_p, -ay) w = r.  Two warps share each lane
+// quarter and split the line at k = n / 2 (twisted elimination):
+//   top    (half 0), y = 0 .. k-1 :  z_y = m_y (r_y + ay z_{y-1})
+//   bottom (half 1), y = n-1 .. k :  z_y = m_{n-1-y} (r_y + ay z_{y+1})
+// with the reciprocal pivots m_j of the elimination from one end (by symmetry the same from
+// either end), g.ym[j * M + p].  z is written back to the TMEM columns.  The halves swap
+// z_{k-1} and z_k through shared memory; with m = m_{k-1} (= m_{n-1-k}) the interface is
+//   w_{k-1} = (z_{k-1} + ay m z_k) / (1 - ay^2 m^2),   w_k = z_k + ay m w_{k-1},
+// and each half back-substitutes its own rows:
+//   top    y = k-1 .. 0 :  w_y = z_y + ay m_y w_{y+1}
+//   bottom y = k .. n-1 :  w_y = z_y + ay m_{n-1-y} w_{y-1}.
+// w is stored split (hi, lo) at [plane][y][p]: a warp's store of one y covers 32 consecutive
+// modes.  tcgen05.ld / st are warp-collective, so every lane runs the loops; lanes past the
+// last mode read mode 0's pivots and store nothing.  xch holds this pair's two 32-value
+// exchange slots; pbar (64 arrivals: both warps' lanes) orders them, waited with a bound.
+template <int SPLIT>
+__device__ __forceinline__ bool ythomas_twist_epilogue(const TcArgs& g, uint32_t trow, int p,
+                                                       int plane, int half, float* xch,
+                                                       uint64_t* pbar, uint32_t parity)
 {
-    constexpr int NC = BN / 32;
+    const int lane = threadIdx.x & 31;
     const bool pok = p < g.M;
-    const int pc = pok ? p : 0;
-    const int ncs = g.N / 32;  // chunks holding rows of the system (N is a multiple of 32)
+    const int n = g.N, k = n >> 1, nck = k >> 4;  // N a multiple of 32: k a multiple of 16
     const float ay = g.ay;
-    const float* tab = g.ym + pc;
     const long long M = g.M;
-    auto load_piv = [&](int c, float (&dst)[32]) {
+    const float* tab = g.ym + (pok ? p : 0);
+    auto load_piv = [&](int blk, float (&dst)[16]) {  // m_j, j = 16 blk .. 16 blk + 15
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            dst[i] = __ldg(tab + (long long)(c * 32 + i) * M);
+        for (int j = 0; j < 16; ++j)
+            dst[j] = __ldg(tab + (long long)(blk * 16 + j) * M);
     };
-    float mn[32];
+    float mn[16];
     load_piv(0, mn);
     float z = 0.0f;
 #pragma unroll 1
-    for (int c = 0; c < NC; ++c) {
-        if (c >= ncs)
-            break;  // uniform: N is the same for every lane
-        float m[32];
+    for (int c = 0; c < nck; ++c) {
+        float m[16];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            m[i] = mn[i];
-        if (c + 1 < ncs)
+        for (int j = 0; j < 16; ++j)
+            m[j] = mn[j];
+        if (c + 1 < nck)
             load_piv(c + 1, mn);
-        uint32_t r[32];
-        tmem_ld32(trow + (uint32_t)(c * 32), r);
+        uint32_t r[16];
+        if (half == 0) {
+            const uint32_t col = (uint32_t)(c * 16);
+            tmem_ld16(trow + col, r);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            z = m[i] * fmaf(ay, z, __uint_as_float(r[i]));
-            r[i] = __float_as_uint(z);
+            for (int j = 0; j < 16; ++j) {
+                z = m[j] * fmaf(ay, z, __uint_as_float(r[j]));
+                r[j] = __float_as_uint(z);
+            }
+            tmem_st16(trow + col, r);
+        } else {
+            // columns n - 16(c+1) .. n - 16c - 1, from the highest; column y uses m_{n-1-y}
+            const uint32_t col = (uint32_t)(n - 16 * (c + 1));
+            tmem_ld16(trow + col, r);
+#pragma unroll
+            for (int j = 15; j >= 0; --j) {
+                z = m[15 - j] * fmaf(ay, z, __uint_as_float(r[j]));
+                r[j] = __float_as_uint(z);
+            }
+            tmem_st16(trow + col, r);
         }
-        tmem_st32(trow + (uint32_t)(c * 32), r);
     }
     tmem_wait_st();
-    load_piv(ncs - 1, mn);
-    float w = 0.0f;
-    const long long obase = (long long)plane * g.plane + p;
+    // interface: top publishes z_{k-1}, bottom z_k
+    xch[half * 32 + lane] = z;
+    mbar_arrive(pbar);
+    const bool ok = mbar_wait_bounded(pbar, parity);
+    const float zt = xch[lane], zb = xch[32 + lane];
+    const float mk = __ldg(tab + (long long)(k - 1) * M);
+    const float wk1 = (zt + ay * mk * zb) / (1.0f - ay * ay * mk * mk);
+    const float wk = fmaf(ay * mk, wk1, zb);
+    float w = half == 0 ? wk : wk1;
+    float* oh = g.out_hi + (long long)plane * g.plane + p;
+    float* ol = g.out_lo + (long long)plane * g.plane + p;
+    // back substitution: chunk order reversed for the top half, pivot blocks reversed for both
+    load_piv(nck - 1, mn);
 #pragma unroll 1
-    for (int c = ncs - 1; c >= 0; --c) {
-        float m[32];
+    for (int c = 0; c < nck; ++c) {
+        float m[16];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            m[i] = mn[i];
-        if (c > 0)
-            load_piv(c - 1, mn);
-        uint32_t r[32];
-        tmem_ld32(trow + (uint32_t)(c * 32), r);
-        float wv[32];
+        for (int j = 0; j < 16; ++j)
+            m[j] = mn[j];
+        if (c + 1 < nck)
+            load_piv(nck - 2 - c, mn);
+        uint32_t r[16];
+        if (half == 0) {
+            // columns 16 b .. 16 b + 15, b = nck-1-c, from the highest; column y uses m_y
+            const int y0 = 16 * (nck - 1 - c);
+            tmem_ld16(trow + (uint32_t)y0, r);
+            float* ph = oh + (long long)y0 * M;
+            float* pl = ol + (long long)y0 * M;
 #pragma unroll
-        for (int i = 31; i >= 0; --i) {
-            w = fmaf(ay * m[i], w, __uint_as_float(r[i]));
-            wv[i] = w;
-        }
-        if (pok) {
+            for (int j = 15; j >= 0; --j) {
+                w = fmaf(ay * m[j], w, __uint_as_float(r[j]));
+                if (pok) {
+                    const uint32_t hb = tf32_rn(w);
+                    ph[j * M] = __uint_as_float(hb);
+                    if (SPLIT == 3)
+                        pl[j * M] = __uint_as_float(tf32_rn(w - __uint_as_float(hb)));
+                }
+            }
+        } else {
+            // columns k + 16 c .. k + 16 c + 15, from the lowest; column y uses m_{n-1-y}, the
+            // block b = nck-1-c reversed
+            const int y0 = k + 16 * c;
+            tmem_ld16(trow + (uint32_t)y0, r);
+            float* ph = oh + (long long)y0 * M;
+            float* pl = ol + (long long)y0 * M;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const long long o = obase + (long long)(c * 32 + i) * M;
-                const uint32_t hb = tf32_rn(wv[i]);
-                g.out_hi[o] = __uint_as_float(hb);
-                if (SPLIT == 3)
-                    g.out_lo[o] = __uint_as_float(tf32_rn(wv[i] - __uint_as_float(hb)));
+            for (int j = 0; j < 16; ++j) {
+                w = fmaf(ay * m[15 - j], w, __uint_as_float(r[j]));
+                if (pok) {
+                    const uint32_t hb = tf32_rn(w);
+                    ph[j * M] = __uint_as_float(hb);
+                    if (SPLIT == 3)
+                        pl[j * M] = __uint_as_float(tf32_rn(w - __uint_as_float(hb)));
+                }
             }
         }
         __syncwarp();  // the next tcgen05.ld is warp-collective
     }
+    return ok;
 }
 
 // Persistent variant: one CTA per SM walks tiles t = blockIdx.x, +gridDim.x, ... of the
 // (n-tile, m-tile, plane) space.  Warp 0 streams K-blocks of every tile through the TMA
 // ring, warp 1 issues the MMAs into one of two TMEM accumulators, warps 2-5 drain the other
-// accumulator (epilogue of the previous tile) at the same time.
-template <int SPLIT, int EPI, int BN, int NST>
-__global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
+// accumulator (epilogue of the previous tile) at the same time.  The y elimination epilogue
+// has eight epilogue warps (warps 2-9): two per TMEM lane quarter, one per half of the line.
+template <int EPI>
+__host__ __device__ constexpr int pers_threads()
+{
+    return EPI == EPI_YTHOMAS ? 320 : 192;
+}
+
+// Shared memory past the ring of the y elimination epilogue: four pair barriers, and a
+// double-buffered exchange area of 4 pairs x 2 halves x 32 values.
+constexpr int kTwistExtra = 4 * 8 + 2 * 4 * 64 * 4;
+
+template <int SPLIT, int EPI, int BN, int NST, int BKT = BK>
+__global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
     const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
     const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
     TcArgs g, int tiles_n, int tiles_m, int nbatch)
 {
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "MMA N for M = 128");
-    constexpr uint32_t A_BYTES = BM * BK * 4;
-    constexpr uint32_t B_BYTES = BN * BK * 4;
+    constexpr uint32_t A_BYTES = BM * BKT * 4;
+    constexpr uint32_t B_BYTES = BN * BKT * 4;
     constexpr uint32_t STAGE = (SPLIT == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
     constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulators
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -521,11 +623,14 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
     uint64_t* accf = empty + NST;  // accumulator a holds a finished tile
     uint64_t* acce = accf + 2;     // accumulator a has been read out
     uint64_t* done = acce + 2;     // every MMA issued by this CTA has completed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    constexpr int NPB = EPI == EPI_YTHOMAS ? 4 : 0;
+    uint64_t* pairb = done + 1;    // y elimination: the two warps of lane quarter q meet here
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pairb + NPB);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* xbase = reinterpret_cast<float*>(pairb + NPB + 1);  // [2][4][2][32]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb = (g.K + BK - 1) / BK;
+    const int nkb = (g.K + BKT - 1) / BKT;
     const long long ntiles = (long long)tiles_n * tiles_m * nbatch;
 
     if (threadIdx.x == 0) {
@@ -535,8 +640,10 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accf[a], 1);
-            mbar_init(&acce[a], 4);
+            mbar_init(&acce[a], EPI == EPI_YTHOMAS ? 8 : 4);
         }
+        for (int q = 0; q < NPB; ++q)
+            mbar_init(&pairb[q], 64);
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -579,7 +686,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
                 }
                 unsigned char* st = base + s * STAGE;
                 mbar_arrive_expect_tx(&full[s], STAGE);
-                const int kx = kb * BK;
+                const int kx = kb * BKT;
                 if (g.a_batched)
                     tma_load_3d(st, &mA_hi, &full[s], kx, m0, plane);
                 else
@@ -630,13 +737,13 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
                 unsigned char* sb_hi = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
                 unsigned char* sb_lo = sb_hi + B_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK / 8; ++k) {
-                    const uint64_t ah = smem_desc_sw128(sa_hi) + (uint64_t)((k * 32) >> 4);
-                    const uint64_t bh = smem_desc_sw128(sb_hi) + (uint64_t)((k * 32) >> 4);
+                for (int k = 0; k < BKT / 8; ++k) {
+                    const uint64_t ah = smem_desc_kmajor<BKT>(sa_hi) + (uint64_t)((k * 32) >> 4);
+                    const uint64_t bh = smem_desc_kmajor<BKT>(sb_hi) + (uint64_t)((k * 32) >> 4);
                     mma_tf32(tacc, ah, bh, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     if (SPLIT == 3) {
-                        const uint64_t al = smem_desc_sw128(sa_lo) + (uint64_t)((k * 32) >> 4);
-                        const uint64_t bl = smem_desc_sw128(sb_lo) + (uint64_t)((k * 32) >> 4);
+                        const uint64_t al = smem_desc_kmajor<BKT>(sa_lo) + (uint64_t)((k * 32) >> 4);
+                        const uint64_t bl = smem_desc_kmajor<BKT>(sb_lo) + (uint64_t)((k * 32) >> 4);
                         mma_tf32(tacc, ah, bl, idesc, 1u);
                         mma_tf32(tacc, al, bh, idesc, 1u);
                     }
@@ -668,7 +775,11 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(
             if constexpr (EPI == EPI_BOX) {
                 box_epilogue<BN>(g, trow, m0 + q * 32 + lane, n0);
             } else if constexpr (EPI == EPI_YTHOMAS) {
-                ythomas_epilogue<BN, SPLIT>(g, trow, m0 + q * 32 + lane, plane);
+                const int half = (warp - 2) >> 2;
+                float* xch = xbase + ((ti & 1) * 4 + q) * 64;
+                if (!ythomas_twist_epilogue<SPLIT>(g, trow, m0 + q * 32 + lane, plane, half, xch,
+                                                   &pairb[q], (uint32_t)(ti & 1)))
+                    *abort_flag = 1;
             } else {
             // Row-direct epilogue: this thread's TMEM lane is output row mrow; a 32-column
             // chunk of it is 128 contiguous bytes, written (and, for the update, the old u
