@@ -68,7 +68,31 @@ struct PlaneState {
     void* ym = nullptr;
     CUtensorMap m_Rf_hi, m_Rf_lo;    // t2 as [k][y][x], box (fbk, fbn) (B of the fused product)
     CUtensorMap m_sxf_hi, m_sxf_lo;  // Sx, box (fbk, 128) (A of the fused product)
+    // gather form of the fused product (R formed in shared memory from u and b): maps of the
+    // grids it reads, [k][y][x] with box (16, fbn), cached by address
+    int fgather = 0;
+    struct GridMap {
+        const void* ptr = nullptr;
+        CUtensorMap map;
+    };
+    GridMap gmaps[4];
+    int gnext = 0;
 };
+
+// Map of a grid for the gather form, encoded on first use of its address.
+const CUtensorMap* grid_map(PlaneState* P, const brs_params& p, const void* ptr)
+{
+    for (auto& e : P->gmaps)
+        if (e.ptr == ptr)
+            return &e.map;
+    PlaneState::GridMap& e = P->gmaps[P->gnext];
+    e.ptr = nullptr;
+    if (brs_tc::encode_map(&e.map, ptr, p.nx, p.ny, p.nz, P->fbn, 16) != BRS_OK)
+        return nullptr;
+    e.ptr = ptr;
+    P->gnext = (P->gnext + 1) % 4;
+    return &e.map;
+}
 
 // Tile shapes of the tensor-core products (N per CTA, ring stages): 128 x 128 tiles with a
 // deep ring at one CTA per SM, or 128 x 64 tiles at two CTAs per SM (one CTA's epilogue
@@ -293,6 +317,30 @@ template <int SPLIT>
 const void* fused_kernel_for(int bn, int bk)
 {
     return bk == 16 ? fused_kernel_bk<SPLIT, 16>(bn) : fused_kernel_bk<SPLIT, 32>(bn);
+}
+
+template <int SPLIT>
+const void* gather_kernel_for(int bn)
+{
+    using brs_tc::EPI_YGATHER;
+    using brs_tc::gather_nst;
+    if (bn == 64)
+        return (const void*)
+            brs_tc::tc_gemm_persistent<SPLIT, EPI_YGATHER, 64, gather_nst(SPLIT, 64), 16>;
+    if (bn == 128)
+        return (const void*)
+            brs_tc::tc_gemm_persistent<SPLIT, EPI_YGATHER, 128, gather_nst(SPLIT, 128), 16>;
+    return (const void*)
+        brs_tc::tc_gemm_persistent<SPLIT, EPI_YGATHER, 256, gather_nst(SPLIT, 256), 16>;
+}
+
+// ring + barriers (full, empty, 2 accf, 2 acce, done, 4 pair, nst converted) + TMEM slot and
+// abort flag + exchange area, after 1024 bytes of alignment slack
+size_t gather_smem(int split, int bn)
+{
+    const int nst = brs_tc::gather_nst(split, bn);
+    return 1024 + (size_t)nst * brs_tc::gather_stage(split, bn) + (size_t)(3 * nst + 9) * 8 + 8 +
+           2 * 4 * 64 * 4 + 16;
 }
 
 size_t fused_smem(int split, int bn, int bk)
@@ -536,6 +584,37 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
     PlaneState* P = ps(c);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const long long plane = (long long)nx * ny;
+    brs_tc::TcArgs g{};
+    g.k0 = k0;
+    g.kstep = kstep;
+    g.plane = plane;
+    g.status = c->dev_status;
+    const CUtensorMap* mu = P->fgather ? grid_map(P, c->p, uin) : nullptr;
+    const CUtensorMap* mb = mu ? grid_map(P, c->p, b) : nullptr;
+    if (mu && mb) {
+        // R_k formed in shared memory, the x-DST, and the y-Thomas in one kernel -> t1 (W)
+        g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
+        g.out_hi = (float*)P->t1; g.out_lo = (float*)P->t1_lo;
+        g.ym = (const float*)P->ym; g.ay = (float)c->p.ay; g.az = (float)c->p.az;
+        int tn = 1, tm = (nx + brs_tc::BM - 1) / brs_tc::BM, nb = nbatch;
+        const long long ntiles = (long long)tm * nb;
+        const int grid = (int)(ntiles < P->sms ? ntiles : P->sms);
+        CUtensorMap a0 = P->m_sxf_hi, a1 = P->m_sxf_lo, b0 = *mu, b1 = *mb;
+        brs_tc::TcArgs gg = g;
+        void* args[] = {&a0, &a1, &b0, &b1, &gg, &tn, &tm, &nb};
+        cudaError_t e = launch_pdl_c(gather_kernel_for<SPLIT>(P->fbn), dim3(grid),
+                                     dim3(brs_tc::pers_threads<brs_tc::EPI_YGATHER>()),
+                                     gather_smem(SPLIT, P->fbn), s, args);
+        if (e != cudaSuccess)
+            return brs_cuda_status(e);
+        g.ym = nullptr;
+        g.M = ny; g.N = nx; g.K = nx; g.a_batched = 1; g.b_batched = 0;
+        g.out_hi = nullptr; g.out_lo = nullptr; g.u = uin; g.uout = uout;
+        g.omega = (float)c->omega;
+        e = launch_tc<SPLIT, brs_tc::EPI_UPDATE>(P, P->m_W_hi, P->m_W_lo, P->m_sxB_hi,
+                                                 P->m_sxB_lo, g, nbatch, s);
+        return brs_cuda_status(e);
+    }
     {
         int blocks = (int)((plane / 4 * nbatch + 255) / 256);
         if (blocks > 152 * 16)
@@ -546,11 +625,6 @@ int plane_pass_tc_xdst(brs_ctx* c, const float* uin, float* uout, const float* b
         if (e != cudaSuccess)
             return brs_cuda_status(e);
     }
-    brs_tc::TcArgs g{};
-    g.k0 = k0;
-    g.kstep = kstep;
-    g.plane = plane;
-    g.status = c->dev_status;
     if (P->fused) {
         // P1 with the y-Thomas in its epilogue: t1 <- W[k][y][p] (split)
         g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
@@ -881,6 +955,19 @@ int fused_setup(brs_ctx* c)
     if (ce != cudaSuccess)
         return brs_cuda_status(ce);
     P->fused = 1;
+    // gather form: on unless BRSMOOTH_PLANE_FGATHER=0 (K blocks of 16 only)
+    const char* genv = std::getenv("BRSMOOTH_PLANE_FGATHER");
+    if ((genv ? std::atoi(genv) != 0 : true) && P->fbk == 16) {
+        const void* kg = split == 3 ? gather_kernel_for<3>(P->fbn) : gather_kernel_for<1>(P->fbn);
+        const size_t gneed = gather_smem(split, P->fbn);
+        cudaFuncAttributes ga{};
+        cudaError_t ge = cudaFuncGetAttributes(&ga, kg);
+        if (ge == cudaSuccess && (size_t)ga.maxDynamicSharedSizeBytes < gneed)
+            ge = cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gneed);
+        if (ge != cudaSuccess)
+            return brs_cuda_status(ge);
+        P->fgather = 1;
+    }
     return BRS_OK;
 }
 

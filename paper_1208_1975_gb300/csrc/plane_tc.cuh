@@ -22,7 +22,14 @@ namespace brs_tc {
 constexpr int BM = 128;  // MMA M (one TMEM lane per output row)
 constexpr int BK = 32;   // K per ring stage: 32 FP32 = one 128-byte swizzle row
 
-enum Epi { EPI_SPLIT = 0, EPI_SCALE_SPLIT = 1, EPI_UPDATE = 2, EPI_BOX = 3, EPI_YTHOMAS = 4 };
+enum Epi {
+    EPI_SPLIT = 0,
+    EPI_SCALE_SPLIT = 1,
+    EPI_UPDATE = 2,
+    EPI_BOX = 3,
+    EPI_YTHOMAS = 4,
+    EPI_YGATHER = 5  // EPI_YTHOMAS with B = R_k formed from u and b in shared memory
+};
 
 struct TcArgs {
     int M, N, K;        // per-plane product sizes
@@ -51,6 +58,10 @@ struct TcArgs {
     // pivots; w is written to out_hi (/ out_lo) as [plane][y][p], split for the next product.
     const float* ym;
     float ay;
+    // EPI_YGATHER: the B maps are u (mB_hi) and b (mB_lo) as [k][y][x]; each stage loads the
+    // boxes of u_{k-1}, u_{k+1} and b_k (planes outside the grid read as zeros) and converter
+    // warps form R = b_k + az (u_{k-1} + u_{k+1}) and its TF32 split in place.
+    float az;
 };
 
 #ifdef __CUDACC__
@@ -597,7 +608,19 @@ __device__ __forceinline__ bool ythomas_twist_epilogue(const TcArgs& g, uint32_t
 template <int EPI>
 __host__ __device__ constexpr int pers_threads()
 {
-    return EPI == EPI_YTHOMAS ? 320 : 192;
+    return EPI == EPI_YGATHER ? 448 : EPI == EPI_YTHOMAS ? 320 : 192;
+}
+
+// Ring stage of the gather form: A hi (/ lo) and three B boxes (u_{k-1}, u_{k+1}, b_k), K blocks
+// of 16; the stage count fills 192 KB (at most 8).
+__host__ __device__ constexpr int gather_stage(int split, int bn)
+{
+    return ((split == 3 ? 2 : 1) * BM + 3 * bn) * 16 * 4;
+}
+
+__host__ __device__ constexpr int gather_nst(int split, int bn)
+{
+    return 196608 / gather_stage(split, bn) < 8 ? 196608 / gather_stage(split, bn) : 8;
 }
 
 // Shared memory past the ring of the y elimination epilogue: four pair barriers, and a
@@ -611,9 +634,15 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
     TcArgs g, int tiles_n, int tiles_m, int nbatch)
 {
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "MMA N for M = 128");
+    constexpr bool GATHER = EPI == EPI_YGATHER;
+    constexpr bool YT = EPI == EPI_YTHOMAS || GATHER;
+    static_assert(!GATHER || BKT == 16, "gather form: K blocks of 16");
+    constexpr uint32_t A_PARTS = SPLIT == 3 ? 2 : 1;
     constexpr uint32_t A_BYTES = BM * BKT * 4;
     constexpr uint32_t B_BYTES = BN * BKT * 4;
-    constexpr uint32_t STAGE = (SPLIT == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
+    constexpr uint32_t STAGE =
+        GATHER ? A_PARTS * A_BYTES + 3 * B_BYTES : A_PARTS * (A_BYTES + B_BYTES);
+    constexpr int EPI_END = YT ? 10 : 6;  // epilogue warps 2 .. EPI_END-1; then converters
     constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulators
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -623,11 +652,13 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
     uint64_t* accf = empty + NST;  // accumulator a holds a finished tile
     uint64_t* acce = accf + 2;     // accumulator a has been read out
     uint64_t* done = acce + 2;     // every MMA issued by this CTA has completed
-    constexpr int NPB = EPI == EPI_YTHOMAS ? 4 : 0;
+    constexpr int NPB = YT ? 4 : 0;
+    constexpr int NCV = GATHER ? NST : 0;
     uint64_t* pairb = done + 1;    // y elimination: the two warps of lane quarter q meet here
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pairb + NPB);
+    uint64_t* conv = pairb + NPB;  // gather form: stage s holds R's split (128 arrivals)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(conv + NCV);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    float* xbase = reinterpret_cast<float*>(pairb + NPB + 1);  // [2][4][2][32]
+    float* xbase = reinterpret_cast<float*>(conv + NCV + 1);  // [2][4][2][32]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = (g.K + BKT - 1) / BKT;
@@ -640,10 +671,12 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accf[a], 1);
-            mbar_init(&acce[a], EPI == EPI_YTHOMAS ? 8 : 4);
+            mbar_init(&acce[a], YT ? 8 : 4);
         }
         for (int q = 0; q < NPB; ++q)
             mbar_init(&pairb[q], 64);
+        for (int q = 0; q < NCV; ++q)
+            mbar_init(&conv[q], 128);
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -697,12 +730,16 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
                     else
                         tma_load_2d(st + A_BYTES, &mA_lo, &full[s], kx, m0);
                 }
-                unsigned char* sb = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
-                if (g.b_batched)
+                unsigned char* sb = st + A_PARTS * A_BYTES;
+                if constexpr (GATHER) {
+                    tma_load_3d(sb, &mB_hi, &full[s], kx, n0, plane - 1);
+                    tma_load_3d(sb + B_BYTES, &mB_hi, &full[s], kx, n0, plane + 1);
+                    tma_load_3d(sb + 2 * B_BYTES, &mB_lo, &full[s], kx, n0, plane);
+                } else if (g.b_batched)
                     tma_load_3d(sb, &mB_hi, &full[s], kx, n0, plane);
                 else
                     tma_load_2d(sb, &mB_hi, &full[s], kx, n0);
-                if (SPLIT == 3) {
+                if (SPLIT == 3 && !GATHER) {
                     if (g.b_batched)
                         tma_load_3d(sb + B_BYTES, &mB_lo, &full[s], kx, n0, plane);
                     else
@@ -726,7 +763,8 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
             bool ok = true;
             for (int kb = 0; kb < nkb; ++kb, ++kg) {
                 const int s = (int)(kg % NST);
-                if (*abort_flag || !mbar_wait_bounded(&full[s], (uint32_t)((kg / NST) & 1))) {
+                uint64_t* ready = GATHER ? &conv[s] : &full[s];
+                if (*abort_flag || !mbar_wait_bounded(ready, (uint32_t)((kg / NST) & 1))) {
                     ok = false;
                     break;
                 }
@@ -734,8 +772,9 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
                 unsigned char* st = base + s * STAGE;
                 unsigned char* sa_hi = st;
                 unsigned char* sa_lo = st + A_BYTES;
-                unsigned char* sb_hi = st + (SPLIT == 3 ? 2 : 1) * A_BYTES;
-                unsigned char* sb_lo = sb_hi + B_BYTES;
+                // gather form: the split of R is in the b_k (hi) and u_{k-1} (lo) boxes
+                unsigned char* sb_hi = st + A_PARTS * A_BYTES + (GATHER ? 2 * B_BYTES : 0);
+                unsigned char* sb_lo = GATHER ? st + A_PARTS * A_BYTES : sb_hi + B_BYTES;
 #pragma unroll
                 for (int k = 0; k < BKT / 8; ++k) {
                     const uint64_t ah = smem_desc_kmajor<BKT>(sa_hi) + (uint64_t)((k * 32) >> 4);
@@ -757,7 +796,46 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
             mma_commit(&accf[a]);
         }
         mma_commit(done);
-    } else if (warp >= 2) {
+    } else if (GATHER && warp >= EPI_END) {
+        // converters: R = b_k + az (u_{k-1} + u_{k+1}) element by element (the three boxes
+        // share one swizzled layout), hi = rn_tf32(R) over b_k's box, lo = rn_tf32(R - hi) over
+        // u_{k-1}'s; the async-proxy fence makes the writes visible to the MMAs
+        const int ct = threadIdx.x - 32 * EPI_END;
+        const float az = g.az;
+        long long kg = 0;
+        bool run = true;
+        for (long long t = blockIdx.x; t < ntiles && run; t += gridDim.x) {
+            for (int kb = 0; kb < nkb; ++kb, ++kg) {
+                const int s = (int)(kg % NST);
+                if (!mbar_wait_bounded(&full[s], (uint32_t)((kg / NST) & 1)) || *abort_flag) {
+                    *abort_flag = 1;
+                    run = false;
+                    break;
+                }
+                unsigned char* sb = base + s * STAGE + A_PARTS * A_BYTES;
+                float4* um = reinterpret_cast<float4*>(sb);
+                const float4* up = reinterpret_cast<const float4*>(sb + B_BYTES);
+                float4* bb = reinterpret_cast<float4*>(sb + 2 * B_BYTES);
+#pragma unroll 2
+                for (int i = ct; i < (int)(B_BYTES / 16); i += 128) {
+                    const float4 x = um[i], y = up[i], b4 = bb[i];
+                    float r[4] = {fmaf(az, x.x + y.x, b4.x), fmaf(az, x.y + y.y, b4.y),
+                                  fmaf(az, x.z + y.z, b4.z), fmaf(az, x.w + y.w, b4.w)};
+                    float h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        h[e] = __uint_as_float(tf32_rn(r[e]));
+                        l[e] = __uint_as_float(tf32_rn(r[e] - h[e]));
+                    }
+                    bb[i] = make_float4(h[0], h[1], h[2], h[3]);
+                    if (SPLIT == 3)
+                        um[i] = make_float4(l[0], l[1], l[2], l[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&conv[s]);
+            }
+        }
+    } else if (warp >= 2 && warp < EPI_END) {
         // epilogue: this warp reads TMEM lanes 32*(warp % 4) .. +31 = tile rows
         const int q = warp & 3;
         int ti = 0;
@@ -774,7 +852,7 @@ __global__ void __launch_bounds__(pers_threads<EPI>(), 1) tc_gemm_persistent(
             const uint32_t trow = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
             if constexpr (EPI == EPI_BOX) {
                 box_epilogue<BN>(g, trow, m0 + q * 32 + lane, n0);
-            } else if constexpr (EPI == EPI_YTHOMAS) {
+            } else if constexpr (YT) {
                 const int half = (warp - 2) >> 2;
                 float* xch = xbase + ((ti & 1) * 4 + q) * 64;
                 if (!ythomas_twist_epilogue<SPLIT>(g, trow, m0 + q * 32 + lane, plane, half, xch,
