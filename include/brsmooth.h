@@ -235,6 +235,19 @@ int brsmooth_sweep_batched(brs_ctx* c, void* u_packed, const void* b_packed, int
 int brsmooth_create_level(int npatch, const int* dims, const int* nbr,
                           const brs_params* common, brs_ctx** out);
 
+/*
+ * Keep a level's ghost layers across calls of brsmooth_sweep_batched (on != 0) or gather
+ * them at every call's first step (on == 0, the default).  Sec. 2 refreshes the ghosts from
+ * the face neighbours after every complete step; when on, the last step of a call also
+ * writes its faces into the ghost array that the next step reads, and the next call's first
+ * step uses them instead of gathering from the iterate.  The caller promises that the
+ * iterate the next call receives holds exactly the values the previous call left (nothing
+ * else writes it in between); then n calls of m steps equal one call of n m steps.  The
+ * first call after switching on gathers.  Errors: BRS_ERR_ARG if `c` is null or not a
+ * level context.
+ */
+int brsmooth_level_keep_ghosts(brs_ctx* c, int on);
+
 /* Launch shape the autotuner chose for a batched context (host outputs). */
 int brsmooth_batched_config(const brs_ctx* c, int* kchunk, int* warps_per_cta, int* ctas,
                             int* work_items);

@@ -92,6 +92,8 @@ def lib():
     L.brsmooth_create_level.restype = I
     IP = ctypes.POINTER(ctypes.c_int)
     L.brsmooth_batched_config.argtypes = [P, IP, IP, IP, IP]
+    L.brsmooth_level_keep_ghosts.argtypes = [P, I]
+    L.brsmooth_level_keep_ghosts.restype = I
     DP = ctypes.POINTER(D)
     L.brsmooth_defect_correction.argtypes = [P, P, P, P, D, I, I, IP, DP, DP, P]
     L.brsmooth_defect_correction.restype = I
@@ -205,6 +207,10 @@ def brsmooth_create_level(dims, nbr, p: brs_params):
 
 def brsmooth_sweep_batched(ctx, u_ptr, b_ptr, nsweeps: int, stream) -> int:
     return lib().brsmooth_sweep_batched(ctx, u_ptr, b_ptr, int(nsweeps), ctypes.c_void_p(stream))
+
+
+def brsmooth_level_keep_ghosts(ctx, on: bool) -> int:
+    return lib().brsmooth_level_keep_ghosts(ctx, 1 if on else 0)
 
 
 def brsmooth_batched_config(ctx):
@@ -457,6 +463,12 @@ class BatchedContext:
                                     _stream_handle(stream))
         _check(rc, "brsmooth_sweep_batched")
         return u
+
+    def keep_ghosts(self, on: bool = True):
+        """Level contexts: keep the ghost layers across calls (the caller leaves the iterate
+        untouched between calls), so a call's first step does not gather them."""
+        _check(brsmooth_level_keep_ghosts(self.h, on), "brsmooth_level_keep_ghosts")
+        return self
 
     def config(self):
         rc, cfg = brsmooth_batched_config(self.h)

@@ -566,6 +566,13 @@ int brsmooth_batched_config(const brs_ctx* c, int* kchunk, int* warps_per_cta, i
     return BRS_OK;
 }
 
+int brsmooth_level_keep_ghosts(brs_ctx* c, int on)
+{
+    if (!c || !c->batch)
+        return BRS_ERR_ARG;
+    return level_keep_ghosts(c, on);
+}
+
 long long brsmooth_cells(const brs_ctx* c)
 {
     return c ? c->cells : 0;

@@ -41,6 +41,7 @@ struct Graph {
     const void* u;
     const void* b;
     int nsweeps;
+    int mode;  // level ghost chaining at capture: bit 0 on, bit 1 ghosts valid, bit 2 parity
     cudaGraphExec_t exec;
 };
 
@@ -71,6 +72,12 @@ struct BatchState {
     void* ghost2 = nullptr;      // the second ghost buffer (written during a step, read by the next)
     long long* d_push = nullptr; // 6 per patch: where each face goes in a ghost buffer, or -1
     bool push = true;            // steps after a call's first write their faces themselves
+    // ghosts kept across calls (brsmooth_level_keep_ghosts): the last step of a call also
+    // writes its faces, and the next call's first step reads them instead of gathering;
+    // gpar is the ghost buffer the next step reads (0: ghost, 1: ghost2)
+    bool keep = false;
+    bool gvalid = false;
+    int gpar = 0;
     int stages = 4;             // its ring depth (z-steps of lookahead per warp)
 };
 
@@ -842,18 +849,22 @@ int enqueue_sweeps(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t
     void* cur = u;
     void* nxt = gs ? u : c->scratch;
     int rc = BRS_OK;
+    const bool chain = B->level && B->push && B->keep;
+    const int par0 = chain ? B->gpar : 0;
     for (int k = 0; k < nsweeps && rc == BRS_OK; ++k) {
         void* gcur = nullptr;
         void* gnext = nullptr;
         if (B->level) {
-            // the call's first step gathers its ghost layer from the iterate; every step
-            // but the last then writes the next step's ghosts as it computes its faces
+            // the call's first step gathers its ghost layer from the iterate (unless the
+            // previous call left it, ghosts kept across calls); every step but the last (every
+            // step, when kept) then writes the next step's ghosts as it computes its faces
             // (two buffers, alternating)
-            gcur = (B->push && (k & 1)) ? B->ghost2 : B->ghost;
-            if (!B->push || k == 0)
+            const int idx = (par0 + k) & 1;
+            gcur = (B->push && idx) ? B->ghost2 : B->ghost;
+            if (!B->push || (k == 0 && !(chain && B->gvalid)))
                 rc = level_exchange(c, cur, gcur, s);
-            if (B->push && k + 1 < nsweeps)
-                gnext = (k & 1) ? B->ghost : B->ghost2;
+            if (B->push && (k + 1 < nsweeps || chain))
+                gnext = idx ? B->ghost : B->ghost2;
         }
         if (rc == BRS_OK)
             rc = launch_one(c, cur, nxt, b, B->d_counters + k, s, gcur, gnext);
@@ -1168,9 +1179,20 @@ int batched_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t 
     int rc = ensure_counters(B, nsweeps);
     if (rc != BRS_OK)
         return rc;
+    const bool chain = B->level && B->push && B->keep;
+    const int mode = chain ? (1 | (B->gvalid ? 2 : 0) | (B->gpar << 2)) : 0;
+    // after this call the kept ghosts are valid and sit in the buffer its next step would read
+    auto advance = [&]() {
+        if (chain) {
+            B->gpar = (B->gpar + nsweeps) & 1;
+            B->gvalid = true;
+        }
+    };
     for (auto& g : B->graphs)
-        if (g.u == u && g.b == b && g.nsweeps == nsweeps)
+        if (g.u == u && g.b == b && g.nsweeps == nsweeps && g.mode == mode) {
+            advance();
             return brs_cuda_status(cudaGraphLaunch(g.exec, s));
+        }
     // capture this call's sweep sequence once on the private stream, replay on `s`
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
@@ -1192,8 +1214,20 @@ int batched_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t 
         cudaGraphExecDestroy(B->graphs.front().exec);
         B->graphs.erase(B->graphs.begin());
     }
-    B->graphs.push_back({u, b, nsweeps, exec});
+    B->graphs.push_back({u, b, nsweeps, mode, exec});
+    advance();
     return brs_cuda_status(cudaGraphLaunch(exec, s));
+}
+
+int level_keep_ghosts(brs_ctx* c, int on)
+{
+    BatchState* B = bs(c);
+    if (!B || !B->level)
+        return BRS_ERR_ARG;
+    B->keep = on != 0 && B->push;
+    B->gvalid = false;
+    B->gpar = 0;
+    return BRS_OK;
 }
 
 void batched_describe(const brs_ctx* c, int* kc, int* warps, int* grid, int* nitems)

@@ -8,4 +8,5 @@ int batched_setup(brs_ctx* c, int npatch, const int* dims);
 int level_setup(brs_ctx* c, const int* nbr);
 void batched_teardown(brs_ctx* c);
 int batched_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s);
+int level_keep_ghosts(brs_ctx* c, int on);
 void batched_describe(const brs_ctx* c, int* kc, int* warps, int* grid, int* nitems);

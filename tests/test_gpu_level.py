@@ -108,6 +108,64 @@ def test_paper_level_three_steps_per_call(brs, push, monkeypatch):
     assert np.array_equal(one, three)
 
 
+@pytest.mark.parametrize("name", list(LAYOUTS))
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_level_ghosts_kept_across_calls(brs, orc, name, dt):
+    """With the ghosts kept across calls (the iterate untouched in between), the last step
+    of a call writes its faces for the next call's first step: 4 calls of 3 steps equal one
+    call of 12 steps bit for bit, and the oracle's level Jacobi after 12 steps.  Odd step
+    counts per call exercise both ghost buffers at a call's start."""
+    dims, nbr = LAYOUTS[name]
+    n = int(np.prod(dims, axis=1).sum())
+    a = (1.0, 0.5, 0.25)
+    u = rounded(uniform_field((n,), 41), dt)
+    b = rounded(uniform_field((n,), 42) * 1e-3, dt)
+    with brs.BatchedContext(dims, a, method="jacobi", dtype=dt, nbr=nbr) as ctx:
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
+        ctx.sweep(ut, bt, 12)
+        twelve = to_np(ut)
+    with brs.BatchedContext(dims, a, method="jacobi", dtype=dt, nbr=nbr) as ctx:
+        ctx.keep_ghosts(True)
+        ut, bt = to_dev(u, dt), to_dev(b, dt)
+        for _ in range(4):
+            ctx.sweep(ut, bt, 3)
+        kept = to_np(ut)
+        assert brs.brsmooth_last_error(ctx.h) == 0
+    assert np.array_equal(twelve, kept)
+    ref = u.astype(np.float64)
+    for _ in range(12):
+        ref = orc.level_sweep(ref, b.astype(np.float64), dims, nbr, a, method="jacobi", omega=0.8)
+    assert rel_max_err(kept, ref) <= TOL[dt] * 12
+
+
+def test_level_keep_ghosts_paper_level_and_errors(brs):
+    """The 96 x 64^3 level, FP32 Jacobi, three steps per call with the ghosts kept (the
+    benchmark's chained form): 3 calls equal one call of 9 steps bit for bit; switching off
+    returns to a gather at every call's start; a batched context without faces is refused."""
+    P, pdim = (4, 4, 6), (64, 64, 64)
+    dims, nbr = tiling(P, pdim)
+    n = 96 * 64 ** 3
+    u = rounded(uniform_field((n,), 43), "f32")
+    b = rounded(uniform_field((n,), 44) * (1.0 / 65) ** 2, "f32")
+    with brs.BatchedContext(dims, (1, 1, 1), method="jacobi", dtype="f32", nbr=nbr) as ctx:
+        ut, bt = to_dev(u, "f32"), to_dev(b, "f32")
+        ctx.sweep(ut, bt, 9)
+        nine = to_np(ut)
+        ut.copy_(to_dev(u, "f32"))
+        ctx.keep_ghosts(True)
+        for _ in range(3):
+            ctx.sweep(ut, bt, 3)
+        assert np.array_equal(to_np(ut), nine)
+        # off again: the next call gathers; the iterate changed outside the context meanwhile
+        ctx.keep_ghosts(False)
+        ut.copy_(to_dev(u, "f32"))
+        ctx.sweep(ut, bt, 9)
+        assert np.array_equal(to_np(ut), nine)
+        assert brs.brsmooth_last_error(ctx.h) == 0
+    with brs.BatchedContext([[16, 8, 8]], (1, 1, 1), method="jacobi", dtype="f32") as plain:
+        assert brs.brsmooth_level_keep_ghosts(plain.h, True) == brs.BRS_ERR_ARG
+
+
 def test_level_gs_converges_to_global_solution(brs, orc):
     P, pdim = (2, 2, 2), (12, 10, 8)
     dims, nbr = tiling(P, pdim)
