@@ -839,7 +839,8 @@ def _variant_level(brs, stream, barrier, which, dt="f32"):
 def _variant_defect(brs, stream):
     """512^3, a=(1,0.1,0.01): FP32 plane sweeps inside FP64 defect correction vs plain FP64
     plane Jacobi.  The inner sweeps (block Jacobi, omega = 0.8, or two-colour block GS,
-    omega = 1) and their count per outer step m are chosen by timed full solves on 64^3
+    omega = 1; split-TF32 or single-TF32 products) and their count per outer step m are
+    chosen by timed full solves on 64^3
     (where the plain FP64 solve is measured too); the 512^3 mixed solve then runs to
     ||r||/||b|| <= 1e-10 and is compared with the oracle's exact solution; the plain FP64
     solve at 512^3 (about 14 000 sweeps) is a projection from timed sweeps."""
@@ -853,10 +854,11 @@ def _variant_defect(brs, stream):
     b = torch.from_numpy(rhs((n, n, n))).cuda()
     per = {}
     with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64:
-        for meth in ("jacobi", "gs"):
-            with brs.Context(n, n, n, a, block="plane", method=meth, dtype="f32") as i32:
-                # full solves to 1e-10 for m in {8, 32, 128}; the fastest (method, m) is kept
-                # (a measured choice) and used at 512^3 below
+        for meth, arith in ((mm, pm) for mm in ("jacobi", "gs") for pm in ("3xtf32", "tf32")):
+            with brs.Context(n, n, n, a, block="plane", method=meth, dtype="f32",
+                             plane_math=arith) as i32:
+                # full solves to 1e-10 for m in {8, 32, 128}; the fastest (method, products,
+                # m) is kept (a measured choice) and used at 512^3 below
                 for m in (8, 32, 128):
                     u = torch.zeros_like(b)
                     brs.defect_correction(o64, i32, u, b, rtol=1e-10, inner_sweeps=m,
@@ -866,11 +868,12 @@ def _variant_defect(brs, stream):
                     t0 = time.perf_counter()
                     d_m, r_m, _ = brs.defect_correction(o64, i32, u, b, rtol=1e-10,
                                                         inner_sweeps=m, max_outer=500)
-                    per[f"{meth}_m{m}"] = {"inner": meth, "m": m, "outer": d_m,
+                    per[f"{meth}_{arith}_m{m}"] = {"inner": meth, "math": arith, "m": m,
+                                                  "outer": d_m,
                                            "inner_sweeps": d_m * m, "rel_residual": r_m,
                                            "s": time.perf_counter() - t0, "u": u.clone()}
         best = min(per, key=lambda k: per[k]["s"])
-        best_meth, best_m = per[best]["inner"], per[best]["m"]
+        best_meth, best_m, best_math = per[best]["inner"], per[best]["m"], per[best]["math"]
         u64 = torch.zeros_like(b)
         sweeps, r = 0, 1.0
         nb = float(torch.linalg.norm(b))
@@ -887,6 +890,7 @@ def _variant_defect(brs, stream):
     for v in per.values():
         del v["u"]
     out["grid64_full_solve"] = {"err_vs_oracle_exact_rel_max": errs, "inner": best_meth,
+                                "inner_products": best_math,
                                 "inner_sweeps_m": best_m, "per_choice": per,
                                 "mixed_outer": per[best]["outer"],
                                 "mixed_inner_sweeps": per[best]["inner_sweeps"],
@@ -899,7 +903,8 @@ def _variant_defect(brs, stream):
     b_np = rhs((n, n, n))
     b = torch.from_numpy(b_np).cuda()
     with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64, \
-            brs.Context(n, n, n, a, block="plane", method=best_meth, dtype="f32") as i32:
+            brs.Context(n, n, n, a, block="plane", method=best_meth, dtype="f32",
+                        plane_math=best_math) as i32:
         u = torch.zeros_like(b)
         brs.defect_correction(o64, i32, u, b, rtol=0.0, inner_sweeps=best_m, max_outer=1)
         u.zero_()
@@ -930,7 +935,8 @@ def _variant_defect(brs, stream):
     mu = a[0] * s1 + a[1] * s1 + 2 * a[2]
     g = 1 - 0.8 * lam / mu
     sweeps_needed = math.log(1e-10) / math.log(g)
-    out["grid512"] = {"inner": best_meth, "inner_sweeps_m": best_m, "mixed_s_measured": t_mixed,
+    out["grid512"] = {"inner": best_meth, "inner_products": best_math, "inner_sweeps_m": best_m,
+                      "mixed_s_measured": t_mixed,
                       "mixed_outer": done, "mixed_inner_sweeps": done * best_m,
                       "mixed_rel_residual": rel,
                       "ms_per_fp64_plane_jacobi_sweep": ms_f64,
