@@ -243,17 +243,18 @@ def _rel_err(got, ref):
     return float(np.max(np.abs(got - ref))) / (s if s > 0 else 1.0)
 
 
-def _sampled_block_err(orc, blk, box, a, method, omega, u, b, got, picks):
-    """Largest error of `got` (the GPU's iterate after one sweep from u) over the sampled
+def _sampled_block_err(orc, blk, box, a, method, omega, u, b, got, picks, nsweeps=1):
+    """Largest error of `got` (the GPU's iterate after nsweeps sweeps from u) over the sampled
     blocks `picks` (block indices (bi, bj, bk)), relative to the oracle block's max-norm and
-    relative to the input's max-norm; oracle cells and seconds."""
+    relative to the input's max-norm; oracle cells and seconds.  A block after s sweeps
+    depends only on blocks within s of it (2 s in the zebra order)."""
     import numpy as np
 
     nz, ny, nx = u.shape
     bx, by, bz = _block_dims(blk, box, u.shape)
     nb = (nx // bx, ny // by, nz // bz)
     zebra = method == "gs_zebra"
-    rad = 2 if zebra else 1
+    rad = (2 if zebra else 1) * nsweeps
     worst, worst_in, cells, secs = 0.0, 0.0, 0, 0.0
     scale_in = float(np.max(np.abs(u)))
     for pk in picks:
@@ -265,10 +266,12 @@ def _sampled_block_err(orc, blk, box, a, method, omega, u, b, got, picks):
         sl = (slice(lo[2] * bz, hi[2] * bz), slice(lo[1] * by, hi[1] * by),
               slice(lo[0] * bx, hi[0] * bx))
         t0 = time.perf_counter()
-        ref = _orc_sweep(orc, np.ascontiguousarray(u[sl]), np.ascontiguousarray(b[sl]), a, blk,
-                         box, method, omega)
+        ref = np.ascontiguousarray(u[sl])
+        bs = np.ascontiguousarray(b[sl])
+        for _ in range(nsweeps):
+            ref = _orc_sweep(orc, ref, bs, a, blk, box, method, omega)
         secs += time.perf_counter() - t0
-        cells += ref.size
+        cells += ref.size * nsweeps  # cell-updates
         c = [(pk[q] - lo[q]) for q in range(3)]
         own = (slice(c[2] * bz, (c[2] + 1) * bz), slice(c[1] * by, (c[1] + 1) * by),
                slice(c[0] * bx, (c[0] + 1) * bx))
@@ -290,7 +293,7 @@ def _picks(blk, box, shape, k=6):
     return out
 
 
-def _gpu_one_sweep(brs, stream, blk, meth, dt, a, math, box, u_np, b_np):
+def _gpu_sweeps(brs, stream, blk, meth, dt, a, math, box, u_np, b_np, nsweeps=1):
     import torch
 
     td = torch.float64 if dt == "f64" else torch.float32
@@ -299,7 +302,7 @@ def _gpu_one_sweep(brs, stream, blk, meth, dt, a, math, box, u_np, b_np):
     bt = torch.from_numpy(b_np).to(td).cuda()
     with brs.Context(nx, ny, nz, a, block=blk, method=meth, dtype=dt, plane_math=math,
                      box=box) as c:
-        c.sweep(ut, bt, 1, stream=stream)
+        c.sweep(ut, bt, nsweeps, stream=stream)
         torch.cuda.synchronize()
         if c.last_error() != 0:
             raise RuntimeError("device status raised")
@@ -357,8 +360,8 @@ def _bracket_leg(orc, brs, stream, blk, dt, a, math, box, shape, sweeps=3):
                        f"{nx}x{ny}x{nz} grid, {secs:.2f} s"})
 
 
-def _grid_cpu_leg(brs, stream, blk, meth, dt, a, math, box):
-    """cpu_baseline and err_vs_oracle of a 256^3 variant."""
+def _grid_cpu_leg(brs, stream, blk, meth, dt, a, math, box, nsweeps=1):
+    """cpu_baseline and err_vs_oracle of a 256^3 variant (nsweeps sweeps in one call)."""
     import numpy as np
 
     orc = _orc()
@@ -368,13 +371,15 @@ def _grid_cpu_leg(brs, stream, blk, meth, dt, a, math, box):
             blk, (128, 256, 256))
         return _bracket_leg(orc, brs, stream, blk, dt, a, math, box, small)
     u_np, b_np = (x.double().numpy() for x in _inputs(dt))
-    got = _gpu_one_sweep(brs, stream, blk, meth, dt, a, math, box, u_np, b_np)
+    got = _gpu_sweeps(brs, stream, blk, meth, dt, a, math, box, u_np, b_np, nsweeps)
     omet = "jacobi" if meth == "jacobi" else "gs_zebra"
     om = 0.8 if meth == "jacobi" else 1.0
     err, err_in, cells, secs = _sampled_block_err(orc, blk, box, a, omet, om, u_np, b_np, got,
-                                                  _picks(blk, box, u_np.shape))
-    tol = 1e-12 if dt == "f64" else (2.0 ** -11 if math == "tf32" else 1e-5)
-    rec = {"metric": "relative max-norm after one sweep, sampled blocks vs the oracle's "
+                                                  _picks(blk, box, u_np.shape), nsweeps)
+    tol = 1e-12 if dt == "f64" else ((2.0 ** -10 if nsweeps > 1 else 2.0 ** -11)
+                                     if math == "tf32" else 1e-5)
+    what = "one sweep" if nsweeps == 1 else f"{nsweeps} sweeps in one call"
+    rec = {"metric": f"relative max-norm after {what}, sampled blocks vs the oracle's "
                      + ("zebra-order GS" if meth == "gs" else "Jacobi"),
            "value": err, "tolerance": tol, "blocks_sampled": 6}
     if meth == "gs":
@@ -386,8 +391,8 @@ def _grid_cpu_leg(brs, stream, blk, meth, dt, a, math, box):
     return (rec,
             {"value": cells / secs / 1e9, "unit": UNIT, "cores": orc.num_threads(),
              "kind": "oracle",
-             "sample": f"oracle {omet} sweeps of the sub-grids around 6 sampled blocks "
-                       f"({cells} cells, {secs:.2f} s)"})
+             "sample": f"oracle {omet} sweeps ({nsweeps} each) of the sub-grids around 6 "
+                       f"sampled blocks ({cells} cell-updates, {secs:.2f} s)"})
 
 
 def run_reference(args):
@@ -514,18 +519,38 @@ def _plane_form(ny):
     return 1 if os.environ.get("BRSMOOTH_PLANE_FORM", "1") == "1" and ny <= 512 else 2
 
 
+def _plane_modes_min(dt, math):
+    """Smallest sweep count per call for which the library runs the x-sine form (plane
+    contexts whose y rows TMA can stage; 0 when switched off by BRSMOOTH_PLANE_MODES=0)."""
+    if os.environ.get("BRSMOOTH_PLANE_MODES", "1") == "0":
+        return 0
+    if os.environ.get("BRSMOOTH_PLANE_MODES_MIN"):
+        return max(1, int(os.environ["BRSMOOTH_PLANE_MODES_MIN"]))
+    return 3 if dt == "f32" and math in ("auto", "tf32", "3xtf32") else 2
+
+
 def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, math="auto",
                   box=(0, 0, 0)):
-    """One 256^3 workload variant: steps x sweeps sweeps timed with CUDA events."""
+    """One 256^3 workload variant: steps x sweeps sweeps timed with CUDA events.  For the
+    x-sine form of plane calls, calls of fewer sweeps are timed too: the difference gives
+    the time of one mode-line sweep and the fixed cost of a call's three transforms."""
     uv0, bv = _inputs(dt)
     uv, bv = uv0.cuda(), bv.cuda()
+    mmin = _plane_modes_min(dt, math) if blk == "plane" else 0
+    modes = mmin > 0 and sweeps >= mmin
+    s_lo = max(mmin, sweeps // 5)
+    es = 8 if dt == "f64" else 4
     with brs.Context(N, N, N, a, block=blk, method=meth, dtype=dt, plane_math=math,
                      box=box) as vc:
         vms = _time_sweeps(vc, uv, bv, steps, 1, sweeps, stream, barrier)
-    es = 8 if dt == "f64" else 4
+        if modes and s_lo < sweeps:
+            lo_ms = _time_sweeps(vc, uv, bv, steps, 1, s_lo, stream, barrier)
+            sweep_ms = (vms - lo_ms) / (steps * (sweeps - s_lo))
+            fixed_ms = vms / steps - sweeps * sweep_ms
     rate = _rate(N ** 3, sweeps * steps, vms)
     out = {"workload": "grid256", "block": blk, "method": meth, "dtype": dt, "coeffs": a,
-           "value": rate, "unit": UNIT, "hbm_frac": rate * 3 * es / peak}
+           "value": rate, "unit": UNIT, "hbm_frac": rate * 3 * es / peak,
+           "sweeps_per_call": sweeps}
     fma = _fma_rate(brs, stream) / 1e9 if dt == "f64" else None
     if blk == "box":
         # the dense block product: n multiply-adds per cell, n = bx by bz (Alg. 2 step 2)
@@ -543,7 +568,27 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
             out["alu_frac_of_fp64_fma_rate"] = rate * nb / fma
     if blk == "plane" and math == "auto":
         math = "3xtf32" if dt == "f32" and N % 32 == 0 else "simt"  # the library's choice
-    if blk == "plane":
+    if blk == "plane" and modes:
+        # x-sine form: per call, the x-DST of b and of u and the inverse x-DST of u (nx
+        # multiply-adds per cell each), then mode-line sweeps: 3 words per cell, HBM-bound
+        passes = 3 if math == "3xtf32" else 1
+        out["plane_form"] = "x-sine basis: 3 transforms per call + mode-line sweeps"
+        out["plane_math"] = math
+        out["tflops"] = 6.0 * N * rate / sweeps / 1e3
+        if s_lo < sweeps:
+            out["mode_sweep_us"] = sweep_ms * 1e3
+            out["mode_sweep_gcell"] = N ** 3 / (sweep_ms / 1e3) / 1e9
+            out["mode_sweep_hbm_frac"] = 3 * es * N ** 3 / (sweep_ms / 1e3) / 1e9 / peak
+            out["transforms_ms_per_call"] = fixed_ms
+            out["transforms_timing"] = (f"calls of {sweeps} and {s_lo} sweeps, the difference "
+                                        "per sweep and the remainder per call")
+            if math in ("tf32", "3xtf32"):
+                out["transforms_tensor_tflops"] = (3 * 2.0 * N * N ** 3 * passes
+                                                   / (fixed_ms / 1e3) / 1e12)
+            if dt == "f64":
+                out["transforms_frac_of_fp64_fma_rate"] = (3.0 * N * N ** 3 / (fixed_ms / 1e3)
+                                                           / (fma * 1e9))
+    elif blk == "plane":
         # dense contractions per plane: form 1 (x sine transform + y tridiagonal solves) runs
         # the forward and inverse x transforms, nx multiply-adds per cell each; form 2 (2D
         # sine basis) runs four, 2 (nx + ny) multiply-adds per cell in all
@@ -571,8 +616,9 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
     if dt == "f64":
         out["fp64_fma_rate_g"] = fma
     if not _NO_CPU_LEGS["on"]:
-        out["err_vs_oracle"], out["cpu_baseline"] = _grid_cpu_leg(brs, stream, blk, meth, dt,
-                                                                  a, math, box)
+        # the x-sine form runs in calls of several sweeps: check such a call
+        out["err_vs_oracle"], out["cpu_baseline"] = _grid_cpu_leg(
+            brs, stream, blk, meth, dt, a, math, box, nsweeps=max(3, mmin) if modes else 1)
     return out
 
 
@@ -836,6 +882,44 @@ def _variant_level(brs, stream, barrier, which, dt="f32"):
     return out
 
 
+FP64_CALL_SWEEPS = 1000  # plain FP64 plane Jacobi at 512^3: sweeps per call (residual between)
+
+
+def _variant_defect512_fp64(brs, stream):
+    """512^3, a=(1,0.1,0.01): the plain FP64 plane-Jacobi solve to ||r||/||b|| <= 1e-10 run
+    in full (calls of FP64_CALL_SWEEPS sweeps, the FP64 residual after each), measured, and
+    its distance to the oracle's exact solution."""
+    import torch
+
+    from brs_inputs import rhs
+
+    a = (1.0, 0.1, 0.01)
+    n = 512
+    b_np = rhs((n, n, n))
+    b = torch.from_numpy(b_np).cuda()
+    nb = float(torch.linalg.norm(b))
+    with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64:
+        u = torch.zeros_like(b)
+        o64.sweep(u, b, 2)
+        u.zero_()
+        sweeps, r, hist = 0, 1.0, []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while r > 1e-10 and sweeps < 40000:
+            o64.sweep(u, b, FP64_CALL_SWEEPS)
+            sweeps += FP64_CALL_SWEEPS
+            r = o64.residual(u, b) / nb
+            hist.append(r)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        assert o64.last_error() == 0
+    out = {"workload": "grid512_aniso plain FP64 plane Jacobi to 1e-10", "coeffs": a,
+           "sweeps": sweeps, "sweeps_per_call": FP64_CALL_SWEEPS, "rel_residual": r,
+           "s_measured": t, "residual_per_call": hist}
+    out["err_vs_oracle"], out["cpu_baseline"] = _defect_cpu_leg(b_np, a, u.cpu().numpy(), r)
+    return out
+
+
 def _variant_defect(brs, stream):
     """512^3, a=(1,0.1,0.01): FP32 plane sweeps inside FP64 defect correction vs plain FP64
     plane Jacobi.  The inner sweeps (block Jacobi, omega = 0.8, or two-colour block GS,
@@ -916,16 +1000,23 @@ def _variant_defect(brs, stream):
         t_mixed = time.perf_counter() - t0
         u_gpu = u.cpu().numpy()
         del u
+        # plain FP64 plane Jacobi in calls of K1 and K2 sweeps (the x-sine form): the
+        # difference gives the time per sweep, the rest the fixed cost of a call
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         u64 = torch.zeros_like(b)
-        o64.sweep(u64, b, 1)
-        torch.cuda.synchronize()
-        e0.record(stream)
         o64.sweep(u64, b, 2)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_f64 = e0.elapsed_time(e1) / 2
+        t_call = {}
+        for k in (FP64_CALL_SWEEPS // 4, FP64_CALL_SWEEPS):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            o64.sweep(u64, b, k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_call[k] = e0.elapsed_time(e1)
+        k1, k2 = sorted(t_call)
+        ms_f64 = (t_call[k2] - t_call[k1]) / (k2 - k1)
+        ms_call_f64 = t_call[k2] - k2 * ms_f64
         del u64
     import math
 
@@ -935,16 +1026,22 @@ def _variant_defect(brs, stream):
     mu = a[0] * s1 + a[1] * s1 + 2 * a[2]
     g = 1 - 0.8 * lam / mu
     sweeps_needed = math.log(1e-10) / math.log(g)
+    t_f64_proj = (sweeps_needed * ms_f64 + math.ceil(sweeps_needed / FP64_CALL_SWEEPS)
+                  * ms_call_f64) / 1e3
     out["grid512"] = {"inner": best_meth, "inner_products": best_math, "inner_sweeps_m": best_m,
                       "mixed_s_measured": t_mixed,
                       "mixed_outer": done, "mixed_inner_sweeps": done * best_m,
                       "mixed_rel_residual": rel,
                       "ms_per_fp64_plane_jacobi_sweep": ms_f64,
+                      "ms_fixed_per_fp64_call": ms_call_f64,
+                      "fp64_sweeps_per_call": FP64_CALL_SWEEPS,
                       "fp64_sweeps_to_1e-10_projected": sweeps_needed,
-                      "fp64_s_projected": sweeps_needed * ms_f64 / 1e3,
-                      "speedup_mixed_vs_fp64_projected": sweeps_needed * ms_f64 / 1e3 / t_mixed,
+                      "fp64_s_projected": t_f64_proj,
+                      "speedup_mixed_vs_fp64_projected": t_f64_proj / t_mixed,
                       "note": "mixed: measured wall time of the whole solve; FP64: measured "
-                              "ms/sweep x log(1e-10)/log(g_111), a projection"}
+                              "ms per sweep x log(1e-10)/log(g_111) sweeps plus the measured "
+                              "fixed cost of each call of fp64_sweeps_per_call sweeps, a "
+                              "projection (bench.py --only defect512_fp64 runs that solve)"}
     out["grid512"]["err_vs_oracle"], out["grid512"]["cpu_baseline"] = _defect_cpu_leg(
         b_np, a, u_gpu, rel)
     return out
@@ -1164,7 +1261,7 @@ def _config2_matrix():
                     if blk == "line":
                         st, sw = (2, 50) if dt == "f64" else (6, 50)
                     else:
-                        st, sw = (1, 2) if dt == "f64" else (4, 10)
+                        st, sw = (1, 50) if dt == "f64" else (4, 50)
                     out[f"{blk}_{meth}_{dt}_{tag}"] = (blk, meth, dt, a, st, sw, "auto")
     return out
 
@@ -1172,8 +1269,14 @@ def _config2_matrix():
 VARIANTS = dict(_config2_matrix())
 VARIANTS.update({
     # other arithmetic of the FP32 plane solve
-    "plane_jacobi_f32_tf32_aniso": ("plane", "jacobi", "f32", ANISO, 4, 10, "tf32"),
-    "plane_jacobi_f32_simt_aniso": ("plane", "jacobi", "f32", ANISO, 2, 10, "simt"),
+    "plane_jacobi_f32_tf32_aniso": ("plane", "jacobi", "f32", ANISO, 4, 50, "tf32"),
+    "plane_jacobi_f32_simt_aniso": ("plane", "jacobi", "f32", ANISO, 2, 50, "simt"),
+    # the per-sweep form of the plane solve (two tensor-core products per sweep), which
+    # calls of one or two sweeps run (BRSMOOTH_PLANE_MODES=0 below)
+    "plane_jacobi_f32_aniso_per_sweep": ("plane", "jacobi", "f32", ANISO, 4, 10, "auto"),
+    "plane_gs_f32_aniso_per_sweep": ("plane", "gs", "f32", ANISO, 4, 10, "auto"),
+    "plane_jacobi_f32_tf32_aniso_per_sweep": ("plane", "jacobi", "f32", ANISO, 4, 10, "tf32"),
+    "plane_jacobi_f64_aniso_per_sweep": ("plane", "jacobi", "f64", ANISO, 1, 2, "auto"),
     # y- and z-lines (x-line sweeps of the permuted grid; three grid passes per call)
     "yline_jacobi_f32": ("yline", "jacobi", "f32", (0.01, 1.0, 0.01), 6, 50, "auto"),
     "zline_jacobi_f32": ("zline", "jacobi", "f32", (0.01, 0.01, 1.0), 6, 50, "auto"),
@@ -1195,7 +1298,7 @@ BOX_VARIANTS = {
 }
 SPECIAL = ("batched600", "level96x64", "table2_mixed", "level96x64_f64", "defect512", "adjoint",
            "block_study64")
-PROFILE_ONLY = ("batched600_graph", "plane512_f32")
+PROFILE_ONLY = ("batched600_graph", "plane512_f32", "defect512_fp64")
 
 
 # the headline workload as a named variant, for profiling runs (`--only`)
@@ -1223,6 +1326,23 @@ def _variant_plane512(brs, stream, barrier, steps):
 
 
 def _run_variant(name, brs, stream, barrier, peak, steps=None):
+    if name.endswith("_per_sweep"):
+        # environment of the library's context set-up, restored afterwards
+        old = os.environ.get("BRSMOOTH_PLANE_MODES")
+        os.environ["BRSMOOTH_PLANE_MODES"] = "0"
+        try:
+            out = _run_variant_env(name, brs, stream, barrier, peak, steps)
+        finally:
+            if old is None:
+                del os.environ["BRSMOOTH_PLANE_MODES"]
+            else:
+                os.environ["BRSMOOTH_PLANE_MODES"] = old
+        out["plane_modes"] = "off (per-sweep form)"
+        return out
+    return _run_variant_env(name, brs, stream, barrier, peak, steps)
+
+
+def _run_variant_env(name, brs, stream, barrier, peak, steps=None):
     if name == "batched600":
         return _variant_batched(brs, stream, barrier)
     if name == "batched600_graph":
@@ -1239,6 +1359,8 @@ def _run_variant(name, brs, stream, barrier, peak, steps=None):
         return out
     if name == "defect512":
         return _variant_defect(brs, stream)
+    if name == "defect512_fp64":
+        return _variant_defect512_fp64(brs, stream)
     if name == "adjoint":
         return _variant_adjoint(brs, stream)
     if name == "block_study64":

@@ -347,6 +347,13 @@ int brsmooth_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, void* stream
         return perm_sweep(c, u, b, nsweeps, s);
     if (c->lseq)
         return line_seq_sweep(c, u, b, nsweeps, s);
+    if (c->plane) {
+        // several plane sweeps in one call: the x-sine form, where the context has it
+        rc = plane_modes_sweep(c, u, b, nsweeps, s);
+        if (rc != BRS_ERR_UNSUPPORTED)
+            return rc;
+        rc = BRS_OK;
+    }
     if (c->p.method == BRS_CHAOTIC_GS) {
         for (int k = 0; k < nsweeps && rc == BRS_OK; ++k)
             rc = sweep_one(c, u, u, b, s);

@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "brs_internal.cuh"
+#include "plane.cuh"
 
 namespace {
 
@@ -87,7 +88,12 @@ extern "C" int brsmooth_defect_correction(brs_ctx* outer, brs_ctx* inner, double
             history[it] = rel;
         if (rel <= rtol || it >= max_outer)
             break;
-        rc = brsmooth_sweep(inner, inner->dc_c, inner->dc_r, inner_sweeps, stream);
+        // c starts from zero: a plane context in the x-sine form skips c's transform
+        rc = inner->plane ? plane_modes_sweep(inner, inner->dc_c, inner->dc_r, inner_sweeps, s,
+                                              true)
+                          : BRS_ERR_UNSUPPORTED;
+        if (rc == BRS_ERR_UNSUPPORTED)
+            rc = brsmooth_sweep(inner, inner->dc_c, inner->dc_r, inner_sweeps, stream);
         if (rc != BRS_OK)
             return rc;
         correct_kernel<<<blocks, 256, 0, s>>>(u, inner->dc_c, n);

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "line_impl.cuh"
@@ -77,6 +78,16 @@ struct PlaneState {
     };
     GridMap gmaps[4];
     int gnext = 0;
+    // x-sine form of calls of several sweeps (plane_modes.cu): b^ and u^ as [k][p][y], the
+    // per-mode factor tables with omega folded in, and the tensor maps of the mode arrays
+    int modes = 0;          // available for this context
+    int modes_min = 2;      // smallest sweep count per call that takes it
+    ModeCfg mcfg;
+    void* mb = nullptr;     // b^
+    void* mu = nullptr;     // u^
+    void* mtab = nullptr;   // [nx][mcfg.tab_len], context dtype
+    CUtensorMap mm_b, mm_u, mm_v;  // maps of mb, mu and the Jacobi second vector
+    const void* mm_v_ptr = nullptr;
 };
 
 // Map of a grid for the gather form, encoded on first use of its address.
@@ -736,6 +747,171 @@ int plane_pass(brs_ctx* c, const T* uin, T* uout, const T* b, int k0, int kstep,
     return brs_cuda_status(e);
 }
 
+// ------------------------------------------------------------------- x-sine form
+// A call of several sweeps runs in the x-sine basis (plane_modes.cu): u^ = S_x u and
+// b^ = S_x b once (layout [k][p][y]), the sweeps as mode-line sweeps of u^, then u = S_x u^.
+// The transforms are the x-DST products of the per-sweep form: P1 (A = Sx, B = the grid) for
+// the forward one, P4 (A = u^ as [k][y][p], B = Sx) for the inverse one.
+
+// TF32 split of an FP32 array, four values per thread with 16-byte accesses.
+__global__ void split_tf32_kernel(const float* __restrict__ x, float* __restrict__ hi,
+                                  float* __restrict__ lo, long long n4, int split)
+{
+    pdl_wait_trigger();
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4* h4 = reinterpret_cast<float4*>(hi);
+    float4* l4 = reinterpret_cast<float4*>(lo);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n4;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float4 v = x4[t];
+        const float r[4] = {v.x, v.y, v.z, v.w};
+        float h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = __uint_as_float(brs_tc::tf32_rn(r[q]));
+            l[q] = __uint_as_float(brs_tc::tf32_rn(r[q] - h[q]));
+        }
+        h4[t] = make_float4(h[0], h[1], h[2], h[3]);
+        if (split == 3)
+            l4[t] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// [k][p][y] -> [k][y][p] through 32 x 32 shared-memory tiles.  SPLIT = 3 / 1: TF32 hi (+ lo)
+// outputs for a tensor-core operand; 0: a plain copy.
+template <typename T, int SPLIT>
+__global__ void __launch_bounds__(256) modes_to_rows_kernel(const T* __restrict__ src,
+                                                            T* __restrict__ hi,
+                                                            T* __restrict__ lo, int nm, int ny,
+                                                            int nz)
+{
+    __shared__ T tile[32][33];
+    pdl_wait_trigger();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int tiles_y = (ny + 31) / 32;
+    const int y0 = (blockIdx.x % tiles_y) * 32, p0 = (blockIdx.x / tiles_y) * 32;
+    const long long plane = (long long)nm * ny;
+    for (int k = blockIdx.y; k < nz; k += gridDim.y) {
+        const T* sk = src + (long long)k * plane;
+        for (int pp = ty; pp < 32; pp += 8) {
+            const int p = p0 + pp, y = y0 + tx;
+            if (p < nm && y < ny)
+                tile[pp][tx] = sk[(long long)p * ny + y];
+        }
+        __syncthreads();
+        for (int yy = ty; yy < 32; yy += 8) {
+            const int y = y0 + yy, p = p0 + tx;
+            if (p < nm && y < ny) {
+                const T v = tile[tx][yy];
+                const long long o = (long long)k * plane + (long long)y * nm + p;
+                if constexpr (SPLIT == 0) {
+                    hi[o] = v;
+                } else {
+                    const float hb = __uint_as_float(brs_tc::tf32_rn((float)v));
+                    hi[o] = hb;
+                    if (SPLIT == 3)
+                        lo[o] = __uint_as_float(brs_tc::tf32_rn((float)v - hb));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+bool modes_simt(const brs_ctx* c, const PlaneState* P)
+{
+    return c->p.dtype == BRS_F64 || P->math == BRS_PLANE_SIMT;
+}
+
+// dst[k][p][y] = sum_x Sx[p][x] src[k][y][x]
+int modes_forward(brs_ctx* c, const void* src, void* dst, cudaStream_t s)
+{
+    PlaneState* P = ps(c);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const long long plane = (long long)nx * ny;
+    cudaError_t e;
+    if (modes_simt(c, P)) {
+        GemmArgs g{};
+        g.M = nx; g.N = ny; g.K = nx; g.strideA = 0; g.strideB = plane; g.strideC = plane;
+        if (c->p.dtype == BRS_F64)
+            e = launch_gemm<double, EPI_STORE>(static_cast<const double*>(P->sx),
+                                               static_cast<const double*>(src),
+                                               static_cast<double*>(dst), g, nz, s);
+        else
+            e = launch_gemm<float, EPI_STORE>(static_cast<const float*>(P->sx),
+                                              static_cast<const float*>(src),
+                                              static_cast<float*>(dst), g, nz, s);
+        return brs_cuda_status(e);
+    }
+    const int split = P->math == BRS_PLANE_3XTF32 ? 3 : 1;
+    const long long n4 = c->cells / 4;  // nx is a multiple of 32 on the tensor path
+    long long blocks = (n4 + 255) / 256;
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    e = launch_pdl(split_tf32_kernel, dim3((unsigned)blocks), dim3(256), 0, s,
+                   static_cast<const float*>(src), (float*)P->t2, (float*)P->t2_lo, n4, split);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    brs_tc::TcArgs g{};
+    g.k0 = 0; g.kstep = 1; g.plane = plane; g.status = c->dev_status;
+    g.M = nx; g.N = ny; g.K = nx; g.a_batched = 0; g.b_batched = 1;
+    g.out_hi = static_cast<float*>(dst); g.out_lo = nullptr; g.out_plain = 1;
+    e = split == 3
+            ? launch_tc<3, brs_tc::EPI_SPLIT>(P, P->m_sx_hi, P->m_sx_lo, P->m_R_hi, P->m_R_lo, g, nz, s)
+            : launch_tc<1, brs_tc::EPI_SPLIT>(P, P->m_sx_hi, P->m_sx_lo, P->m_R_hi, P->m_R_lo, g, nz, s);
+    return brs_cuda_status(e);
+}
+
+// dst[k][y][x] = sum_p Sx[x][p] src[k][p][y]  (S is symmetric)
+int modes_inverse(brs_ctx* c, const void* src, void* dst, cudaStream_t s)
+{
+    PlaneState* P = ps(c);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const long long plane = (long long)nx * ny;
+    const dim3 tgrid((unsigned)(((ny + 31) / 32) * ((nx + 31) / 32)), (unsigned)(nz < 65535 ? nz : 65535));
+    cudaError_t e;
+    if (modes_simt(c, P)) {
+        GemmArgs g{};
+        g.M = ny; g.N = nx; g.K = nx; g.strideA = plane; g.strideB = 0; g.strideC = plane;
+        if (c->p.dtype == BRS_F64) {
+            e = launch_pdl(modes_to_rows_kernel<double, 0>, tgrid, dim3(256), 0, s,
+                           static_cast<const double*>(src), (double*)P->t2, (double*)nullptr, nx,
+                           ny, nz);
+            if (e == cudaSuccess)
+                e = launch_gemm<double, EPI_STORE>((const double*)P->t2,
+                                                   static_cast<const double*>(P->sx),
+                                                   static_cast<double*>(dst), g, nz, s);
+        } else {
+            e = launch_pdl(modes_to_rows_kernel<float, 0>, tgrid, dim3(256), 0, s,
+                           static_cast<const float*>(src), (float*)P->t2, (float*)nullptr, nx,
+                           ny, nz);
+            if (e == cudaSuccess)
+                e = launch_gemm<float, EPI_STORE>((const float*)P->t2,
+                                                  static_cast<const float*>(P->sx),
+                                                  static_cast<float*>(dst), g, nz, s);
+        }
+        return brs_cuda_status(e);
+    }
+    const int split = P->math == BRS_PLANE_3XTF32 ? 3 : 1;
+    e = split == 3 ? launch_pdl(modes_to_rows_kernel<float, 3>, tgrid, dim3(256), 0, s,
+                                static_cast<const float*>(src), (float*)P->t2, (float*)P->t2_lo,
+                                nx, ny, nz)
+                   : launch_pdl(modes_to_rows_kernel<float, 1>, tgrid, dim3(256), 0, s,
+                                static_cast<const float*>(src), (float*)P->t2, (float*)P->t2_lo,
+                                nx, ny, nz);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    brs_tc::TcArgs g{};
+    g.k0 = 0; g.kstep = 1; g.plane = plane; g.status = c->dev_status;
+    g.M = ny; g.N = nx; g.K = nx; g.a_batched = 1; g.b_batched = 0;
+    g.out_hi = static_cast<float*>(dst); g.out_lo = nullptr; g.out_plain = 1;
+    e = split == 3 ? launch_tc<3, brs_tc::EPI_SPLIT>(P, P->m_W2_hi, P->m_W2_lo, P->m_sxB_hi,
+                                                     P->m_sxB_lo, g, nz, s)
+                   : launch_tc<1, brs_tc::EPI_SPLIT>(P, P->m_W2_hi, P->m_W2_lo, P->m_sxB_hi,
+                                                     P->m_sxB_lo, g, nz, s);
+    return brs_cuda_status(e);
+}
+
 // Orthonormal DST-I matrix S[i][j] = sqrt(2/(n+1)) sin((i+1)(j+1) pi/(n+1)).
 std::vector<double> dst1(int n)
 {
@@ -971,6 +1147,60 @@ int fused_setup(brs_ctx* c)
     return BRS_OK;
 }
 
+// x-sine form: per-mode scan-Thomas tables of tridiag(-ay, ax s_p + 2 ay + 2 az, -ay) along y
+// with the context's omega folded in (factored once in FP64), the mode arrays and their
+// maps.  Leaves the form off (per-sweep form only) when BRSMOOTH_PLANE_MODES=0 or the y rows
+// cannot be staged by TMA.
+template <typename T>
+int modes_setup(brs_ctx* c)
+{
+    PlaneState* P = ps(c);
+    const brs_params& p = c->p;
+    const char* env = std::getenv("BRSMOOTH_PLANE_MODES");
+    if (env && *env && std::atoi(env) == 0)
+        return BRS_OK;
+    // measured at 256^3 (same box): two split-TF32 sweeps per call take 0.350 ms in this form
+    // against 0.304 ms per-sweep (three transforms against four products), ten take 0.61 ms
+    // against 1.5; on the SIMT and FP64 paths, whose products are slower, two already gain
+    const char* menv = std::getenv("BRSMOOTH_PLANE_MODES_MIN");
+    const int dflt = (P->math == BRS_PLANE_TF32 || P->math == BRS_PLANE_3XTF32) ? 3 : 2;
+    P->modes_min = (menv && *menv && std::atoi(menv) >= 1) ? std::atoi(menv) : dflt;
+    ModeCfg m;
+    int rc = mode_config(p.ny, p.nx, p.nz, p.dtype, c->device, &m);
+    if (rc == BRS_ERR_UNSUPPORTED)
+        return BRS_OK;
+    if (rc != BRS_OK)
+        return rc;
+    std::vector<T> all;
+    all.reserve((size_t)p.nx * m.tab_len);
+    for (int q = 0; q < p.nx; ++q) {
+        const double sp = 2.0 - 2.0 * std::cos(M_PI * (q + 1) / (p.nx + 1));
+        auto t = scan_thomas_tables<T>(p.ny, p.ay, p.ax * sp + 2.0 * p.ay + 2.0 * p.az, c->omega,
+                                       m.E, m.G, false);
+        if ((int)t.size() != m.tab_len)
+            return BRS_ERR_UNSUPPORTED;
+        all.insert(all.end(), t.begin(), t.end());
+    }
+    cudaError_t e = cudaMalloc(&P->mtab, all.size() * sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->mtab, all.data(), all.size() * sizeof(T), cudaMemcpyHostToDevice);
+    const size_t bytes = (size_t)c->cells * sizeof(T);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&P->mb, bytes);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&P->mu, bytes);
+    if (e != cudaSuccess)
+        return brs_cuda_status(e);
+    rc = mode_encode_map(m, &P->mm_b, P->mb);
+    if (rc == BRS_OK)
+        rc = mode_encode_map(m, &P->mm_u, P->mu);
+    if (rc != BRS_OK)
+        return rc;
+    P->mcfg = m;
+    P->modes = 1;
+    return BRS_OK;
+}
+
 }  // namespace
 
 int plane_setup(brs_ctx* c)
@@ -1019,6 +1249,8 @@ int plane_setup(brs_ctx* c)
             rc = ythomas_setup<float>(c);
         if (rc == BRS_OK && P->form == 1)
             rc = fused_setup(c);
+        if (rc == BRS_OK)
+            rc = modes_setup<float>(c);
         return rc;
     }
     if (p.dtype == BRS_F64)
@@ -1036,6 +1268,8 @@ int plane_setup(brs_ctx* c)
         rc = brs_cuda_status(cudaMalloc(&P->t2, bytes));
     if (rc == BRS_OK && P->form == 1)
         rc = p.dtype == BRS_F64 ? ythomas_setup<double>(c) : ythomas_setup<float>(c);
+    if (rc == BRS_OK)
+        rc = p.dtype == BRS_F64 ? modes_setup<double>(c) : modes_setup<float>(c);
     return rc;
 }
 
@@ -1045,7 +1279,7 @@ void plane_teardown(brs_ctx* c)
     if (!P)
         return;
     for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo,
-                    P->ytab, P->ym})
+                    P->ytab, P->ym, P->mb, P->mu, P->mtab})
         if (q)
             cudaFree(q);
     delete P;
@@ -1093,4 +1327,48 @@ int plane_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, c
         return rc;
     }
     return run(float{});
+}
+
+int plane_modes_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s,
+                      bool u_zero)
+{
+    PlaneState* P = ps(c);
+    if (!P || !P->modes || nsweeps < P->modes_min)
+        return BRS_ERR_UNSUPPORTED;
+    const bool gs = c->p.method == BRS_CHAOTIC_GS;
+    if (!gs && !c->scratch)
+        return BRS_ERR_UNSUPPORTED;
+    const ModeCfg& m = P->mcfg;
+    if (!gs && P->mm_v_ptr != c->scratch) {
+        // the Jacobi second vector is the context's scratch array (allocated after set-up)
+        int rc = mode_encode_map(m, &P->mm_v, c->scratch);
+        if (rc != BRS_OK)
+            return rc;
+        P->mm_v_ptr = c->scratch;
+    }
+    int rc = modes_forward(c, b, P->mb, s);
+    if (rc == BRS_OK)
+        rc = u_zero ? brs_cuda_status(cudaMemsetAsync(P->mu, 0, (size_t)c->cells * c->esize, s))
+                    : modes_forward(c, u, P->mu, s);
+    const double az = c->p.az, om = c->omega;
+    void* cur = P->mu;
+    void* nxt = c->scratch;
+    const CUtensorMap* mcur = &P->mm_u;
+    const CUtensorMap* mnxt = &P->mm_v;
+    for (int it = 0; it < nsweeps && rc == BRS_OK; ++it) {
+        if (gs) {
+            // even planes, then odd planes, in place
+            rc = mode_sweep_launch(m, &P->mm_u, &P->mm_b, P->mu, P->mtab, az, om, 0, c->dev_status, s);
+            if (rc == BRS_OK && c->p.nz > 1)
+                rc = mode_sweep_launch(m, &P->mm_u, &P->mm_b, P->mu, P->mtab, az, om, 1,
+                                       c->dev_status, s);
+        } else {
+            rc = mode_sweep_launch(m, mcur, &P->mm_b, nxt, P->mtab, az, om, -1, c->dev_status, s);
+            std::swap(cur, nxt);
+            std::swap(mcur, mnxt);
+        }
+    }
+    if (rc == BRS_OK)
+        rc = modes_inverse(c, cur, u, s);
+    return rc;
 }

@@ -350,11 +350,14 @@ def test_plane_512_single_mode_damping(brs, orc, dt, math):
 
 
 @pytest.mark.parametrize("dt,math", [("f32", "3xtf32"), ("f64", "simt")])
-def test_full_size_256_plane_three_sweeps_in_one_call(brs, orc, dt, math):
-    """256^3 plane Jacobi (a = (1, 1, 0.01)) in the benchmark's launch configuration:
-    3 sweeps in one call equal 3 one-sweep calls bit for bit, and sampled planes equal the
-    oracle after 3 sweeps (a plane after s sweeps depends only on planes within s of it)."""
+def test_full_size_256_plane_three_sweeps_in_one_call(brs, orc, dt, math, monkeypatch):
+    """256^3 plane Jacobi (a = (1, 1, 0.01)) in the per-sweep form (the x-sine form of
+    calls of several sweeps switched off; it is tested in test_gpu_plane_modes.py): 3 sweeps
+    in one call equal 3 one-sweep calls bit for bit, and sampled planes equal the oracle
+    after 3 sweeps (a plane after s sweeps depends only on planes within s of it)."""
     import torch
+
+    monkeypatch.setenv("BRSMOOTH_PLANE_MODES", "0")
 
     n, K = 256, 3
     a = (1.0, 1.0, 0.01)
