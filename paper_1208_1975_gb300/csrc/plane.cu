@@ -86,7 +86,9 @@ struct PlaneState {
     void* mb = nullptr;     // b^
     void* mu = nullptr;     // u^
     void* mtab = nullptr;   // [nx][mcfg.tab_len], context dtype
-    CUtensorMap mm_b, mm_u, mm_v;  // maps of mb, mu and the Jacobi second vector
+    void* mv = nullptr;     // second vector of Gauss-Seidel in one launch per sweep
+    int gs_fused = 1;       // GS: one launch per sweep (zebra order into mv), else two in place
+    CUtensorMap mm_b, mm_u, mm_v;  // maps of mb, mu and the second vector (mv or scratch)
     const void* mm_v_ptr = nullptr;
 };
 
@@ -1196,6 +1198,20 @@ int modes_setup(brs_ctx* c)
         rc = mode_encode_map(m, &P->mm_u, P->mu);
     if (rc != BRS_OK)
         return rc;
+    // Gauss-Seidel in one launch per sweep writes a second vector (measured at 256^3 FP32:
+    // two in-place colour launches per sweep, 16 bytes per cell, 57 us; one launch, 12 bytes
+    // per cell: see the x-sine row of the design notes); BRSMOOTH_MODE_GS_FUSED=0 keeps the
+    // two launches
+    const char* genv = std::getenv("BRSMOOTH_MODE_GS_FUSED");
+    P->gs_fused = !(genv && *genv && std::atoi(genv) == 0);
+    if (p.method == BRS_CHAOTIC_GS && P->gs_fused) {
+        rc = brs_cuda_status(cudaMalloc(&P->mv, bytes));
+        if (rc == BRS_OK)
+            rc = mode_encode_map(m, &P->mm_v, P->mv);
+        if (rc != BRS_OK)
+            return rc;
+        P->mm_v_ptr = P->mv;
+    }
     P->mcfg = m;
     P->modes = 1;
     return BRS_OK;
@@ -1279,7 +1295,7 @@ void plane_teardown(brs_ctx* c)
     if (!P)
         return;
     for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo,
-                    P->ytab, P->ym, P->mb, P->mu, P->mtab})
+                    P->ytab, P->ym, P->mb, P->mu, P->mtab, P->mv})
         if (q)
             cudaFree(q);
     delete P;
@@ -1339,6 +1355,7 @@ int plane_modes_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStrea
     if (!gs && !c->scratch)
         return BRS_ERR_UNSUPPORTED;
     const ModeCfg& m = P->mcfg;
+    const bool two_pass = gs && !P->gs_fused;
     if (!gs && P->mm_v_ptr != c->scratch) {
         // the Jacobi second vector is the context's scratch array (allocated after set-up)
         int rc = mode_encode_map(m, &P->mm_v, c->scratch);
@@ -1352,18 +1369,20 @@ int plane_modes_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStrea
                     : modes_forward(c, u, P->mu, s);
     const double az = c->p.az, om = c->omega;
     void* cur = P->mu;
-    void* nxt = c->scratch;
+    void* nxt = gs ? P->mv : c->scratch;
     const CUtensorMap* mcur = &P->mm_u;
     const CUtensorMap* mnxt = &P->mm_v;
     for (int it = 0; it < nsweeps && rc == BRS_OK; ++it) {
-        if (gs) {
+        if (two_pass) {
             // even planes, then odd planes, in place
             rc = mode_sweep_launch(m, &P->mm_u, &P->mm_b, P->mu, P->mtab, az, om, 0, c->dev_status, s);
             if (rc == BRS_OK && c->p.nz > 1)
                 rc = mode_sweep_launch(m, &P->mm_u, &P->mm_b, P->mu, P->mtab, az, om, 1,
                                        c->dev_status, s);
         } else {
-            rc = mode_sweep_launch(m, mcur, &P->mm_b, nxt, P->mtab, az, om, -1, c->dev_status, s);
+            // Jacobi, or both colours in one launch (zebra order), into the second vector
+            rc = mode_sweep_launch(m, mcur, &P->mm_b, nxt, P->mtab, az, om, gs ? 2 : -1,
+                                   c->dev_status, s);
             std::swap(cur, nxt);
             std::swap(mcur, mnxt);
         }

@@ -28,8 +28,9 @@ struct ModeCfg {
 int mode_config(int ny, int nm, int nz, int dtype, int device, ModeCfg* out);
 // Tensor map of an [nz][nm][ny] array with the kernel's box (bx, JT, 1).
 int mode_encode_map(const ModeCfg& m, CUtensorMap* map, const void* ptr);
-// One Jacobi sweep from the array of `mu` into `out` (colour < 0), or the in-place update of
-// the planes with k % 2 == colour.  tab: nm tables of tab_len entries (omega folded in).
+// One sweep from the array of `mu`: Jacobi into `out` (colour < 0), the in-place update of the
+// planes with k % 2 == colour (colour 0 or 1), or the whole two-colour sweep, even planes then
+// odd planes, into `out` (colour 2).  tab: nm tables of tab_len entries (omega folded in).
 int mode_sweep_launch(const ModeCfg& m, const CUtensorMap* mu, const CUtensorMap* mb, void* out,
                       const void* tab, double az, double omega, int colour, int* status,
                       cudaStream_t s);

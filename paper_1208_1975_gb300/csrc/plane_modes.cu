@@ -21,11 +21,20 @@
 // (u^_{k+1}, b^_k); u^_{k-1} and u^_k come from registers after the first step.  Boxes
 // outside the grid (plane -1, plane nz, rows past the last mode) read as zeros: the
 // homogeneous Dirichlet boundary in z.
-//  * COLOUR = false: Jacobi, from the input array into another one.
-//  * COLOUR = true: the planes with k % 2 == colour are updated in place; every value they
-//    read belongs to the other colour, which this launch does not write, so the result does
-//    not depend on the CTAs' order.  Two launches (colour 0, then 1) make one sweep in the
-//    order even planes, then odd planes.
+//  * MODE 0: Jacobi, from the input array into another one.
+//  * MODE 1: the planes with k % 2 == colour are updated in place; every value they read
+//    belongs to the other colour, which this launch does not write, so the result does not
+//    depend on the CTAs' order.  Two launches (colour 0, then 1) make one sweep in the order
+//    even planes, then odd planes.
+//  * MODE 2: the same sweep (even planes, then odd planes from the new even ones) in one
+//    launch, from the input array into another one.  A CTA marches over its planes
+//    [kb, ke) extended by one plane at each end; at an even plane j it forms the new even
+//    plane from the old odd neighbours and then the new odd plane j-1 from the new even
+//    planes j-2 and j (the odd plane's b^ + az u^_{j-2} is formed at step j-1 and kept in
+//    registers, in the place of the new even plane j-2).  The even planes kb-1 and ke just outside the
+//    segment are recomputed from the same old values their owners use, so every CTA sees
+//    the same new even planes and the result does not depend on the CTAs' order; 3 words
+//    per cell, as for Jacobi.
 #include <cstdlib>
 
 #include "line_impl.cuh"
@@ -39,12 +48,12 @@ struct ModeArgs {
     int JT, NS, pieces, bx;
     long long total;       // tiles * nz plane-steps
     double az, om1;        // z coefficient, 1 - omega
-    int colour;            // COLOUR kernels: the colour updated by this launch
+    int colour;            // MODE 1: the colour updated by this launch
     int tab_len;           // table entries per mode
     int* status;
 };
 
-template <typename T, int E, int G, bool COLOUR>
+template <typename T, int E, int G, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
     mode_tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_b,
                     T* __restrict__ out, const T* __restrict__ tab, ModeArgs a)
@@ -79,10 +88,20 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
         return reinterpret_cast<T*>(smem_raw + (uint32_t)slot * (uint32_t)slot_bytes);
     };
     auto inc = [&](int slot) { return slot + 1 == NS ? 0 : slot + 1; };
+    constexpr bool COLOUR = MODE == 1;
     // stage t of a segment starting at plane kb carries b^ rows (plane kb-2+t) if it is a
     // step's last stage and, for a colour launch, that step's plane is updated
     auto has_b = [&](int t, int kb) {
         return t >= 2 && (!COLOUR || ((kb - 2 + t) & 1) == a.colour);
+    };
+    // MODE 2 marches over each segment extended by one plane at both ends
+    auto next_seg = [&](brs::SegIter& it) {
+        const bool ok = it.next();
+        if (MODE == 2 && ok) {
+            it.kb -= 1;
+            it.n += 2;
+        }
+        return ok;
     };
 
     // producer state (thread 0); stage indices are per CTA
@@ -95,7 +114,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
             if (!p_has || p_next >= p_end) {
                 if (p_has)
                     p_seg_base = p_end;
-                p_has = pit.next();
+                p_has = next_seg(pit);
                 if (!p_has)
                     return;
                 p_end = p_seg_base + pit.n + 2;
@@ -131,7 +150,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
             if (!has || b_pre >= end) {
                 if (has)
                     seg_base = end;
-                has = it.next();
+                has = next_seg(it);
                 if (!has)
                     break;
                 end = seg_base + it.n + 2;
@@ -162,12 +181,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
     const uint32_t row_off = (uint32_t)(piece * box + g * bx + yo);
     const size_t plane = (size_t)a.nm * a.ny;
 
-    while (cit.next()) {
+    while (next_seg(cit)) {
         const int p = cit.jt * JT + g;
         const bool pin = p < a.nm;
         brs::LineTables<T, E, G> tb;  // this mode's factor tables (omega folded in)
         tb.load(tab + (size_t)(pin ? p : 0) * a.tab_len, lane);
-        T* outp = out + ((size_t)cit.kb * a.nm + p) * a.ny + y0;
+        // planes this CTA writes: the segment (without MODE 2's extension)
+        const int kw0 = MODE == 2 ? cit.kb + 1 : cit.kb;
+        const int kw1 = MODE == 2 ? cit.kb + cit.n - 1 : cit.kb + cit.n;
+        T* const out_row = out + (size_t)p * a.ny + y0;  // plane 0 of this lane's row
+        // MODE 2: after an even step the new even plane, after an odd step k the odd plane's
+        // right-hand side so far, b^_k + az (new u^_{k-1})
+        T carry[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            carry[q] = T(0);
         for (int s = 0; s < cit.n; ++s) {
             const int need = c_base + s + 3;
             bool ok = true;
@@ -183,49 +211,73 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
             ok = __all_sync(0xffffffffu, ok);  // the solve shuffles across the warp
             const int s1 = inc(cs_slot), s2 = inc(s1);
             const int k = cit.kb + s;
-            const bool act = !COLOUR || (k & 1) == a.colour;  // uniform over the CTA
+            // steps that solve: every plane (Jacobi), this launch's colour (MODE 1), the even
+            // planes (MODE 2); uniform over the CTA
+            const bool act = MODE == 0 || (MODE == 1 ? (k & 1) == a.colour : (k & 1) == 0);
             if (ok) {
                 const T* st2 = slot_ptr(s2);
+                T bb[E];
                 if (yin) {
                     if (s == 0) {
                         brs::ld_row<T, E>(um, slot_ptr(cs_slot) + row_off, lane);
                         brs::ld_row<T, E>(uc, slot_ptr(s1) + row_off, lane);
                     }
                     brs::ld_row<T, E>(up, st2 + row_off, lane);
+                    if (act || MODE == 2)
+                        brs::ld_row<T, E>(bb, st2 + u_elems + row_off, lane);
                 } else {
 #pragma unroll
                     for (int q = 0; q < E; ++q)
-                        um[q] = uc[q] = up[q] = T(0);
+                        um[q] = uc[q] = up[q] = bb[q] = T(0);
                 }
                 if (act) {
-                    if (yin) {
-                        T bb[E];
-                        brs::ld_row<T, E>(bb, st2 + u_elems + row_off, lane);
+                    T v[E];
+                    if (MODE == 2 && k >= a.nz) {
+                        // the even plane past the grid: the Dirichlet zeros
 #pragma unroll
                         for (int q = 0; q < E; ++q)
-                            r[q] = fma(az, um[q] + up[q], bb[q]);
+                            v[q] = T(0);
                     } else {
 #pragma unroll
                         for (int q = 0; q < E; ++q)
-                            r[q] = T(0);
+                            r[q] = fma(az, um[q] + up[q], bb[q]);
+                        brs::line_solve<T, E, G>(r, tb, lane);
+#pragma unroll
+                        for (int q = 0; q < E; ++q)
+                            v[q] = fma(tb.wp[q], r[q], om1 * uc[q]);
                     }
-                    brs::line_solve<T, E, G>(r, tb, lane);
-                    T v[E];
+                    if (yin && pin && k >= kw0 && k < kw1)
+                        brs::st_global_vec<T, E>(out_row + (size_t)k * plane, v);
+                    if (MODE == 2) {
+                        // the odd plane below, now that both its new even neighbours exist
+                        if (k - 1 >= kw0 && k - 1 < kw1) {
+#pragma unroll
+                            for (int q = 0; q < E; ++q)
+                                r[q] = fma(az, v[q], carry[q]);
+                            brs::line_solve<T, E, G>(r, tb, lane);
+#pragma unroll
+                            for (int q = 0; q < E; ++q)
+                                r[q] = fma(tb.wp[q], r[q], om1 * um[q]);
+                            if (yin && pin)
+                                brs::st_global_vec<T, E>(out_row + (size_t)(k - 1) * plane, r);
+                        }
+#pragma unroll
+                        for (int q = 0; q < E; ++q)
+                            carry[q] = v[q];
+                    }
+                } else if (MODE == 2) {
 #pragma unroll
                     for (int q = 0; q < E; ++q)
-                        v[q] = fma(tb.wp[q], r[q], om1 * uc[q]);
-                    if (yin && pin)
-                        brs::st_global_vec<T, E>(outp, v);
+                        carry[q] = fma(az, carry[q], bb[q]);
                 }
-                // the neighbours of the next steps are old values: Jacobi reads only old
-                // planes, and a colour launch reads only planes of the other colour
+                // the neighbours of the next steps are old values: Jacobi and MODE 2 read the
+                // input array, a colour launch reads only planes of the other colour
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     um[q] = uc[q];
                     uc[q] = up[q];
                 }
             }
-            outp += plane;
             cs_slot = s1;
             failed = __syncthreads_or(!ok) != 0;
             if (failed)
@@ -252,12 +304,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? 2 : 1)
     }
 }
 
-template <typename T, bool COLOUR>
+template <typename T, int MODE>
 const void* mode_kernel_for(int E, int G)
 {
 #define BRS_MODE_CASE(EE, GG)                                                  \
     if (E == EE && G == GG)                                                    \
-        return (const void*)mode_tma_kernel<T, EE, GG, COLOUR>;
+        return (const void*)mode_tma_kernel<T, EE, GG, MODE>;
     BRS_MODE_CASE(4, 4)
     BRS_MODE_CASE(4, 8)
     BRS_MODE_CASE(4, 16)
@@ -269,11 +321,13 @@ const void* mode_kernel_for(int E, int G)
     return nullptr;
 }
 
-const void* mode_kernel(int dtype, bool colour, int E, int G)
+const void* mode_kernel(int dtype, int mode, int E, int G)
 {
     if (dtype == BRS_F64)
-        return colour ? mode_kernel_for<double, true>(E, G) : mode_kernel_for<double, false>(E, G);
-    return colour ? mode_kernel_for<float, true>(E, G) : mode_kernel_for<float, false>(E, G);
+        return mode == 0 ? mode_kernel_for<double, 0>(E, G)
+             : mode == 1 ? mode_kernel_for<double, 1>(E, G) : mode_kernel_for<double, 2>(E, G);
+    return mode == 0 ? mode_kernel_for<float, 0>(E, G)
+         : mode == 1 ? mode_kernel_for<float, 1>(E, G) : mode_kernel_for<float, 2>(E, G);
 }
 
 int env_int(const char* name, int dflt)
@@ -320,8 +374,8 @@ int mode_config(int ny, int nm, int nz, int dtype, int device, ModeCfg* out)
     m.smem = (size_t)m.NS * slot_bytes(m, es) + (size_t)m.NS * 8;
     m.tab_len = scan_table_len(m.E, m.G, false);
     int occ = 1 << 30;
-    for (int colour = 0; colour < 2; ++colour) {
-        const void* k = mode_kernel(dtype, colour != 0, m.E, m.G);
+    for (int mode = 0; mode < 3; ++mode) {
+        const void* k = mode_kernel(dtype, mode, m.E, m.G);
         if (!k)
             return BRS_ERR_UNSUPPORTED;
         // the attribute belongs to the kernel, shared by every context: only ever raise it
@@ -377,7 +431,8 @@ int mode_sweep_launch(const ModeCfg& m, const CUtensorMap* mu, const CUtensorMap
                       const void* tab, double az, double omega, int colour, int* status,
                       cudaStream_t s)
 {
-    const void* k = mode_kernel(m.dtype, colour >= 0, m.E, m.G);
+    // colour: -1 Jacobi, 0 / 1 one colour in place, 2 both colours (zebra order) into out
+    const void* k = mode_kernel(m.dtype, colour < 0 ? 0 : colour == 2 ? 2 : 1, m.E, m.G);
     if (!k)
         return BRS_ERR_UNSUPPORTED;
     ModeArgs a{};
@@ -391,7 +446,7 @@ int mode_sweep_launch(const ModeCfg& m, const CUtensorMap* mu, const CUtensorMap
     a.total = m.total;
     a.az = az;
     a.om1 = 1.0 - omega;
-    a.colour = colour < 0 ? 0 : colour;
+    a.colour = colour == 0 || colour == 1 ? colour : 0;
     a.tab_len = m.tab_len;
     a.status = status;
     CUtensorMap tu = *mu, tbm = *mb;
