@@ -885,38 +885,46 @@ def _variant_level(brs, stream, barrier, which, dt="f32"):
 FP64_CALL_SWEEPS = 1000  # plain FP64 plane Jacobi at 512^3: sweeps per call (residual between)
 
 
-def _variant_defect512_fp64(brs, stream):
-    """512^3, a=(1,0.1,0.01): the plain FP64 plane-Jacobi solve to ||r||/||b|| <= 1e-10 run
-    in full (calls of FP64_CALL_SWEEPS sweeps, the FP64 residual after each), measured, and
-    its distance to the oracle's exact solution."""
+def _fp64_plane_solve(brs, b, a, rtol=1e-10, max_sweeps=40000):
+    """Plain FP64 plane Jacobi (omega = 0.8) from u = 0 in calls of FP64_CALL_SWEEPS sweeps,
+    the FP64 residual after each call, until ||r|| / ||b|| <= rtol: measured wall time."""
     import torch
 
-    from brs_inputs import rhs
-
-    a = (1.0, 0.1, 0.01)
-    n = 512
-    b_np = rhs((n, n, n))
-    b = torch.from_numpy(b_np).cuda()
+    n = b.shape[0]
     nb = float(torch.linalg.norm(b))
     with brs.Context(n, n, n, a, block="plane", method="jacobi", dtype="f64") as o64:
         u = torch.zeros_like(b)
-        o64.sweep(u, b, 2)
+        o64.sweep(u, b, 2)  # warm-up (set-up of the tables and maps)
         u.zero_()
         sweeps, r, hist = 0, 1.0, []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        while r > 1e-10 and sweeps < 40000:
+        while r > rtol and sweeps < max_sweeps:
             o64.sweep(u, b, FP64_CALL_SWEEPS)
             sweeps += FP64_CALL_SWEEPS
             r = o64.residual(u, b) / nb
             hist.append(r)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
-        assert o64.last_error() == 0
-    out = {"workload": "grid512_aniso plain FP64 plane Jacobi to 1e-10", "coeffs": a,
-           "sweeps": sweeps, "sweeps_per_call": FP64_CALL_SWEEPS, "rel_residual": r,
-           "s_measured": t, "residual_per_call": hist}
-    out["err_vs_oracle"], out["cpu_baseline"] = _defect_cpu_leg(b_np, a, u.cpu().numpy(), r)
+        if o64.last_error() != 0:
+            raise RuntimeError("device status raised during the FP64 solve")
+    return u, {"sweeps": sweeps, "sweeps_per_call": FP64_CALL_SWEEPS, "rel_residual": r,
+               "s_measured": t, "residual_per_call": hist}
+
+
+def _variant_defect512_fp64(brs, stream):
+    """512^3, a=(1,0.1,0.01): the plain FP64 plane-Jacobi solve to ||r||/||b|| <= 1e-10 alone,
+    and its distance to the oracle's exact solution."""
+    import torch
+
+    from brs_inputs import rhs
+
+    a = (1.0, 0.1, 0.01)
+    b_np = rhs((512, 512, 512))
+    u, rec = _fp64_plane_solve(brs, torch.from_numpy(b_np).cuda(), a)
+    out = {"workload": "grid512_aniso plain FP64 plane Jacobi to 1e-10", "coeffs": a, **rec}
+    out["err_vs_oracle"], out["cpu_baseline"] = _defect_cpu_leg(b_np, a, u.cpu().numpy(),
+                                                                rec["rel_residual"])
     return out
 
 
@@ -925,9 +933,9 @@ def _variant_defect(brs, stream):
     plane Jacobi.  The inner sweeps (block Jacobi, omega = 0.8, or two-colour block GS,
     omega = 1; split-TF32 or single-TF32 products) and their count per outer step m are
     chosen by timed full solves on 64^3
-    (where the plain FP64 solve is measured too); the 512^3 mixed solve then runs to
-    ||r||/||b|| <= 1e-10 and is compared with the oracle's exact solution; the plain FP64
-    solve at 512^3 (about 14 000 sweeps) is a projection from timed sweeps."""
+    (where the plain FP64 solve is measured too); at 512^3 the mixed solve and the plain FP64
+    plane-Jacobi solve (about 9000 sweeps) both run to ||r||/||b|| <= 1e-10 and are compared
+    with the oracle's exact solution."""
     import torch
 
     from brs_inputs import rhs
@@ -981,8 +989,8 @@ def _variant_defect(brs, stream):
                                 "mixed_rel_residual": per[best]["rel_residual"],
                                 "mixed_s": per[best]["s"], "fp64_sweeps": sweeps,
                                 "fp64_rel_residual": r, "fp64_s": t_f64}
-    # 512^3: the mixed solve run to ||r|| / ||b|| <= 1e-10 (measured), compared with the
-    # oracle's exact solution; plain FP64 plane Jacobi timed on a segment and projected
+    # 512^3: the mixed solve and the plain FP64 solve, each run to ||r|| / ||b|| <= 1e-10
+    # (measured) and compared with the oracle's exact solution
     n = 512
     b_np = rhs((n, n, n))
     b = torch.from_numpy(b_np).cuda()
@@ -1000,24 +1008,10 @@ def _variant_defect(brs, stream):
         t_mixed = time.perf_counter() - t0
         u_gpu = u.cpu().numpy()
         del u
-        # plain FP64 plane Jacobi in calls of K1 and K2 sweeps (the x-sine form): the
-        # difference gives the time per sweep, the rest the fixed cost of a call
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        u64 = torch.zeros_like(b)
-        o64.sweep(u64, b, 2)
-        t_call = {}
-        for k in (FP64_CALL_SWEEPS // 4, FP64_CALL_SWEEPS):
-            torch.cuda.synchronize()
-            e0.record(stream)
-            o64.sweep(u64, b, k)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_call[k] = e0.elapsed_time(e1)
-        k1, k2 = sorted(t_call)
-        ms_f64 = (t_call[k2] - t_call[k1]) / (k2 - k1)
-        ms_call_f64 = t_call[k2] - k2 * ms_f64
-        del u64
+    # the plain FP64 plane-Jacobi solve to the same residual, run in full
+    u64, f64 = _fp64_plane_solve(brs, b, a)
+    u64_np = u64.cpu().numpy()
+    del u64
     import math
 
     # contraction per sweep of plane Jacobi (omega=0.8) on the slowest mode: g_111
@@ -1026,31 +1020,28 @@ def _variant_defect(brs, stream):
     mu = a[0] * s1 + a[1] * s1 + 2 * a[2]
     g = 1 - 0.8 * lam / mu
     sweeps_needed = math.log(1e-10) / math.log(g)
-    t_f64_proj = (sweeps_needed * ms_f64 + math.ceil(sweeps_needed / FP64_CALL_SWEEPS)
-                  * ms_call_f64) / 1e3
     out["grid512"] = {"inner": best_meth, "inner_products": best_math, "inner_sweeps_m": best_m,
                       "mixed_s_measured": t_mixed,
                       "mixed_outer": done, "mixed_inner_sweeps": done * best_m,
                       "mixed_rel_residual": rel,
-                      "ms_per_fp64_plane_jacobi_sweep": ms_f64,
-                      "ms_fixed_per_fp64_call": ms_call_f64,
-                      "fp64_sweeps_per_call": FP64_CALL_SWEEPS,
-                      "fp64_sweeps_to_1e-10_projected": sweeps_needed,
-                      "fp64_s_projected": t_f64_proj,
-                      "speedup_mixed_vs_fp64_projected": t_f64_proj / t_mixed,
-                      "note": "mixed: measured wall time of the whole solve; FP64: measured "
-                              "ms per sweep x log(1e-10)/log(g_111) sweeps plus the measured "
-                              "fixed cost of each call of fp64_sweeps_per_call sweeps, a "
-                              "projection (bench.py --only defect512_fp64 runs that solve)"}
-    out["grid512"]["err_vs_oracle"], out["grid512"]["cpu_baseline"] = _defect_cpu_leg(
-        b_np, a, u_gpu, rel)
+                      "fp64_plane_jacobi": f64,
+                      "fp64_s_measured": f64["s_measured"],
+                      "speedup_mixed_vs_fp64_measured": f64["s_measured"] / t_mixed,
+                      "fp64_sweeps_slowest_mode_bound": sweeps_needed,
+                      "note": "both arms measured to ||r||/||b|| <= 1e-10 (wall time of the "
+                              "whole solve); the FP64 arm checks its residual after every "
+                              "call of fp64_plane_jacobi.sweeps_per_call sweeps"}
+    out["grid512"]["err_vs_oracle"], out["grid512"]["cpu_baseline"], fp64_err = _defect_cpu_leg(
+        b_np, a, u_gpu, rel, also=(u64_np, f64["rel_residual"]))
+    out["grid512"]["fp64_plane_jacobi"]["err_vs_oracle"] = fp64_err
     return out
 
 
-def _defect_cpu_leg(b_np, a, u_gpu, rel):
-    """512^3: the oracle's exact solution u* = A^-1 b (3D DST-I), timed, and the mixed
-    solve's distance to it.  With ||b - A u|| <= 1e-10 ||b|| the error obeys
-    ||u - u*|| <= kappa(A) 1e-10 ||u*|| in the 2-norm."""
+def _defect_cpu_leg(b_np, a, u_gpu, rel, also=None):
+    """512^3: the oracle's exact solution u* = A^-1 b (3D DST-I), timed, and the solve's
+    distance to it.  With ||b - A u|| <= rel ||b|| the error obeys
+    ||u - u*|| <= kappa(A) rel ||u*|| in the 2-norm.  also = (u, rel) of a second solve of
+    the same problem: its distance is returned as a third item."""
     import math
 
     import numpy as np
@@ -1060,18 +1051,23 @@ def _defect_cpu_leg(b_np, a, u_gpu, rel):
     t0 = time.perf_counter()
     ustar = orc.exact_solve(b_np, a)
     secs = time.perf_counter() - t0
-    d = u_gpu - ustar
     s1 = 2 - 2 * math.cos(math.pi / (n + 1))
     sn = 2 - 2 * math.cos(n * math.pi / (n + 1))
     kappa = sum(a) * sn / (sum(a) * s1)
-    return ({"metric": "distance of the final iterate to the oracle's exact DST solution",
-             "rel_max_norm": float(np.max(np.abs(d)) / np.max(np.abs(ustar))),
-             "rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(ustar)),
-             "bound_rel_2norm": kappa * rel, "kappa_A": kappa},
-            {"value": b_np.size / secs / 1e9, "unit": "Gcell/s (exact solve)",
-             "cores": orc.num_threads(), "kind": "oracle",
-             "sample": f"the oracle's exact solve of the 512^3 problem (3D DST-I, scipy), "
-                       f"{secs:.1f} s"})
+
+    def dist(u, r):
+        d = u - ustar
+        return {"metric": "distance of the final iterate to the oracle's exact DST solution",
+                "rel_max_norm": float(np.max(np.abs(d)) / np.max(np.abs(ustar))),
+                "rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(ustar)),
+                "bound_rel_2norm": kappa * r, "kappa_A": kappa}
+
+    out = (dist(u_gpu, rel),
+           {"value": b_np.size / secs / 1e9, "unit": "Gcell/s (exact solve)",
+            "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"the oracle's exact solve of the 512^3 problem (3D DST-I, scipy), "
+                      f"{secs:.1f} s"})
+    return out + (dist(*also),) if also is not None else out
 
 
 STUDY_BLOCKS = [("box", (1, 1, 1)), ("box", (2, 2, 2)), ("box", (4, 2, 2)), ("box", (4, 4, 2)),
