@@ -24,6 +24,9 @@ struct LineCfg {
     int grid = 0;       // persistent CTAs (TMA path)
     size_t smem = 0;    // dynamic shared memory bytes (TMA path)
     bool pdl = true;    // launch each sweep as a programmatic dependent of the previous one
+    bool pair = false;  // TMA path, FP32 lines of 385-512 cells: two warps per line
+                        // (64 lanes of 8 cells, tables in line_tab2); E, G stay the
+                        // one-warp layout of line_tab, which the other line kernels use
 };
 
 // Arguments of the line kernels (passed by value).
@@ -52,6 +55,7 @@ struct brs_ctx {
     void* scratch = nullptr;
     // line solve tables (device, context dtype)
     void* line_tab = nullptr;
+    void* line_tab2 = nullptr;  // two-warp layout (LineCfg::pair), FP32
     LineCfg lcfg;
     // residual reduction
     double* partials = nullptr;

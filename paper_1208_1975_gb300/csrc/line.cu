@@ -37,6 +37,13 @@ struct LineKernels {
     }
 };
 
+// The TMA kernel of two-warp lines (8 cells x 64 lanes), FP32.
+const void* pair_kernel(bool gs)
+{
+    return gs ? (const void*)brs::line_tma_kernel<float, 8, 64, true>
+              : (const void*)brs::line_tma_kernel<float, 8, 64, false>;
+}
+
 template <typename T>
 bool kernels_for(int E, int G, bool gs, const void** tma, const void** plain)
 {
@@ -79,22 +86,28 @@ int line_setup(brs_ctx* c)
     L.tma = (p.nx * es) % 16 == 0 && p.nx % L.E == 0 && p.nx % L.pieces == 0 &&
             (L.bx * es) % 16 == 0 && L.bx % L.E == 0 && L.bx <= 256 &&
             env_int("BRSMOOTH_LINE_PLAIN", 0) == 0;
-    const int groups_per_warp = 32 / L.G;
+    // FP32 lines of 385-512 cells on the TMA path: two warps per line at 8 cells per lane
+    // (the one-warp form holds 16 cells per lane at 221 registers, two 128-thread CTAs per
+    // SM); BRSMOOTH_LINE_PAIR=0 keeps the one-warp form
+    L.pair = L.tma && c->p.dtype == BRS_F32 && L.E == 16 && L.bx % kPairE == 0 &&
+             env_int("BRSMOOTH_LINE_PAIR", 1) != 0;
+    const int lanes = L.pair ? 64 : L.G;  // threads per line
+    const int groups_per_warp = lanes >= 32 ? 1 : 32 / lanes;
     // Wide lines (E >= 12 cells per lane, 168+ registers) fit one 256-thread CTA per SM; at
     // 4 lines per tile and a 4-stage ring three (nx = 384) or two (512) CTAs fit, which
     // measured 409 -> 471 Gcell/s at 384^3 and 321 -> 336 at 512^3 (same box, FP32 Jacobi).
-    const bool wide = c->p.dtype == BRS_F32 && L.E >= 12;
-    int jt_default = (c->p.dtype == BRS_F64 && L.E >= 8) ? 4 : wide ? 128 / L.G : 256 / L.G;
+    const bool wide = c->p.dtype == BRS_F32 && L.E >= 12 && !L.pair;
+    int jt_default = (c->p.dtype == BRS_F64 && L.E >= 8) ? 4 : wide ? 128 / L.G : 256 / lanes;
     int jt = env_int("BRSMOOTH_LINE_JT", jt_default);
     const int ny_round = ((p.ny + groups_per_warp - 1) / groups_per_warp) * groups_per_warp;
     if (jt > ny_round)
         jt = ny_round;
     jt = ((jt + groups_per_warp - 1) / groups_per_warp) * groups_per_warp;
-    if (jt * L.G > 256)
-        jt = 256 / L.G;
+    if (jt * lanes > 256)
+        jt = 256 / lanes;
     L.JT = jt;
     // ring depth: stages s..s+2 are being read, the rest are loads in flight
-    L.NS = env_int("BRSMOOTH_LINE_NS", (p.dtype == BRS_F64 || wide) ? 4 : 6);
+    L.NS = env_int("BRSMOOTH_LINE_NS", (p.dtype == BRS_F64 || wide || L.pair) ? 4 : 6);
     if (L.NS < 3)
         L.NS = 3;
     while (L.NS > 3 && (size_t)L.NS * (tma_slot_bytes(L, es) + 8) > 227u * 1024u)
@@ -106,8 +119,12 @@ int line_setup(brs_ctx* c)
                                    : kernels_for<float>(L.E, L.G, gs, &ktma, &kplain);
     if (!ok)
         return BRS_ERR_UNSUPPORTED;
+    if (L.pair)
+        ktma = pair_kernel(gs);
     if (L.tma) {
-        L.smem = (size_t)L.NS * tma_slot_bytes(L, es) + (size_t)L.NS * 8;
+        // ring, its barriers, and (two-warp lines) two exchange slots per line
+        L.smem = (size_t)L.NS * tma_slot_bytes(L, es) + (size_t)L.NS * 8 +
+                 (L.pair ? (size_t)2 * L.JT * es : 0);
         // the attribute belongs to the kernel, shared by every context: only ever raise it
         cudaFuncAttributes fa{};
         cudaError_t e = cudaFuncGetAttributes(&fa, ktma);
@@ -117,7 +134,7 @@ int line_setup(brs_ctx* c)
         if (e != cudaSuccess)
             return brs_cuda_status(e);
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ktma, L.JT * L.G, L.smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ktma, L.JT * lanes, L.smem);
         if (e != cudaSuccess)
             return brs_cuda_status(e);
         if (occ < 1)
@@ -149,6 +166,15 @@ int line_setup(brs_ctx* c)
         e = cudaMalloc(&c->line_tab, bytes);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->line_tab, tab.data(), bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && L.pair) {
+            auto t2 = scan_pair_tables<float>(p.nx, p.ax, 2.0 * (p.ax + p.ay + p.az), c->omega);
+            if (t2.empty())
+                return BRS_ERR_UNSUPPORTED;
+            e = cudaMalloc(&c->line_tab2, t2.size() * sizeof(float));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->line_tab2, t2.data(), t2.size() * sizeof(float),
+                               cudaMemcpyHostToDevice);
+        }
     }
     return brs_cuda_status(e);
 }
@@ -157,7 +183,10 @@ void line_teardown(brs_ctx* c)
 {
     if (c->line_tab)
         cudaFree(c->line_tab);
+    if (c->line_tab2)
+        cudaFree(c->line_tab2);
     c->line_tab = nullptr;
+    c->line_tab2 = nullptr;
 }
 
 int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cudaStream_t s)
@@ -170,6 +199,8 @@ int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cu
         kernels_for<double>(L.E, L.G, gs, &ktma, &kplain);
     else
         kernels_for<float>(L.E, L.G, gs, &ktma, &kplain);
+    if (L.pair)
+        ktma = pair_kernel(gs);
     LineArgs a{};
     a.nx = p.nx;
     a.ny = p.ny;
@@ -195,11 +226,11 @@ int line_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, cu
             return rc;
         CUtensorMap tu = *mu, tbm = *mb;
         void* out = uout;
-        const void* tab = c->line_tab;
+        const void* tab = L.pair ? c->line_tab2 : c->line_tab;
         void* args[] = {&tu, &tbm, &out, (void*)&tab, &a};
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(L.grid);
-        cfg.blockDim = dim3(L.JT * L.G);
+        cfg.blockDim = dim3(L.JT * (L.pair ? 64 : L.G));
         cfg.dynamicSmemBytes = L.smem;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];

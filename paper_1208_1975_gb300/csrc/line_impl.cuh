@@ -116,6 +116,124 @@ __device__ __forceinline__ void line_solve(T (&r)[E], const LineTables<T, E, G>&
     }
 }
 
+// Two-warp form for lines of up to 512 cells (tables of scan_pair_fill): 64 lanes of 8
+// cells, the line's first 256 cells in lanes 0-31 of one warp and the rest in lanes 32-63
+// of the next.  Each warp scans its half as line_solve does; the forward carry of the lower
+// half's last cell and the backward carry of the upper half's first cell cross through
+// shared memory (xch, two values per line) at a barrier of the line's 64 threads.  Every
+// other lane's carry is its half-local scan value plus the crossing carry times the product
+// of the multipliers in between (pf, pb): 5 scan steps per direction instead of the 4 cells
+// x 32 lanes form's 16-cell chunks, at 8 cells per lane.
+template <typename T>
+struct PairTables {
+    static constexpr int E = 8, NP = 512, L = 64, LG = 5;
+    T c[E], e[E], wp[E];
+    T af[LG], ab[LG];
+    T pf, pb;
+
+    __device__ __forceinline__ void load(const T* __restrict__ tab, int lane64)
+    {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            c[q] = tab[lane64 * E + q];
+            e[q] = tab[NP + lane64 * E + q];
+            wp[q] = tab[2 * NP + lane64 * E + q];
+        }
+#pragma unroll
+        for (int t = 0; t < LG; ++t) {
+            af[t] = tab[3 * NP + t * L + lane64];
+            ab[t] = tab[3 * NP + LG * L + t * L + lane64];
+        }
+        pf = tab[3 * NP + 2 * LG * L + lane64];
+        pb = tab[3 * NP + 2 * LG * L + L + lane64];
+    }
+};
+
+// the factor tables a line group of G lanes with E cells each reads
+template <typename T, int E, int G>
+struct SolveTables {
+    using type = LineTables<T, E, G>;
+};
+template <typename T>
+struct SolveTables<T, 8, 64> {
+    using type = PairTables<T>;
+};
+
+// Named barrier `id` (1-4: the lines of a two-warp tile) of 64 threads; the immediate ids
+// let ptxas reserve only the barriers in use.
+__device__ __forceinline__ void bar_sync_64(int id)
+{
+    switch (id) {
+    case 1: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+    case 3: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+    }
+}
+
+// Solve M_line x = rhs for one line held by the 64 lanes of two warps (lane64 = 0..63);
+// on return r[q] holds w_i as for line_solve.  bar: the named barrier of this line's
+// 64 threads (1..4); xch: this line's two exchange slots.
+template <typename T>
+__device__ __forceinline__ void line_solve_pair(T (&r)[8], const PairTables<T>& tb, int lane64,
+                                                T* xch, int bar)
+{
+    constexpr int E = 8, LG = 5;
+    const int half = lane64 >> 5, lane = lane64 & 31;
+    // forward: half-local inclusive scan of the chunk summaries
+    T z = T(0);
+#pragma unroll
+    for (int q = 0; q < E; ++q)
+        z = fma(tb.c[q], z, r[q]);
+    T B = z;
+#pragma unroll
+    for (int t = 0; t < LG; ++t) {
+        const int d = 1 << t;
+        const T Bp = __shfl_up_sync(0xffffffffu, B, d);
+        if (lane >= d)
+            B = fma(tb.af[t], Bp, B);
+    }
+    if (half == 0 && lane == 31)
+        xch[0] = B;
+    bar_sync_64(bar);
+    const T C = half ? xch[0] : T(0);  // z of the lower half's last cell
+    T carry = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0)
+        carry = T(0);
+    z = fma(tb.pf, C, carry);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        z = fma(tb.c[q], z, r[q]);
+        r[q] = z;
+    }
+    // backward, mirrored
+    T w = T(0);
+#pragma unroll
+    for (int q = E - 1; q >= 0; --q)
+        w = fma(tb.e[q], w, r[q]);
+    B = w;
+#pragma unroll
+    for (int t = 0; t < LG; ++t) {
+        const int d = 1 << t;
+        const T Bn = __shfl_down_sync(0xffffffffu, B, d);
+        if (lane + d < 32)
+            B = fma(tb.ab[t], Bn, B);
+    }
+    if (half == 1 && lane == 0)
+        xch[1] = B;
+    bar_sync_64(bar);
+    const T D = half ? T(0) : xch[1];  // w of the upper half's first cell
+    carry = __shfl_down_sync(0xffffffffu, B, 1);
+    if (lane == 31)
+        carry = T(0);
+    w = fma(tb.pb, D, carry);
+#pragma unroll
+    for (int q = E - 1; q >= 0; --q) {
+        w = fma(tb.e[q], w, r[q]);
+        r[q] = w;
+    }
+}
+
 // 16-byte vector with the element type T (loads and stores through it keep T arrays in
 // registers; a vector of another element type would force them into local memory).
 template <typename T>
@@ -245,8 +363,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
     const int piece = xin ? x0 / bx : 0;
     const int xo = x0 - piece * bx;
 
-    LineTables<T, E, G> tb;
+    typename SolveTables<T, E, G>::type tb;
     tb.load(tab, lane);
+    // two-warp lines: this line's exchange slots after the ring barriers, its named barrier
+    T* xch = reinterpret_cast<T*>(full + NS) + 2 * g;
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s)
@@ -368,8 +488,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
                         w_phase ^= 1u;
                 }
             }
-            // the solve shuffles across the warp: skip it warp-uniformly on a timeout
-            ok = __all_sync(0xffffffffu, ok);
+            // the solve shuffles across the warp: skip it warp-uniformly on a timeout (and,
+            // for two-warp lines, whose halves meet at a barrier, CTA-uniformly)
+            if constexpr (G == 64)
+                ok = __syncthreads_and(ok) != 0;
+            else
+                ok = __all_sync(0xffffffffu, ok);
             const int s1 = inc(cs_slot), s2 = inc(s1);
             if (ok) {
                 const T* st1 = slot_ptr(s1);
@@ -394,7 +518,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && E <= 8) ? BRS_LINE_MIN
                         um[q] = uc[q] = up[q] = T(0);
                     }
                 }
-                line_solve<T, E, G>(r, tb, lane);
+                if constexpr (G == 64)
+                    line_solve_pair<T>(r, tb, lane, xch, 1 + g);
+                else
+                    line_solve<T, E, G>(r, tb, lane);
                 T v[E];
 #pragma unroll
                 for (int q = 0; q < E; ++q)

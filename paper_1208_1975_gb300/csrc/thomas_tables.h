@@ -98,6 +98,65 @@ BRS_HD int scan_thomas_fill(T* tab, int cap, int n, double off, double diag, dou
     return len;
 }
 
+// Tables of the two-warp line solve (line_solve_pair in line_impl.cuh) for lines of up to
+// 512 cells: 64 lanes of kPairE = 8 cells, lanes 0-31 (cells 0-255) in one warp and lanes
+// 32-63 (cells 256-511) in the other.  Each warp scans its half on its own; the halves'
+// carries cross through shared memory.  Layout (NP = 512):
+//   [0, NP)                  c_i   (as for scan_thomas_fill)
+//   [NP, 2NP)                e_i
+//   [2NP, 3NP)               omega p_i
+//   [3NP, 3NP+5*64)          forward scan multipliers within a half, step t at [t*64 + lane]
+//   [3NP+5*64, 3NP+10*64)    backward scan multipliers within a half
+//   [3NP+640, 3NP+704)       pf: product of the half's lane products before the lane
+//   [3NP+704, 3NP+768)       pb: product of the half's lane products after the lane
+constexpr int kPairE = 8;
+constexpr int kPairLen = 3 * 512 + 768;
+
+template <typename T>
+BRS_HD int scan_pair_fill(T* tab, int cap, int n, double off, double diag, double omega)
+{
+    constexpr int NP = 512, L = 64, H = 32, LG = 5;
+    if (n > NP || cap < kPairLen)
+        return -1;
+    double Af[L], Ab[L];
+    for (int l = 0; l < L; ++l)
+        Af[l] = Ab[l] = 1.0;
+    double pprev = 0.0, pcur = 1.0 / diag;
+    for (int i = 0; i < NP; ++i) {
+        const double pi = i < n ? pcur : 0.0;
+        const double pnext = i + 1 < n ? 1.0 / (diag - off * off * pi) : 0.0;
+        const double ci = (i >= 1 && i < n) ? off * pprev : 0.0;
+        const double ei = i + 1 < n ? off * pnext : 0.0;
+        tab[i] = (T)ci;
+        tab[NP + i] = (T)ei;
+        tab[2 * NP + i] = (T)(omega * pi);
+        Af[i / kPairE] *= ci;
+        Ab[i / kPairE] *= ei;
+        pprev = pi;
+        pcur = pnext;
+    }
+    for (int m = 0; m < L; ++m) {
+        const int h0 = (m / H) * H, h1 = h0 + H - 1;  // the lanes of m's half
+        for (int t = 0; t < LG; ++t) {
+            double f = 1.0, b = 1.0;
+            for (int q = m - (1 << t) + 1 < h0 ? h0 : m - (1 << t) + 1; q <= m; ++q)
+                f *= Af[q];
+            for (int q = m; q <= h1 && q < m + (1 << t); ++q)
+                b *= Ab[q];
+            tab[3 * NP + t * L + m] = (T)f;
+            tab[3 * NP + LG * L + t * L + m] = (T)b;
+        }
+        double pf = 1.0, pb = 1.0;
+        for (int q = h0; q < m; ++q)
+            pf *= Af[q];
+        for (int q = m + 1; q <= h1; ++q)
+            pb *= Ab[q];
+        tab[3 * NP + 2 * LG * L + m] = (T)pf;
+        tab[3 * NP + 2 * LG * L + L + m] = (T)pb;
+    }
+    return kPairLen;
+}
+
 // Host convenience: the tables as a vector (empty if the layout is too large).
 template <typename T>
 std::vector<T> scan_thomas_tables(int n, double off, double diag, double omega, int E, int G,
@@ -105,6 +164,15 @@ std::vector<T> scan_thomas_tables(int n, double off, double diag, double omega, 
 {
     std::vector<T> tab(scan_table_len(E, G, with_p));
     if (scan_thomas_fill<T>(tab.data(), (int)tab.size(), n, off, diag, omega, E, G, with_p) < 0)
+        tab.clear();
+    return tab;
+}
+
+template <typename T>
+std::vector<T> scan_pair_tables(int n, double off, double diag, double omega)
+{
+    std::vector<T> tab(kPairLen);
+    if (scan_pair_fill<T>(tab.data(), (int)tab.size(), n, off, diag, omega) < 0)
         tab.clear();
     return tab;
 }

@@ -366,3 +366,57 @@ def test_full_size_256_five_sweeps_in_one_call(brs, orc, dt):
     lines = [(0, 0), (n - 1, n - 1), (3, n - 2), (128, 129)]
     lines += [tuple(x) for x in rng.integers(0, n, size=(12, 2))]
     assert _sampled_lines_after(orc, u, b, a, got, lines, K) <= TOL[dt]
+
+
+# ----------------------------------------------------------------- two-warp lines (385-512)
+
+PAIR_SHAPES = [(416, 9, 5), (480, 6, 7), (512, 13, 8), (448, 1, 3)]
+
+
+@pytest.mark.parametrize("shape", PAIR_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("a", COEFFS + [(2.0, 0.001, 0.001)],
+                         ids=["iso", "aniso_z", "aniso_yz", "strong_x"])
+def test_two_warp_lines_jacobi_parity(brs, orc, shape, a):
+    """FP32 lines of 416-512 cells (two warps per line, the halves' carries crossing through
+    shared memory): one sweep and a call of three sweeps against the oracle, and within the
+    tolerance of the one-warp form (BRSMOOTH_LINE_PAIR=0)."""
+    nx, ny, nz = shape
+    u = rounded(initial_guess((nz, ny, nx)), "f32")
+    b = rounded(rhs((nz, ny, nx)), "f32")
+    ref1 = orc.sweep(u, b, a, block="line", method="jacobi", omega=0.8)
+    ref3 = orc.sweep(orc.sweep(ref1, b, a, block="line", omega=0.8), b, a, block="line",
+                     omega=0.8)
+    assert rel_max_err(gpu_sweep(brs, u, b, a, dt="f32"), ref1) <= TOL["f32"]
+    assert rel_max_err(gpu_sweep(brs, u, b, a, dt="f32", nsweeps=3), ref3) <= TOL["f32"]
+
+
+def test_two_warp_lines_equal_one_warp_form(brs, orc, monkeypatch):
+    nx, ny, nz = 512, 11, 6
+    a = (1.0, 0.1, 0.01)
+    u = rounded(initial_guess((nz, ny, nx)), "f32")
+    b = rounded(rhs((nz, ny, nx)), "f32")
+    pair = gpu_sweep(brs, u, b, a, dt="f32", nsweeps=2)
+    monkeypatch.setenv("BRSMOOTH_LINE_PAIR", "0")
+    one = gpu_sweep(brs, u, b, a, dt="f32", nsweeps=2)
+    assert rel_max_err(pair, one) <= 2 * TOL["f32"]
+
+
+def test_two_warp_lines_chaotic_gs_perron_and_convergence(brs, orc):
+    """Chaotic GS on 512-cell lines: the Perron bound on the slowest sine mode (b = 0) and
+    convergence to A^{-1} b."""
+    nx, ny, nz = 512, 6, 5
+    a = (1.0, 1.0, 1.0)
+    m = sine_mode(nx, ny, nz, 1, 1, 1)
+    g = orc.mode_factor(nx, ny, nz, a, "line", 1.0)[0, 0, 0]
+    with brs.Context(nx, ny, nz, a, block="line", method="gs", dtype="f32") as ctx:
+        ut, bt = to_dev(m, "f32"), to_dev(np.zeros_like(m), "f32")
+        mr = to_np(ut)
+        for k in range(1, 6):
+            ctx.sweep(ut, bt, 1)
+            got = to_np(ut)
+            assert np.all(got >= -1e-6 * k) and np.all(got <= g ** k * mr + 2e-6 * (1 + k))
+        b = rounded(rhs((nz, ny, nx)), "f32")
+        ut, bt = to_dev(np.zeros_like(b), "f32"), to_dev(b, "f32")
+        ctx.sweep(ut, bt, 300)
+        assert ctx.last_error() == 0
+        assert rel_max_err(to_np(ut), orc.exact_solve(b, a)) <= 1e-4
