@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 # (nx, ny, nz): y rows that TMA can stage (ny * element size a multiple of 16 bytes, whole
 # lane chunks), several tiles of mode rows, odd and even plane counts
 SHAPES = [(32, 32, 7), (64, 96, 6), (24, 40, 5), (33, 24, 4), (128, 64, 9), (16, 16, 3),
-          (96, 128, 2)]
+          (96, 128, 2), (32, 512, 4), (64, 416, 3)]  # the last two: 16 cells per lane, two TMA pieces
 COEFFS = [(1.0, 1.0, 1.0), (1.0, 1.0, 0.01), (1.0, 0.1, 0.01)]
 MATHS = [("f64", "simt"), ("f32", "3xtf32"), ("f32", "tf32"), ("f32", "simt")]
 
@@ -69,8 +69,8 @@ def test_modes_jacobi_parity(brs, orc, dt, math, shape, a):
 
 
 @pytest.mark.parametrize("dt,math", MATHS, ids=lambda v: v)
-@pytest.mark.parametrize("shape", [(32, 32, 7), (64, 96, 6), (33, 24, 4), (16, 16, 1)],
-                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", [(32, 32, 7), (64, 96, 6), (33, 24, 4), (16, 16, 1),
+                                   (32, 512, 5)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("omega", [1.0, 0.7])
 def test_modes_gs_equals_oracle_zebra(brs, orc, dt, math, shape, omega):
     """Gauss-Seidel in the x-sine basis: even planes, then odd planes from the new even ones,
