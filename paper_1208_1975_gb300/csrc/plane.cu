@@ -90,6 +90,15 @@ struct PlaneState {
     int gs_fused = 1;       // GS: one launch per sweep (zebra order into mv), else two in place
     CUtensorMap mm_b, mm_u, mm_v;  // maps of mb, mu and the second vector (mv or scratch)
     const void* mm_v_ptr = nullptr;
+    // FP64: the twisted-elimination form of the mode-line sweep, arrays [k][y][p]
+    // (plane_modes_f64.cu); b^ is stored scaled by omega pv (tscale) by the forward product
+    int twist = 0;
+    void* tfm = nullptr;     // [Rc][nx]: ay p_s of mode p
+    void* tfb = nullptr;     // [Rc][nx]: omega p_s az
+    void* tgm = nullptr;     // [nx]: ay g_m (twist cell)
+    void* tgb = nullptr;     // [nx]: omega g_m az
+    void* tscale = nullptr;  // [ny][nx]: omega pv_y
+    void* mz = nullptr;      // Gauss-Seidel: the elimination's values
 };
 
 // Map of a grid for the gather form, encoded on first use of its address.
@@ -1149,6 +1158,101 @@ int fused_setup(brs_ctx* c)
     return BRS_OK;
 }
 
+// FP64 x-sine form with the twisted elimination: per-mode pivots of tridiag(-ay, d_p, -ay),
+// d_p = ax s_p + 2 ay + 2 az (twist_pivots, FP64), as the tables the kernel reads per step,
+// and the mode arrays; any ny.
+int twist_setup(brs_ctx* c)
+{
+    PlaneState* P = ps(c);
+    const brs_params& p = c->p;
+    const int nx = p.nx, ny = p.ny, m = (ny - 1) / 2, Rc = ny - 1 - m;
+    const double om = c->omega;
+    std::vector<double> fm((size_t)(Rc > 0 ? Rc : 1) * nx, 0.0), fb(fm.size(), 0.0);
+    std::vector<double> gm(nx), gb(nx), sc((size_t)ny * nx);
+    for (int q = 0; q < nx; ++q) {
+        const double sp = 2.0 - 2.0 * std::cos(M_PI * (q + 1) / (nx + 1));
+        const std::vector<double> pv = twist_pivots(ny, p.ay, p.ax * sp + 2.0 * p.ay + 2.0 * p.az);
+        for (int s = 0; s < Rc; ++s) {
+            const double ps_ = pv[ny - 1 - s];  // p_s: the right side's pivot at step s
+            fm[(size_t)s * nx + q] = p.ay * ps_;
+            fb[(size_t)s * nx + q] = om * ps_ * p.az;
+        }
+        gm[q] = p.ay * pv[m];
+        gb[q] = om * pv[m] * p.az;
+        for (int y = 0; y < ny; ++y)
+            sc[(size_t)y * nx + q] = om * pv[y];
+    }
+    auto up = [&](void** dst, const std::vector<double>& v) {
+        cudaError_t e = cudaMalloc(dst, v.size() * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+        return brs_cuda_status(e);
+    };
+    int rc = up(&P->tfm, fm);
+    if (rc == BRS_OK)
+        rc = up(&P->tfb, fb);
+    if (rc == BRS_OK)
+        rc = up(&P->tgm, gm);
+    if (rc == BRS_OK)
+        rc = up(&P->tgb, gb);
+    if (rc == BRS_OK)
+        rc = up(&P->tscale, sc);
+    const size_t bytes = (size_t)c->cells * sizeof(double);
+    for (void** q : {&P->mb, &P->mu})
+        if (rc == BRS_OK)
+            rc = brs_cuda_status(cudaMalloc(q, bytes));
+    if (rc == BRS_OK && p.method == BRS_CHAOTIC_GS)
+        rc = brs_cuda_status(cudaMalloc(&P->mz, bytes));
+    if (rc != BRS_OK)
+        return rc;
+    P->twist = 1;
+    P->modes = 1;
+    return BRS_OK;
+}
+
+// The twisted FP64 form of a call: b^' = (b Sx^T) .* omega pv and u^ = u Sx^T ([k][y][p]), the
+// sweeps, u = u^ Sx^T (Sx is symmetric, so one product form serves both directions).
+int twist_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s, bool u_zero)
+{
+    PlaneState* P = ps(c);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const long long plane = (long long)nx * ny;
+    const double* Sx = static_cast<const double*>(P->sx);
+    GemmArgs g{};
+    g.M = ny; g.N = nx; g.K = nx; g.strideA = plane; g.strideB = 0; g.strideC = plane;
+    GemmArgs gs_ = g;
+    gs_.scale = P->tscale;
+    double* mb = static_cast<double*>(P->mb);
+    double* mu = static_cast<double*>(P->mu);
+    cudaError_t e = launch_gemm<double, EPI_SCALE>(static_cast<const double*>(b), Sx, mb, gs_, nz, s);
+    if (e == cudaSuccess)
+        e = u_zero ? cudaMemsetAsync(mu, 0, (size_t)c->cells * sizeof(double), s)
+                   : launch_gemm<double, EPI_STORE>(static_cast<const double*>(u), Sx, mu, g, nz, s);
+    int rc = brs_cuda_status(e);
+    const double* fm = static_cast<const double*>(P->tfm);
+    const double* fb = static_cast<const double*>(P->tfb);
+    const double* gm = static_cast<const double*>(P->tgm);
+    const double* gb = static_cast<const double*>(P->tgb);
+    double* cur = mu;
+    if (c->p.method == BRS_CHAOTIC_GS) {
+        // even planes, then odd planes, in place; the elimination's values in mz
+        double* zs = static_cast<double*>(P->mz);
+        for (int it = 0; it < nsweeps && rc == BRS_OK; ++it)
+            for (int col = 0; col < 2 && rc == BRS_OK; ++col)
+                rc = mode_twist_launch(cur, cur, zs, mb, fm, fb, gm, gb, nx, ny, nz, c->omega,
+                                       col, s);
+    } else {
+        double* nxt = static_cast<double*>(c->scratch);
+        for (int it = 0; it < nsweeps && rc == BRS_OK; ++it) {
+            rc = mode_twist_launch(cur, nxt, nxt, mb, fm, fb, gm, gb, nx, ny, nz, c->omega, -1, s);
+            std::swap(cur, nxt);
+        }
+    }
+    if (rc == BRS_OK)
+        rc = brs_cuda_status(launch_gemm<double, EPI_STORE>(cur, Sx, static_cast<double*>(u), g, nz, s));
+    return rc;
+}
+
 // x-sine form: per-mode scan-Thomas tables of tridiag(-ay, ax s_p + 2 ay + 2 az, -ay) along y
 // with the context's omega folded in (factored once in FP64), the mode arrays and their
 // maps.  Leaves the form off (per-sweep form only) when BRSMOOTH_PLANE_MODES=0 or the y rows
@@ -1167,6 +1271,9 @@ int modes_setup(brs_ctx* c)
     const char* menv = std::getenv("BRSMOOTH_PLANE_MODES_MIN");
     const int dflt = (P->math == BRS_PLANE_TF32 || P->math == BRS_PLANE_3XTF32) ? 3 : 2;
     P->modes_min = (menv && *menv && std::atoi(menv) >= 1) ? std::atoi(menv) : dflt;
+    const char* tenv = std::getenv("BRSMOOTH_MODE_TWIST");
+    if (sizeof(T) == 8 && !(tenv && *tenv && std::atoi(tenv) == 0))
+        return twist_setup(c);
     ModeCfg m;
     int rc = mode_config(p.ny, p.nx, p.nz, p.dtype, c->device, &m);
     if (rc == BRS_ERR_UNSUPPORTED)
@@ -1295,7 +1402,8 @@ void plane_teardown(brs_ctx* c)
     if (!P)
         return;
     for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo,
-                    P->ytab, P->ym, P->mb, P->mu, P->mtab, P->mv})
+                    P->ytab, P->ym, P->mb, P->mu, P->mtab, P->mv, P->tfm, P->tfb, P->tgm,
+                    P->tgb, P->tscale, P->mz})
         if (q)
             cudaFree(q);
     delete P;
@@ -1354,6 +1462,8 @@ int plane_modes_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStrea
     const bool gs = c->p.method == BRS_CHAOTIC_GS;
     if (!gs && !c->scratch)
         return BRS_ERR_UNSUPPORTED;
+    if (P->twist)
+        return twist_sweep(c, u, b, nsweeps, s, u_zero);
     const ModeCfg& m = P->mcfg;
     const bool two_pass = gs && !P->gs_fused;
     if (!gs && P->mm_v_ptr != c->scratch) {

@@ -11,6 +11,14 @@ int plane_sweep_launch(brs_ctx* c, const void* uin, void* uout, const void* b, c
 int plane_modes_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s,
                       bool u_zero = false);
 
+// FP64 mode-line sweep with the twisted elimination (plane_modes_f64.cu): arrays [k][y][p];
+// one Jacobi sweep from uin into out (z in out), or (colour 0 / 1) the in-place update of
+// the planes k % 2 == colour (z in the scratch array zs).  Tables per mode p: fm[s][p],
+// fb[s][p] (s < ny - 1 - (ny-1)/2), gm[p], gb[p]; bs holds b^ scaled by omega pv.
+int mode_twist_launch(const double* uin, double* out, double* zs, const double* bs,
+                      const double* fm, const double* fb, const double* gm, const double* gb,
+                      int nx, int ny, int nz, double omega, int colour, cudaStream_t s);
+
 // Mode-line sweeps of the x-sine form (plane_modes.cu): lines of ny cells along y, one row per
 // x-mode (nm rows), nz planes, array layout [k][p][y].
 struct ModeCfg {

@@ -157,6 +157,27 @@ BRS_HD int scan_pair_fill(T* tab, int cap, int n, double off, double diag, doubl
     return kPairLen;
 }
 
+// Pivots of the elimination from both ends (twisted factorisation) of tridiag(-off, diag,
+// -off) of size n, FP64: pv_i = p_i left of the twist cell m = (n-1)/2 (p_0 = 1/diag,
+// p_i = 1/(diag - off^2 p_{i-1})), g_m = 1/(diag - off^2 (p_{m-1} + q_{m+1})) at it, and
+// q_i = p_{n-1-i} right of it (the same recurrence from the other end).
+inline std::vector<double> twist_pivots(int n, double off, double diag)
+{
+    const int m = (n - 1) / 2;
+    std::vector<double> pv(n, 0.0);
+    double p = 0.0;
+    for (int i = 0; i < n - 1 - m; ++i) {  // p_0 .. p_{n-2-m}: both sides' steps
+        p = 1.0 / (diag - (i ? off * off * p : 0.0));
+        if (i < m)
+            pv[i] = p;
+        pv[n - 1 - i] = p;
+    }
+    const double pl = m >= 1 ? pv[m - 1] : 0.0;
+    const double qr = m + 1 <= n - 1 ? pv[m + 1] : 0.0;
+    pv[m] = 1.0 / (diag - off * off * pl - off * off * qr);
+    return pv;
+}
+
 // Host convenience: the tables as a vector (empty if the layout is too large).
 template <typename T>
 std::vector<T> scan_thomas_tables(int n, double off, double diag, double omega, int E, int G,

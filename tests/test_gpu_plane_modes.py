@@ -154,10 +154,11 @@ def test_modes_full_size_256(brs, orc, dt, math, method, monkeypatch):
         assert rel_max_err(got[k], sub[k - k0]) <= TOL[dt], k
 
 
-@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("dt", ["f32"])
 def test_modes_rows_not_tma_aligned_use_the_per_sweep_form(brs, orc, dt):
-    """y rows that TMA cannot stage (ny = 9): the context keeps the per-sweep form, so a call
-    of three sweeps equals three one-sweep calls bit for bit, and the oracle."""
+    """FP32 y rows that TMA cannot stage (ny = 9): the context keeps the per-sweep form, so a
+    call of three sweeps equals three one-sweep calls bit for bit, and the oracle.  (FP64
+    contexts take the x-sine form for any ny: see the twisted-elimination tests below.)"""
     import torch
 
     nx, ny, nz = 20, 9, 6
@@ -189,3 +190,45 @@ def test_modes_convergence_to_exact_solution(brs, orc, dt, math):
     exact = orc.exact_solve(b, a)
     got = run(brs, u, b, a, dt=dt, math=math, method="gs", nsweeps=600)
     assert rel_max_err(got, exact) <= (1e-10 if dt == "f64" else 1e-4)
+
+
+# FP64: the twisted-elimination mode-line sweep ([k][y][p], two threads per y-line), any ny
+TWIST_SHAPES = [(20, 9, 6), (7, 1, 5), (33, 17, 4), (5, 2, 3), (16, 16, 1), (48, 40, 7),
+                (1, 12, 4), (70, 3, 2)]
+
+
+@pytest.mark.parametrize("shape", TWIST_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("a", COEFFS, ids=["iso", "aniso_z", "aniso_yz"])
+def test_modes_f64_twisted_jacobi_any_shape(brs, orc, shape, a):
+    nx, ny, nz = shape
+    u, b = initial_guess((nz, ny, nx)), rhs((nz, ny, nx))
+    ref = u
+    for _ in range(4):
+        ref = orc.sweep(ref, b, a, block="plane", method="jacobi", omega=0.8)
+    got = run(brs, u, b, a, dt="f64", math="simt", method="jacobi", nsweeps=4)
+    assert rel_max_err(got, ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("shape", TWIST_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("omega", [1.0, 0.7])
+def test_modes_f64_twisted_gs_equals_oracle_zebra(brs, orc, shape, omega):
+    nx, ny, nz = shape
+    a = (1.0, 0.1, 0.01)
+    u, b = initial_guess((nz, ny, nx)), rhs((nz, ny, nx))
+    ref = u
+    for _ in range(3):
+        ref = orc.sweep(ref, b, a, block="plane", method="gs_zebra", omega=omega)
+    got = run(brs, u, b, a, dt="f64", math="simt", method="gs", nsweeps=3, omega=omega)
+    assert rel_max_err(got, ref) <= TOL["f64"]
+
+
+def test_modes_f64_twisted_equals_lane_scan_form(brs, orc, monkeypatch):
+    """256 x 256 x 6 FP64: the twisted form and the lane-scan mode form (BRSMOOTH_MODE_TWIST=0)
+    agree to FP64 rounding after a call of 5 sweeps."""
+    nx, ny, nz = 256, 256, 6
+    a = (1.0, 1.0, 0.01)
+    u, b = initial_guess((nz, ny, nx)), rhs((nz, ny, nx))
+    tw = run(brs, u, b, a, dt="f64", math="simt", method="jacobi", nsweeps=5)
+    monkeypatch.setenv("BRSMOOTH_MODE_TWIST", "0")
+    sc = run(brs, u, b, a, dt="f64", math="simt", method="jacobi", nsweeps=5)
+    assert rel_max_err(tw, sc) <= 1e-13
