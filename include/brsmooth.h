@@ -121,16 +121,18 @@ typedef struct brs_params {
  * admissible order of the chaotic scheme, deterministic.  BRSMOOTH_LINE_SEQ=0 in the
  * environment at creation selects the lane-scan kernel of the FP32 path instead.
  * xy-plane blocks (BRS_XYPLANE): the plane block is diagonalised along x by the
- * orthonormal DST-I.  Where TMA can stage rows of ny elements (ny times the element size a
- * multiple of 16 bytes, ny a whole number of the lane chunks of the line solve), the
- * context also holds the x-sine form of calls of several sweeps: two more grids (b and u
- * transformed, layout [k][p][y]) and, for chaotic GS, a third.  Such a call transforms b
+ * orthonormal DST-I.  FP64 contexts, and FP32 contexts where TMA can stage rows of ny
+ * elements (ny times 4 bytes a multiple of 16, ny a whole number of the lane chunks of the
+ * line solve), also hold the x-sine form of calls of several sweeps: two more grids (b and
+ * u transformed; FP32 [k][p][y], FP64 [k][y][p]) and, for chaotic GS, a third.  Such a call
+ * transforms b
  * and u once, runs its sweeps as y-line solves per x-mode with the z coupling, and
  * transforms u back; the iterates are the plane sweeps' own in exact arithmetic (the
  * transform commutes with the sweep), rounded differently, so a call of n sweeps is not
  * bitwise equal to n one-sweep calls.  It is taken for calls of at least 3 sweeps on the
  * tensor-core path and at least 2 otherwise (BRSMOOTH_PLANE_MODES_MIN); BRSMOOTH_PLANE_MODES=0
- * in the environment at creation leaves it out.  Chaotic GS on plane contexts visits the
+ * in the environment at creation leaves it out.  FP64 solves each y-line by elimination from
+ * both ends (BRSMOOTH_MODE_TWIST=0: the lane-scan solve, TMA rows only).  Chaotic GS on plane contexts visits the
  * planes in two colours, even k then odd k, each colour reading the other's newest values.
  */
 int brsmooth_create(const brs_params* p, brs_ctx** out);
