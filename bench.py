@@ -570,11 +570,16 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
         math = "3xtf32" if dt == "f32" and N % 32 == 0 else "simt"  # the library's choice
     if blk == "plane" and modes:
         # x-sine form: per call, the x-DST of b and of u and the inverse x-DST of u (nx
-        # multiply-adds per cell each), then mode-line sweeps: 3 words per cell, HBM-bound
+        # multiply-adds per cell each; FP64 splits each by the basis's even/odd symmetry into
+        # two half-size products, (ceil(nx/2)^2 + floor(nx/2)^2) / nx per cell), then
+        # mode-line sweeps: 3 words per cell, HBM-bound in FP32
         passes = 3 if math == "3xtf32" else 1
+        fold = dt == "f64" and os.environ.get("BRSMOOTH_MODE_FOLD", "1") != "0"
+        fma_t = ((N - N // 2) ** 2 + (N // 2) ** 2) / N if fold else float(N)
         out["plane_form"] = "x-sine basis: 3 transforms per call + mode-line sweeps"
         out["plane_math"] = math
-        out["tflops"] = 6.0 * N * rate / sweeps / 1e3
+        out["transform_fma_per_cell"] = fma_t
+        out["tflops"] = 6.0 * fma_t * rate / sweeps / 1e3
         if s_lo < sweeps:
             out["mode_sweep_us"] = sweep_ms * 1e3
             out["mode_sweep_gcell"] = N ** 3 / (sweep_ms / 1e3) / 1e9
@@ -586,8 +591,8 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
                 out["transforms_tensor_tflops"] = (3 * 2.0 * N * N ** 3 * passes
                                                    / (fixed_ms / 1e3) / 1e12)
             if dt == "f64":
-                out["transforms_frac_of_fp64_fma_rate"] = (3.0 * N * N ** 3 / (fixed_ms / 1e3)
-                                                           / (fma * 1e9))
+                out["transforms_frac_of_fp64_fma_rate"] = (3.0 * fma_t * N ** 3
+                                                           / (fixed_ms / 1e3) / (fma * 1e9))
     elif blk == "plane":
         # dense contractions per plane: form 1 (x sine transform + y tridiagonal solves) runs
         # the forward and inverse x transforms, nx multiply-adds per cell each; form 2 (2D

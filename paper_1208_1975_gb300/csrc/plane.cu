@@ -99,6 +99,12 @@ struct PlaneState {
     void* tgb = nullptr;     // [nx]: omega g_m az
     void* tscale = nullptr;  // [ny][nx]: omega pv_y
     void* mz = nullptr;      // Gauss-Seidel: the elimination's values
+    // the x-DST products of this form by the even/odd symmetry (dst_fold_forward / _inverse)
+    void* tSe = nullptr;     // [Ks][Ks]: S[2q][x]
+    void* tSo = nullptr;     // [Kd][Kd]: S[2q+1][x]
+    void* tSeT = nullptr;    // transposes
+    void* tSoT = nullptr;
+    int fold = 1;            // BRSMOOTH_MODE_FOLD=0: the plain products
 };
 
 // Map of a grid for the gather form, encoded on first use of its address.
@@ -1188,9 +1194,34 @@ int twist_setup(brs_ctx* c)
             e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
         return brs_cuda_status(e);
     };
+    // S's even and odd rows on the first ceil(nx/2) / floor(nx/2) columns, and transposes
+    const int Kd = nx / 2, Ks = nx - Kd;
+    const std::vector<double> S = dst1(nx);
+    std::vector<double> se((size_t)Ks * Ks), so((size_t)(Kd > 0 ? Kd : 1) * (Kd > 0 ? Kd : 1), 0.0);
+    std::vector<double> set(se.size()), sot(so.size(), 0.0);
+    for (int q = 0; q < Ks; ++q)
+        for (int x = 0; x < Ks; ++x) {
+            se[(size_t)q * Ks + x] = S[(size_t)(2 * q) * nx + x];
+            set[(size_t)x * Ks + q] = S[(size_t)(2 * q) * nx + x];
+        }
+    for (int q = 0; q < Kd; ++q)
+        for (int x = 0; x < Kd; ++x) {
+            so[(size_t)q * Kd + x] = S[(size_t)(2 * q + 1) * nx + x];
+            sot[(size_t)x * Kd + q] = S[(size_t)(2 * q + 1) * nx + x];
+        }
+    const char* fenv = std::getenv("BRSMOOTH_MODE_FOLD");
+    P->fold = !(fenv && *fenv && std::atoi(fenv) == 0);
     int rc = up(&P->tfm, fm);
     if (rc == BRS_OK)
         rc = up(&P->tfb, fb);
+    if (rc == BRS_OK)
+        rc = up(&P->tSe, se);
+    if (rc == BRS_OK)
+        rc = up(&P->tSo, so);
+    if (rc == BRS_OK)
+        rc = up(&P->tSeT, set);
+    if (rc == BRS_OK)
+        rc = up(&P->tSoT, sot);
     if (rc == BRS_OK)
         rc = up(&P->tgm, gm);
     if (rc == BRS_OK)
@@ -1224,11 +1255,27 @@ int twist_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s,
     gs_.scale = P->tscale;
     double* mb = static_cast<double*>(P->mb);
     double* mu = static_cast<double*>(P->mu);
-    cudaError_t e = launch_gemm<double, EPI_SCALE>(static_cast<const double*>(b), Sx, mb, gs_, nz, s);
-    if (e == cudaSuccess)
-        e = u_zero ? cudaMemsetAsync(mu, 0, (size_t)c->cells * sizeof(double), s)
-                   : launch_gemm<double, EPI_STORE>(static_cast<const double*>(u), Sx, mu, g, nz, s);
-    int rc = brs_cuda_status(e);
+    double* w1 = static_cast<double*>(P->t1);
+    double* w2 = static_cast<double*>(P->t2);
+    const double* Se = static_cast<const double*>(P->tSe);
+    const double* So = static_cast<const double*>(P->tSo);
+    int rc;
+    if (P->fold) {
+        rc = dst_fold_forward(static_cast<const double*>(b), mb,
+                              static_cast<const double*>(P->tscale), w1, Se, So, nx, ny, nz, s);
+        if (rc == BRS_OK)
+            rc = u_zero ? brs_cuda_status(cudaMemsetAsync(mu, 0, (size_t)c->cells * sizeof(double), s))
+                        : dst_fold_forward(static_cast<const double*>(u), mu, nullptr, w1, Se, So,
+                                           nx, ny, nz, s);
+    } else {
+        cudaError_t e =
+            launch_gemm<double, EPI_SCALE>(static_cast<const double*>(b), Sx, mb, gs_, nz, s);
+        if (e == cudaSuccess)
+            e = u_zero ? cudaMemsetAsync(mu, 0, (size_t)c->cells * sizeof(double), s)
+                       : launch_gemm<double, EPI_STORE>(static_cast<const double*>(u), Sx, mu, g,
+                                                        nz, s);
+        rc = brs_cuda_status(e);
+    }
     const double* fm = static_cast<const double*>(P->tfm);
     const double* fb = static_cast<const double*>(P->tfb);
     const double* gm = static_cast<const double*>(P->tgm);
@@ -1249,7 +1296,11 @@ int twist_sweep(brs_ctx* c, void* u, const void* b, int nsweeps, cudaStream_t s,
         }
     }
     if (rc == BRS_OK)
-        rc = brs_cuda_status(launch_gemm<double, EPI_STORE>(cur, Sx, static_cast<double*>(u), g, nz, s));
+        rc = P->fold ? dst_fold_inverse(cur, static_cast<double*>(u), w1, w2,
+                                        static_cast<const double*>(P->tSeT),
+                                        static_cast<const double*>(P->tSoT), nx, ny, nz, s)
+                     : brs_cuda_status(
+                           launch_gemm<double, EPI_STORE>(cur, Sx, static_cast<double*>(u), g, nz, s));
     return rc;
 }
 
@@ -1403,7 +1454,7 @@ void plane_teardown(brs_ctx* c)
         return;
     for (void* q : {P->sx, P->sy, P->ilam, P->t1, P->t2, P->sx_lo, P->sy_lo, P->t1_lo, P->t2_lo,
                     P->ytab, P->ym, P->mb, P->mu, P->mtab, P->mv, P->tfm, P->tfb, P->tgm,
-                    P->tgb, P->tscale, P->mz})
+                    P->tgb, P->tscale, P->mz, P->tSe, P->tSo, P->tSeT, P->tSoT})
         if (q)
             cudaFree(q);
     delete P;

@@ -19,6 +19,16 @@ int mode_twist_launch(const double* uin, double* out, double* zs, const double* 
                       const double* fm, const double* fb, const double* gm, const double* gb,
                       int nx, int ny, int nz, double omega, int colour, cudaStream_t s);
 
+// FP64 x-DST along the rows of [nz][ny][nx] arrays by the sine basis's even/odd symmetry
+// (plane_modes_f64.cu): out[k][y][p] = sum_x S[p][x] u[k][y][x] (times scale[y][p] if set),
+// and the inverse out[k][y][x] = sum_p S[x][p] uh[k][y][p].  Se / So: S's even / odd rows on
+// the first ceil(nx/2) / floor(nx/2) columns; SeT / SoT their transposes.  work arrays: grid
+// sized.
+int dst_fold_forward(const double* u, double* out, const double* scale, double* work,
+                     const double* Se, const double* So, int nx, int ny, int nz, cudaStream_t s);
+int dst_fold_inverse(const double* uh, double* out, double* work1, double* work2,
+                     const double* SeT, const double* SoT, int nx, int ny, int nz, cudaStream_t s);
+
 // Mode-line sweeps of the x-sine form (plane_modes.cu): lines of ny cells along y, one row per
 // x-mode (nm rows), nz planes, array layout [k][p][y].
 struct ModeCfg {

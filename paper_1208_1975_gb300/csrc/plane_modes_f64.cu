@@ -137,7 +137,204 @@ __global__ void __launch_bounds__(256, 4) mode_twist_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// x-DST along rows with the sine basis's even/odd symmetry.  For the orthonormal DST-I of
+// length n, S[p][n-1-x] = (-1)^p S[p][x], so with h = floor(n/2), Ks = ceil(n/2), Kd = h,
+//   forward  u^_p = sum_{x<h} S[p][x] (u_x + (-1)^p u_{n-1-x})  (+ S[p][h] u_h, p even, n odd)
+//   inverse  u_x = E_x + O_x,  u_{n-1-x} = E_x - O_x,  E_x = sum_q S[x][2q] u^_{2q},
+//            O_x = sum_q S[x][2q+1] u^_{2q+1}  (u_h = E_h for odd n)
+// so each transform is two dense products of half the size (Ks x Ks and Kd x Kd): half the
+// FP64 multiply-adds of the plain product, plus one elementwise pass before (fold,
+// de-interleave) and, for the inverse, one after (combine).
+
+// dst[row][0..Ks) = u_x + u_{n-1-x} (x < h; u_h last for odd n), dst[row][Ks..n) = u_x - u_{n-1-x}
+__global__ void __launch_bounds__(256) fold_rows_kernel(const double* __restrict__ src,
+                                                        double* __restrict__ dst, int n,
+                                                        long long rows)
+{
+    pdl_wait_trigger();
+    const int h = n / 2, Ks = n - h;
+    const long long total = rows * (long long)Ks;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / Ks;
+        const int x = (int)(t - r * Ks);
+        const double* a = src + r * n;
+        double* d = dst + r * n;
+        if (x < h) {
+            const double lo = a[x], hi = a[n - 1 - x];
+            d[x] = lo + hi;
+            d[Ks + x] = lo - hi;
+        } else {
+            d[x] = a[x];  // the middle element of an odd length
+        }
+    }
+}
+
+// dst[row][q] = src[row][2q] (q < Ks), dst[row][Ks + q] = src[row][2q+1] (q < Kd)
+__global__ void __launch_bounds__(256) deinterleave_rows_kernel(const double* __restrict__ src,
+                                                                double* __restrict__ dst, int n,
+                                                                long long rows)
+{
+    pdl_wait_trigger();
+    const int Ks = n - n / 2;
+    const long long total = rows * (long long)n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / n;
+        const int p = (int)(t - r * n);
+        dst[r * n + (p & 1 ? Ks + (p >> 1) : (p >> 1))] = src[t];
+    }
+}
+
+// src[row] = [E_0..E_{Ks-1} | O_0..O_{Kd-1}] -> dst[row][x] = E_x + O_x, dst[row][n-1-x] = E_x - O_x
+__global__ void __launch_bounds__(256) combine_rows_kernel(const double* __restrict__ src,
+                                                           double* __restrict__ dst, int n,
+                                                           long long rows)
+{
+    pdl_wait_trigger();
+    const int h = n / 2, Ks = n - h;
+    const long long total = rows * (long long)Ks;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / Ks;
+        const int x = (int)(t - r * Ks);
+        const double* a = src + r * n;
+        double* d = dst + r * n;
+        if (x < h) {
+            const double e = a[x], o = a[Ks + x];
+            d[x] = e + o;
+            d[n - 1 - x] = e - o;
+        } else {
+            d[x] = a[x];
+        }
+    }
+}
+
+// C[m][n] at C + b sC + m ldc + n ccs = sum_k A[b sA + m lda + k] B[n ldb + k] (times scale at
+// C's offset when scale is set); 64 x 64 tiles, 4 x 4 outputs per thread.
+struct StridedGemm {
+    int M, N, K;
+    long long lda, ldb, ldc, ccs, sA, sC;
+    const double* scale;
+};
+
+constexpr int kTM = 64, kTN = 64, kTK = 16;
+
+__global__ void __launch_bounds__(256) gemm_strided_kernel(const double* __restrict__ A,
+                                                           const double* __restrict__ B,
+                                                           double* C, StridedGemm g)
+{
+    pdl_wait_trigger();
+    __shared__ double As[kTK][kTM + 1];
+    __shared__ double Bs[kTK][kTN + 1];
+    const double* Ab = A + (long long)blockIdx.z * g.sA;
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < g.K; k0 += kTK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = threadIdx.x + r * 256;
+            const int row = idx / kTK, kk = idx % kTK;
+            const int gm = m0 + row, gn = n0 + row, gk = k0 + kk;
+            As[kk][row] = (gm < g.M && gk < g.K) ? Ab[(long long)gm * g.lda + gk] : 0.0;
+            Bs[kk][row] = (gn < g.N && gk < g.K) ? B[(long long)gn * g.ldb + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTK; ++kk) {
+            double a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty + 16 * i];
+                bv[i] = Bs[kk][tx + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double* Cb = C + (long long)blockIdx.z * g.sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < g.M && n < g.N) {
+                const long long o = (long long)m * g.ldc + (long long)n * g.ccs;
+                Cb[o] = g.scale ? acc[i][j] * g.scale[o] : acc[i][j];
+            }
+        }
+}
+
+cudaError_t launch_strided(const double* A, const double* B, double* C, const StridedGemm& g,
+                           int batch, cudaStream_t s)
+{
+    if (g.M == 0 || g.N == 0 || batch == 0)
+        return cudaSuccess;
+    dim3 grid((g.N + kTN - 1) / kTN, (g.M + kTM - 1) / kTM, batch);
+    return launch_pdl(gemm_strided_kernel, grid, dim3(256), 0, s, A, B, C, g);
+}
+
+unsigned row_grid(long long work)
+{
+    long long b = (work + 255) / 256;
+    return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
 }  // namespace
+
+int dst_fold_forward(const double* u, double* out, const double* scale, double* work,
+                     const double* Se, const double* So, int nx, int ny, int nz, cudaStream_t s)
+{
+    const int h = nx / 2, Ks = nx - h, Kd = h;
+    const long long rows = (long long)ny * nz, plane = (long long)nx * ny;
+    cudaError_t e = launch_pdl(fold_rows_kernel, dim3(row_grid(rows * Ks)), dim3(256), 0, s, u,
+                               work, nx, rows);
+    StridedGemm g{};
+    g.M = ny; g.lda = nx; g.ldc = nx; g.ccs = 2; g.sA = plane; g.sC = plane;
+    // even modes p = 2q: the folded sums against Se[q][x'] = S[2q][x'] (x' < Ks)
+    g.N = Ks; g.K = Ks; g.ldb = Ks; g.scale = scale;
+    if (e == cudaSuccess)
+        e = launch_strided(work, Se, out, g, nz, s);
+    // odd modes p = 2q+1: the folded differences against So[q][x'] = S[2q+1][x'] (x' < Kd)
+    g.N = Kd; g.K = Kd; g.ldb = Kd; g.scale = scale ? scale + 1 : nullptr;
+    if (e == cudaSuccess && Kd > 0)
+        e = launch_strided(work + Ks, So, out + 1, g, nz, s);
+    return brs_cuda_status(e);
+}
+
+int dst_fold_inverse(const double* uh, double* out, double* work1, double* work2,
+                     const double* SeT, const double* SoT, int nx, int ny, int nz, cudaStream_t s)
+{
+    const int h = nx / 2, Ks = nx - h, Kd = h;
+    const long long rows = (long long)ny * nz, plane = (long long)nx * ny;
+    cudaError_t e = launch_pdl(deinterleave_rows_kernel, dim3(row_grid(rows * nx)), dim3(256), 0,
+                               s, uh, work1, nx, rows);
+    StridedGemm g{};
+    g.M = ny; g.lda = nx; g.ldc = nx; g.ccs = 1; g.sA = plane; g.sC = plane; g.scale = nullptr;
+    // E_x = sum_q S[x][2q] u^_{2q}: B[x][q] = SeT[x][q] (x < Ks)
+    g.N = Ks; g.K = Ks; g.ldb = Ks;
+    if (e == cudaSuccess)
+        e = launch_strided(work1, SeT, work2, g, nz, s);
+    // O_x = sum_q S[x][2q+1] u^_{2q+1}: B[x][q] = SoT[x][q] (x < Kd)
+    g.N = Kd; g.K = Kd; g.ldb = Kd;
+    if (e == cudaSuccess && Kd > 0)
+        e = launch_strided(work1 + Ks, SoT, work2 + Ks, g, nz, s);
+    if (e == cudaSuccess)
+        e = launch_pdl(combine_rows_kernel, dim3(row_grid(rows * Ks)), dim3(256), 0, s,
+                       (const double*)work2, out, nx, rows);
+    return brs_cuda_status(e);
+}
 
 int mode_twist_launch(const double* uin, double* out, double* zs, const double* bs,
                       const double* fm, const double* fb, const double* gm, const double* gb,

@@ -232,3 +232,22 @@ def test_modes_f64_twisted_equals_lane_scan_form(brs, orc, monkeypatch):
     monkeypatch.setenv("BRSMOOTH_MODE_TWIST", "0")
     sc = run(brs, u, b, a, dt="f64", math="simt", method="jacobi", nsweeps=5)
     assert rel_max_err(tw, sc) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(256, 64, 4), (255, 33, 3), (33, 17, 4), (1, 9, 3), (2, 5, 3)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_modes_f64_folded_transforms_equal_plain_products(brs, orc, shape, monkeypatch):
+    """The FP64 x-DST by the sine basis's even/odd symmetry (two half-size products) against
+    the plain products (BRSMOOTH_MODE_FOLD=0), even and odd nx, after a call of 3 sweeps; and
+    the oracle."""
+    nx, ny, nz = shape
+    a = (1.0, 0.1, 0.01)
+    u, b = initial_guess((nz, ny, nx)), rhs((nz, ny, nx))
+    ref = u
+    for _ in range(3):
+        ref = orc.sweep(ref, b, a, block="plane", method="jacobi", omega=0.8)
+    fold = run(brs, u, b, a, dt="f64", math="simt", method="jacobi", nsweeps=3)
+    monkeypatch.setenv("BRSMOOTH_MODE_FOLD", "0")
+    plain = run(brs, u, b, a, dt="f64", math="simt", method="jacobi", nsweeps=3)
+    assert rel_max_err(fold, plain) <= 1e-13
+    assert rel_max_err(fold, ref) <= TOL["f64"]
