@@ -178,3 +178,58 @@ def test_box_argument_errors(brs):
     with pytest.raises(brs.BrsError) as e:
         brs.Context(16, 16, 16, block="box", box=(2, 2, 2), dtype="f32", plane_math="tf32")
     assert e.value.code == brs.BRS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("case", [((32, 32, 16), (8, 8, 8)), ((24, 18, 15), (6, 3, 5)),
+                                  ((10, 40, 6), (1, 40, 1)), ((40, 24, 16), (8, 4, 4)),
+                                  ((28, 14, 8), (7, 7, 1))],
+                         ids=lambda c: "b" + "x".join(map(str, c[1])))
+@pytest.mark.parametrize("method", ["jacobi", "gs"])
+def test_box_parity_classes_equal_full_product(brs, orc, dt, case, method, monkeypatch):
+    """CUDA-core boxes: the inverse applied by parity classes (rows folded into sums and
+    differences of mirrored cells, one product per class, unfolded in the update) against the
+    full n x n product (BRSMOOTH_BOX_FOLD=0), two sweeps, even and odd box extents (every
+    case has a class of 16 or more cells, so the classes are used)."""
+    shape, box = case
+    a = (1.0, 0.1, 0.01)
+    u, b = inputs(shape, dt)
+    fold = gpu_sweeps(brs, u, b, a, box, dt=dt, method=method, nsweeps=2, math="simt")
+    monkeypatch.setenv("BRSMOOTH_BOX_FOLD", "0")
+    full = gpu_sweeps(brs, u, b, a, box, dt=dt, method=method, nsweeps=2, math="simt")
+    tol = 1e-13 if dt == "f64" else 2 * TOL["f32"]
+    assert rel_max_err(fold[1], full[1]) <= tol
+
+
+def test_box_parity_classes_full_size_fp64_gs(brs, orc):
+    """256^3 FP64 two-colour GS with 8^3 boxes (the paper's block and precision), by parity
+    classes: one sweep on sampled blocks against the oracle's zebra order."""
+    import torch
+
+    n = 256
+    a = (1.0, 1.0, 1.0)
+    box = (8, 8, 8)
+    gen = torch.Generator(device="cuda").manual_seed(29)
+    u0 = torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+    bt = (torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen) * 2 - 1) \
+        / (n + 1) ** 2
+    with brs.Context(n, n, n, a, block="box", box=box, method="gs", dtype="f64") as ctx:
+        ut = u0.clone()
+        ctx.sweep(ut, bt, 1)
+        torch.cuda.synchronize()
+        assert ctx.last_error() == 0
+    u, b, got = to_np(u0), to_np(bt), to_np(ut)
+    # a block after one zebra sweep depends on the blocks within distance 2 (colours kept)
+    for (bi, bj, bk) in [(0, 0, 0), (17, 9, 30), (31, 31, 31)]:
+        lo = [max(0, q - 2) for q in (bi, bj, bk)]
+        if sum(lo) % 2:
+            d = next(q for q in range(3) if lo[q] > 0)
+            lo[d] -= 1
+        hi = [min(32, q + 3) for q in (bi, bj, bk)]
+        sl = (slice(lo[2] * 8, hi[2] * 8), slice(lo[1] * 8, hi[1] * 8), slice(lo[0] * 8, hi[0] * 8))
+        ref = orc.sweep(np.ascontiguousarray(u[sl]), np.ascontiguousarray(b[sl]), a, block="box",
+                        box=box, method="gs_zebra", omega=1.0)
+        c = [(q - l) * 8 for q, l in zip((bi, bj, bk), lo)]
+        own = ref[c[2]:c[2] + 8, c[1]:c[1] + 8, c[0]:c[0] + 8]
+        g = got[bk * 8:bk * 8 + 8, bj * 8:bj * 8 + 8, bi * 8:bi * 8 + 8]
+        assert float(np.max(np.abs(g - own))) <= 1e-12 * float(np.max(np.abs(u))), (bi, bj, bk)
