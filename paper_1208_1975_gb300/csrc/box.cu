@@ -371,28 +371,43 @@ cudaError_t launch_simt(const BoxState* B, const T* R, const T* inv, const T* u,
 }
 
 // ---------------------------------------------------------------- parity classes
-// Rf[row][f] = sum over f's cells l of +-R[row][l] (the butterflies of G)
+// Rf[row][f] = sum over f's cells l of +-R[row][l] (the butterflies of G).  A CTA stages the
+// butterfly table and kRowsPerCta rows at a time in shared memory, so every row is read
+// from global memory once, coalesced, and the butterflies read shared memory.
+constexpr int kRowsPerCta = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) box_fold_kernel(const T* __restrict__ R, T* __restrict__ Rf,
                                                        const int* __restrict__ fmap, long long M,
                                                        int n)
 {
+    extern __shared__ __align__(16) unsigned char fold_smem[];
+    int* map = reinterpret_cast<int*>(fold_smem);
+    T* rows = reinterpret_cast<T*>(fold_smem + (size_t)n * 8 * sizeof(int));
     pdl_wait_trigger();
-    const long long total = M * n;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long row = t / n;
-        const int f = (int)(t - row * n);
-        const T* r = R + row * n;
-        T acc = T(0);
+    for (int i = threadIdx.x; i < n * 8; i += blockDim.x)
+        map[i] = __ldg(fmap + i);
+    const long long chunks = (M + kRowsPerCta - 1) / kRowsPerCta;
+    for (long long ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+        const long long r0 = ch * kRowsPerCta;
+        const int nr = (int)(M - r0 < kRowsPerCta ? M - r0 : kRowsPerCta);
+        __syncthreads();  // the previous chunk's rows are consumed (and the map is staged)
+        for (int i = threadIdx.x; i < nr * n; i += blockDim.x)
+            rows[i] = R[r0 * n + i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr * n; i += blockDim.x) {
+            const int rr = i / n, f = i - rr * n;
+            const T* r = rows + rr * n;
+            T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = __ldg(fmap + f * 8 + q);
-            if (e == 0)
-                break;
-            acc = e > 0 ? acc + r[e - 1] : acc - r[-e - 1];
+            for (int q = 0; q < 8; ++q) {
+                const int e = map[f * 8 + q];
+                if (e == 0)
+                    break;
+                acc = e > 0 ? acc + r[e - 1] : acc - r[-e - 1];
+            }
+            Rf[r0 * n + i] = acc;
         }
-        Rf[t] = acc;
     }
 }
 
@@ -465,7 +480,8 @@ __global__ void __launch_bounds__(256) box_class_gemm(const T* __restrict__ Rf,
 }
 
 // uout[cell] = (1 - omega) u[cell] + omega D[l],  D[l] = sum over l's folded indices f of
-// +-Df[row][f] (G^T), for every cell l of every block row of the pass
+// +-Df[row][f] (G^T), for every cell l of every block row of the pass; rows and the
+// butterfly table staged in shared memory as for the fold
 template <typename T>
 __global__ void __launch_bounds__(256) box_unfold_kernel(const T* __restrict__ Df,
                                                          const int* __restrict__ umap,
@@ -475,35 +491,52 @@ __global__ void __launch_bounds__(256) box_unfold_kernel(const T* __restrict__ D
                                                          int n, int bx, int by, int bz, int nx,
                                                          int ny, double omega)
 {
+    extern __shared__ __align__(16) unsigned char fold_smem[];
+    int* map = reinterpret_cast<int*>(fold_smem);
+    T* drow = reinterpret_cast<T*>(fold_smem + (size_t)n * 8 * sizeof(int));
     pdl_wait_trigger();
+    for (int i = threadIdx.x; i < n * 8; i += blockDim.x)
+        map[i] = __ldg(umap + i);
     const T om = (T)omega, om1 = (T)(1.0 - omega);
-    const long long total = M * n;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long row = t / n;
-        const int l = (int)(t - row * n);
-        const T* d = Df + row * n;
-        T acc = T(0);
+    const long long chunks = (M + kRowsPerCta - 1) / kRowsPerCta;
+    for (long long ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+        const long long r0 = ch * kRowsPerCta;
+        const int nr = (int)(M - r0 < kRowsPerCta ? M - r0 : kRowsPerCta);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr * n; i += blockDim.x)
+            drow[i] = Df[r0 * n + i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr * n; i += blockDim.x) {
+            const int rr = i / n, l = i - rr * n;
+            const T* d = drow + rr * n;
+            T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = __ldg(umap + l * 8 + q);
-            if (e == 0)
-                break;
-            acc = e > 0 ? acc + d[e - 1] : acc - d[-e - 1];
+            for (int q = 0; q < 8; ++q) {
+                const int e = map[l * 8 + q];
+                if (e == 0)
+                    break;
+                acc = e > 0 ? acc + d[e - 1] : acc - d[-e - 1];
+            }
+            const long long pk = rows[r0 + rr];
+            const long long base = (pk & 0x1FFFFF) * bx +
+                                   (long long)nx * (((pk >> 21) & 0x1FFFFF) * by +
+                                                    (long long)ny * (pk >> 42) * bz);
+            const long long cell = base + __ldg(off + l);
+            uout[cell] = fma(om, acc, om1 * u[cell]);
         }
-        const long long pk = rows[row];
-        const long long base = (pk & 0x1FFFFF) * bx +
-                               (long long)nx * (((pk >> 21) & 0x1FFFFF) * by +
-                                                (long long)ny * (pk >> 42) * bz);
-        const long long cell = base + __ldg(off + l);
-        uout[cell] = fma(om, acc, om1 * u[cell]);
     }
 }
 
-unsigned elem_grid(long long work)
+unsigned chunk_grid(long long M)
 {
-    const long long b = (work + 255) / 256;
-    return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+    const long long ch = (M + kRowsPerCta - 1) / kRowsPerCta;
+    return (unsigned)(ch < 152 * 8 ? (ch > 0 ? ch : 1) : 152 * 8);
+}
+
+template <typename T>
+size_t fold_smem(int n)
+{
+    return (size_t)n * 8 * sizeof(int) + (size_t)kRowsPerCta * n * sizeof(T);
 }
 
 // gather, fold, one product per class, unfold with the update
@@ -518,7 +551,7 @@ int box_pass_fold(brs_ctx* c, const T* uin, T* uout, const T* b, const long long
     cudaError_t e = launch_gather<T, 0>(B, p, uin, b, R, nullptr, rows, M, s);
     const int n = B->n;
     if (e == cudaSuccess)
-        e = launch_pdl(box_fold_kernel<T>, dim3(elem_grid(M * n)), dim3(256), 0, s,
+        e = launch_pdl(box_fold_kernel<T>, dim3(chunk_grid(M)), dim3(256), fold_smem<T>(n), s,
                        (const T*)R, Rf, (const int*)B->fmap, M, n);
     const T* Pc = static_cast<const T*>(B->Pc);
     for (int cl = 0; cl < 8 && e == cudaSuccess; ++cl) {
@@ -538,7 +571,7 @@ int box_pass_fold(brs_ctx* c, const T* uin, T* uout, const T* b, const long long
                            (const T*)Rf, Pc + B->pc_off[cl], R, M, n, B->cls_off[cl], nc);
     }
     if (e == cudaSuccess)
-        e = launch_pdl(box_unfold_kernel<T>, dim3(elem_grid(M * n)), dim3(256), 0, s,
+        e = launch_pdl(box_unfold_kernel<T>, dim3(chunk_grid(M)), dim3(256), fold_smem<T>(n), s,
                        (const T*)R, (const int*)B->umap, uin, uout, rows, (const int*)B->off, M,
                        n, B->bx, B->by, B->bz, p.nx, p.ny, c->omega);
     return brs_cuda_status(e);
