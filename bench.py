@@ -519,6 +519,27 @@ def _plane_form(ny):
     return 1 if os.environ.get("BRSMOOTH_PLANE_FORM", "1") == "1" and ny <= 512 else 2
 
 
+def _box_fma_per_cell(box, dt, math):
+    """Multiply-adds per cell of the box product as the library runs it: n for the full
+    product; sum over the 8 parity classes of n_c^2 / n on CUDA cores where that saves half
+    the work and a class has 16+ cells (BRSMOOTH_BOX_FOLD=0: the full product)."""
+    n = box[0] * box[1] * box[2]
+    cuda_cores = dt == "f64" or math == "simt" or (math == "auto" and (n % 4 or n < 32))
+    if not cuda_cores or os.environ.get("BRSMOOTH_BOX_FOLD", "1") == "0":
+        return float(n)
+    sizes = []
+    for cl in range(8):
+        nc = 1
+        for d in range(3):
+            h = box[d] // 2
+            nc *= h if (cl >> d) & 1 else box[d] - h
+        sizes.append(nc)
+    work = sum(x * x for x in sizes)
+    if 2 * work > n * n or max(sizes) < 16:
+        return float(n)
+    return work / n
+
+
 def _plane_modes_min(dt, math):
     """Smallest sweep count per call for which the library runs the x-sine form (plane
     contexts whose y rows TMA can stage; 0 when switched off by BRSMOOTH_PLANE_MODES=0)."""
@@ -553,10 +574,14 @@ def _variant_grid(brs, stream, barrier, peak, blk, meth, dt, a, steps, sweeps, m
            "sweeps_per_call": sweeps}
     fma = _fma_rate(brs, stream) / 1e9 if dt == "f64" else None
     if blk == "box":
-        # the dense block product: n multiply-adds per cell, n = bx by bz (Alg. 2 step 2)
-        nb = box[0] * box[1] * box[2]
+        # the dense block product: n multiply-adds per cell, n = bx by bz (Alg. 2 step 2); on
+        # CUDA cores by parity classes where the library uses them: sum_c n_c^2 / n
+        nfull = box[0] * box[1] * box[2]
+        nb = _box_fma_per_cell(box, dt, math)
         out["box"] = list(box)
         out["plane_math"] = math
+        out["fma_per_cell"] = nb
+        out["parity_classes"] = nb < nfull
         out["tflops"] = rate * 2 * nb / 1e3
         if math in ("tf32", "3xtf32"):
             passes = 3 if math == "3xtf32" else 1

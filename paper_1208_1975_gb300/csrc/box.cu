@@ -53,14 +53,16 @@ struct BoxState {
     CUtensorMap mR_hi, mR_lo, mA_hi, mA_lo;
     // parity classes (CUDA-core path): class sizes and offsets in the folded row, the class
     // blocks of P (class c at pc_off[c], nc x nc), the folded rows, and the butterflies:
-    // fmap[f][0..8) = +-(l+1) of folded index f's cells (0 = none), umap[l][0..8) = +-(f+1)
+    // fmap[q][f] (q < 8) = +-(l+1) of folded index f's cells (0 = none), umap[q][l] = +-(f+1)
     int fold = 0;
     int cls_n[8] = {0}, cls_off[8] = {0};
     long long pc_off[8] = {0};
     void* Pc = nullptr;
     void* Rf = nullptr;
-    int* fmap = nullptr;
+    int* fmap = nullptr;  // (host-side construction of P; not used by the kernels)
     int* umap = nullptr;
+    void* ftab = nullptr; // [3][n] int2: the fold's passes (x, y, z), the last into class order
+    void* utab = nullptr; // [3][n] int2: the unfold's passes (z, y, x), the first from class order
 };
 
 BoxState* bs(brs_ctx* c) { return static_cast<BoxState*>(c->box); }
@@ -371,43 +373,52 @@ cudaError_t launch_simt(const BoxState* B, const T* R, const T* inv, const T* u,
 }
 
 // ---------------------------------------------------------------- parity classes
-// Rf[row][f] = sum over f's cells l of +-R[row][l] (the butterflies of G).  A CTA stages the
-// butterfly table and kRowsPerCta rows at a time in shared memory, so every row is read
-// from global memory once, coalesced, and the butterflies read shared memory.
+// G and G^T are separable: one 2 x 2 butterfly per mirrored pair along each axis, so each is
+// applied in three passes (x, y, z for G; z, y, x for G^T) with one addition per element and
+// pass.  A pass is a table over its output positions o: out[o] = in[t.x] + sign in[|t.y| - 1]
+// (t.y = 0: out[o] = in[t.x]).  The fold's last pass writes the class-major order, the unfold's
+// first pass reads it.  A CTA stages kRowsPerCta rows and the three tables in shared memory.
 constexpr int kRowsPerCta = 4;
 
 template <typename T>
+__device__ __forceinline__ T butterfly(const T* in, int2 t)
+{
+    const T a = in[t.x];
+    return t.y == 0 ? a : t.y > 0 ? a + in[t.y - 1] : a - in[-t.y - 1];
+}
+
+// Rf[row] = G R[row] in class-major order
+template <typename T>
 __global__ void __launch_bounds__(256) box_fold_kernel(const T* __restrict__ R, T* __restrict__ Rf,
-                                                       const int* __restrict__ fmap, long long M,
+                                                       const int2* __restrict__ tabs, long long M,
                                                        int n)
 {
     extern __shared__ __align__(16) unsigned char fold_smem[];
-    int* map = reinterpret_cast<int*>(fold_smem);
-    T* rows = reinterpret_cast<T*>(fold_smem + (size_t)n * 8 * sizeof(int));
+    int2* tab = reinterpret_cast<int2*>(fold_smem);  // [3][n]
+    T* A = reinterpret_cast<T*>(fold_smem + (size_t)3 * n * sizeof(int2));
+    T* Bf = A + (size_t)kRowsPerCta * n;
     pdl_wait_trigger();
-    for (int i = threadIdx.x; i < n * 8; i += blockDim.x)
-        map[i] = __ldg(fmap + i);
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x)
+        tab[i] = tabs[i];
     const long long chunks = (M + kRowsPerCta - 1) / kRowsPerCta;
     for (long long ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
         const long long r0 = ch * kRowsPerCta;
         const int nr = (int)(M - r0 < kRowsPerCta ? M - r0 : kRowsPerCta);
-        __syncthreads();  // the previous chunk's rows are consumed (and the map is staged)
+        __syncthreads();  // the previous chunk is consumed (and the tables are staged)
         for (int i = threadIdx.x; i < nr * n; i += blockDim.x)
-            rows[i] = R[r0 * n + i];
+            A[i] = R[r0 * n + i];
         __syncthreads();
-        for (int i = threadIdx.x; i < nr * n; i += blockDim.x) {
-            const int rr = i / n, f = i - rr * n;
-            const T* r = rows + rr * n;
-            T acc = T(0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = map[f * 8 + q];
-                if (e == 0)
-                    break;
-                acc = e > 0 ? acc + r[e - 1] : acc - r[-e - 1];
-            }
-            Rf[r0 * n + i] = acc;
-        }
+        for (int rr = 0; rr < nr; ++rr)
+            for (int o = threadIdx.x; o < n; o += blockDim.x)
+                Bf[rr * n + o] = butterfly(A + rr * n, tab[o]);
+        __syncthreads();
+        for (int rr = 0; rr < nr; ++rr)
+            for (int o = threadIdx.x; o < n; o += blockDim.x)
+                A[rr * n + o] = butterfly(Bf + rr * n, tab[n + o]);
+        __syncthreads();
+        for (int rr = 0; rr < nr; ++rr)
+            for (int o = threadIdx.x; o < n; o += blockDim.x)
+                Rf[(r0 + rr) * n + o] = butterfly(A + rr * n, tab[2 * n + o]);
     }
 }
 
@@ -479,12 +490,11 @@ __global__ void __launch_bounds__(256) box_class_gemm(const T* __restrict__ Rf,
     }
 }
 
-// uout[cell] = (1 - omega) u[cell] + omega D[l],  D[l] = sum over l's folded indices f of
-// +-Df[row][f] (G^T), for every cell l of every block row of the pass; rows and the
-// butterfly table staged in shared memory as for the fold
+// uout[cell] = (1 - omega) u[cell] + omega D[l], D = G^T Df[row] (class-major in), for every
+// cell l of every block row of the pass
 template <typename T>
 __global__ void __launch_bounds__(256) box_unfold_kernel(const T* __restrict__ Df,
-                                                         const int* __restrict__ umap,
+                                                         const int2* __restrict__ tabs,
                                                          const T* u, T* uout,
                                                          const long long* __restrict__ rows,
                                                          const int* __restrict__ off, long long M,
@@ -492,11 +502,12 @@ __global__ void __launch_bounds__(256) box_unfold_kernel(const T* __restrict__ D
                                                          int ny, double omega)
 {
     extern __shared__ __align__(16) unsigned char fold_smem[];
-    int* map = reinterpret_cast<int*>(fold_smem);
-    T* drow = reinterpret_cast<T*>(fold_smem + (size_t)n * 8 * sizeof(int));
+    int2* tab = reinterpret_cast<int2*>(fold_smem);
+    T* A = reinterpret_cast<T*>(fold_smem + (size_t)3 * n * sizeof(int2));
+    T* Bf = A + (size_t)kRowsPerCta * n;
     pdl_wait_trigger();
-    for (int i = threadIdx.x; i < n * 8; i += blockDim.x)
-        map[i] = __ldg(umap + i);
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x)
+        tab[i] = tabs[i];
     const T om = (T)omega, om1 = (T)(1.0 - omega);
     const long long chunks = (M + kRowsPerCta - 1) / kRowsPerCta;
     for (long long ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
@@ -504,25 +515,26 @@ __global__ void __launch_bounds__(256) box_unfold_kernel(const T* __restrict__ D
         const int nr = (int)(M - r0 < kRowsPerCta ? M - r0 : kRowsPerCta);
         __syncthreads();
         for (int i = threadIdx.x; i < nr * n; i += blockDim.x)
-            drow[i] = Df[r0 * n + i];
+            A[i] = Df[r0 * n + i];
         __syncthreads();
-        for (int i = threadIdx.x; i < nr * n; i += blockDim.x) {
-            const int rr = i / n, l = i - rr * n;
-            const T* d = drow + rr * n;
-            T acc = T(0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = map[l * 8 + q];
-                if (e == 0)
-                    break;
-                acc = e > 0 ? acc + d[e - 1] : acc - d[-e - 1];
-            }
+        for (int rr = 0; rr < nr; ++rr)
+            for (int o = threadIdx.x; o < n; o += blockDim.x)
+                Bf[rr * n + o] = butterfly(A + rr * n, tab[o]);
+        __syncthreads();
+        for (int rr = 0; rr < nr; ++rr)
+            for (int o = threadIdx.x; o < n; o += blockDim.x)
+                A[rr * n + o] = butterfly(Bf + rr * n, tab[n + o]);
+        __syncthreads();
+        for (int rr = 0; rr < nr; ++rr) {
             const long long pk = rows[r0 + rr];
             const long long base = (pk & 0x1FFFFF) * bx +
                                    (long long)nx * (((pk >> 21) & 0x1FFFFF) * by +
                                                     (long long)ny * (pk >> 42) * bz);
-            const long long cell = base + __ldg(off + l);
-            uout[cell] = fma(om, acc, om1 * u[cell]);
+            for (int l = threadIdx.x; l < n; l += blockDim.x) {
+                const T d = butterfly(A + rr * n, tab[2 * n + l]);
+                const long long cell = base + __ldg(off + l);
+                uout[cell] = fma(om, d, om1 * u[cell]);
+            }
         }
     }
 }
@@ -536,7 +548,7 @@ unsigned chunk_grid(long long M)
 template <typename T>
 size_t fold_smem(int n)
 {
-    return (size_t)n * 8 * sizeof(int) + (size_t)kRowsPerCta * n * sizeof(T);
+    return (size_t)3 * n * sizeof(int2) + (size_t)2 * kRowsPerCta * n * sizeof(T);
 }
 
 // gather, fold, one product per class, unfold with the update
@@ -552,7 +564,7 @@ int box_pass_fold(brs_ctx* c, const T* uin, T* uout, const T* b, const long long
     const int n = B->n;
     if (e == cudaSuccess)
         e = launch_pdl(box_fold_kernel<T>, dim3(chunk_grid(M)), dim3(256), fold_smem<T>(n), s,
-                       (const T*)R, Rf, (const int*)B->fmap, M, n);
+                       (const T*)R, Rf, (const int2*)B->ftab, M, n);
     const T* Pc = static_cast<const T*>(B->Pc);
     for (int cl = 0; cl < 8 && e == cudaSuccess; ++cl) {
         const int nc = B->cls_n[cl];
@@ -572,7 +584,7 @@ int box_pass_fold(brs_ctx* c, const T* uin, T* uout, const T* b, const long long
     }
     if (e == cudaSuccess)
         e = launch_pdl(box_unfold_kernel<T>, dim3(chunk_grid(M)), dim3(256), fold_smem<T>(n), s,
-                       (const T*)R, (const int*)B->umap, uin, uout, rows, (const int*)B->off, M,
+                       (const T*)R, (const int2*)B->utab, uin, uout, rows, (const int*)B->off, M,
                        n, B->bx, B->by, B->bz, p.nx, p.ny, c->omega);
     return brs_cuda_status(e);
 }
@@ -777,8 +789,8 @@ int parity_setup(BoxState* B, const std::vector<double>& inv)
                 if (!ok)
                     continue;
                 const int l = x[0] + b[0] * (x[1] + b[1] * x[2]);
-                fmap[(size_t)f * 8 + q++] = sign * (l + 1);
-                umap[(size_t)l * 8 + ucount[l]++] = sign * (f + 1);
+                fmap[(size_t)(q++) * n + f] = sign * (l + 1);
+                umap[(size_t)(ucount[l]++) * n + l] = sign * (f + 1);
             }
             for (int d = 0; d < 3; ++d)
                 if (j[d] < ha[d])
@@ -794,11 +806,11 @@ int parity_setup(BoxState* B, const std::vector<double>& inv)
         for (int f = o; f < o + nc; ++f)
             for (int g = o; g < o + nc; ++g) {
                 double acc = 0.0;
-                for (int q = 0; q < 8 && fmap[(size_t)f * 8 + q]; ++q) {
-                    const int ef = fmap[(size_t)f * 8 + q];
+                for (int q = 0; q < 8 && fmap[(size_t)q * n + f]; ++q) {
+                    const int ef = fmap[(size_t)q * n + f];
                     const int l = (ef > 0 ? ef : -ef) - 1;
-                    for (int r = 0; r < 8 && fmap[(size_t)g * 8 + r]; ++r) {
-                        const int eg = fmap[(size_t)g * 8 + r];
+                    for (int r = 0; r < 8 && fmap[(size_t)r * n + g]; ++r) {
+                        const int eg = fmap[(size_t)r * n + g];
                         const int l2 = (eg > 0 ? eg : -eg) - 1;
                         const double v = inv[(size_t)l * n + l2];
                         acc += ((ef > 0) == (eg > 0)) ? v : -v;
@@ -807,11 +819,64 @@ int parity_setup(BoxState* B, const std::vector<double>& inv)
                 pc.push_back((T)(W[f] * W[g] * acc));
             }
     }
+    // the separable passes: layouts are (c0, c1, c2) lexicographic with each coordinate a
+    // cell or, once its axis is folded, a folded coordinate (sums first, then differences)
+    auto lex = [&](const int c[3]) { return c[0] + b[0] * (c[1] + b[1] * c[2]); };
+    std::vector<int> perm(n);  // lexicographic folded index -> class-major index
+    for (int cl = 0; cl < 8; ++cl) {
+        const int c3[3] = {cl & 1, (cl >> 1) & 1, (cl >> 2) & 1};
+        const int sz[3] = {c3[0] ? ha[0] : hs[0], c3[1] ? ha[1] : hs[1], c3[2] ? ha[2] : hs[2]};
+        for (int i = 0; i < B->cls_n[cl]; ++i) {
+            const int j[3] = {i % sz[0], (i / sz[0]) % sz[1], i / (sz[0] * sz[1])};
+            const int f[3] = {j[0] + c3[0] * hs[0], j[1] + c3[1] * hs[1], j[2] + c3[2] * hs[2]};
+            perm[lex(f)] = B->cls_off[cl] + i;
+        }
+    }
+    std::vector<int2> ftab((size_t)3 * n), utab((size_t)3 * n);
+    for (int d = 0; d < 3; ++d)
+        for (int o = 0; o < n; ++o) {
+            int c[3] = {o % b[0], (o / b[0]) % b[1], o / (b[0] * b[1])};
+            // fold pass d: output folded coordinate c[d] from the cells along d
+            {
+                int ca[3] = {c[0], c[1], c[2]}, cb[3] = {c[0], c[1], c[2]};
+                const bool anti = c[d] >= hs[d];
+                const int jj = anti ? c[d] - hs[d] : c[d];
+                ca[d] = jj;
+                cb[d] = b[d] - 1 - jj;
+                int2 t;
+                t.x = lex(ca);
+                t.y = jj < ha[d] ? (anti ? -(lex(cb) + 1) : lex(cb) + 1) : 0;  // cb valid for pairs
+                // the last pass (z) writes class order: its table is indexed by the output's
+                // class-major position
+                ftab[(size_t)d * n + (d == 2 ? perm[o] : o)] = t;
+            }
+            // unfold pass (z, y, x): output cell coordinate c[ax] from the folded ones
+            {
+                const int ax = 2 - d;
+                int ca[3] = {c[0], c[1], c[2]}, cb[3] = {c[0], c[1], c[2]};
+                const int x = c[ax], jj = x < b[ax] - 1 - x ? x : b[ax] - 1 - x;
+                ca[ax] = jj;
+                cb[ax] = hs[ax] + jj;
+                int2 t;
+                const bool pair = jj < ha[ax];  // else the middle cell: no difference term
+                t.x = d == 0 ? perm[lex(ca)] : lex(ca);
+                t.y = 0;
+                if (pair) {
+                    const int ib = d == 0 ? perm[lex(cb)] : lex(cb);
+                    t.y = x == jj ? ib + 1 : -(ib + 1);
+                }
+                utab[(size_t)d * n + o] = t;
+            }
+        }
     int rc = upload(&B->Pc, pc);
     if (rc == BRS_OK)
         rc = upload(reinterpret_cast<void**>(&B->fmap), fmap);
     if (rc == BRS_OK)
         rc = upload(reinterpret_cast<void**>(&B->umap), umap);
+    if (rc == BRS_OK)
+        rc = upload(&B->ftab, ftab);
+    if (rc == BRS_OK)
+        rc = upload(&B->utab, utab);
     if (rc == BRS_OK)
         rc = brs_cuda_status(cudaMalloc(&B->Rf, (size_t)B->nblk * n * sizeof(T)));
     if (rc == BRS_OK)
@@ -951,7 +1016,7 @@ void box_teardown(brs_ctx* c)
     if (!B)
         return;
     void* bufs[] = {B->inv, B->inv_lo, B->R, B->R_lo, B->rows, B->off, B->Pc, B->Rf, B->fmap,
-                    B->umap};
+                    B->umap, B->ftab, B->utab};
     for (void* q : bufs)
         if (q)
             cudaFree(q);
