@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "box.cuh"
+#include "box_parity.h"
 #include "plane_tc.cuh"
 #include "tc_host.cuh"
 
@@ -52,15 +53,12 @@ struct BoxState {
     int* off = nullptr;          // local cell l -> lx + nx (ly + ny lz)
     CUtensorMap mR_hi, mR_lo, mA_hi, mA_lo;
     // parity classes (CUDA-core path): class sizes and offsets in the folded row, the class
-    // blocks of P (class c at pc_off[c], nc x nc), the folded rows, and the butterflies:
-    // fmap[q][f] (q < 8) = +-(l+1) of folded index f's cells (0 = none), umap[q][l] = +-(f+1)
+    // blocks of P (class c at pc_off[c], nc x nc), the folded rows, and the butterfly passes
     int fold = 0;
     int cls_n[8] = {0}, cls_off[8] = {0};
     long long pc_off[8] = {0};
     void* Pc = nullptr;
     void* Rf = nullptr;
-    int* fmap = nullptr;  // (host-side construction of P; not used by the kernels)
-    int* umap = nullptr;
     void* ftab = nullptr; // [3][n] int2: the fold's passes (x, y, z), the last into class order
     void* utab = nullptr; // [3][n] int2: the unfold's passes (z, y, x), the first from class order
 };
@@ -727,158 +725,28 @@ int upload(void** dst, const std::vector<T>& v)
 
 }  // namespace
 
-// Parity classes of a bx x by x bz box (see the file comment).  Along an axis of extent b the
-// folded coordinates are the sums j < ceil(b/2) (pair (j, b-1-j), or the middle cell of an
-// odd b) and the differences j < floor(b/2); a class picks sums or differences per axis.
-// Builds the class sizes and offsets, the butterflies of G (fmap) and G^T (umap), and the
-// class blocks of P = W G Ahat G^T W from the FP64 inverse.
+// Parity classes of the box (box_parity.h builds the tables on the host in FP64).
 template <typename T>
 int parity_setup(BoxState* B, const std::vector<double>& inv)
 {
-    const int b[3] = {B->bx, B->by, B->bz}, n = B->n;
-    int hs[3], ha[3];
-    for (int d = 0; d < 3; ++d) {
-        ha[d] = b[d] / 2;
-        hs[d] = b[d] - ha[d];
-    }
-    long long work = 0;
-    int off = 0;
-    for (int cl = 0; cl < 8; ++cl) {
-        int nc = 1;
-        for (int d = 0; d < 3; ++d)
-            nc *= ((cl >> d) & 1) ? ha[d] : hs[d];
-        B->cls_n[cl] = nc;
-        B->cls_off[cl] = off;
-        off += nc;
-        work += (long long)nc * nc;
-    }
-    // only where it saves at least half of the multiply-adds and the class products are not
-    // tiny: 4^3 boxes (classes of 8 cells) measured 8.27 -> 7.64 Gcell/s (FP64 GS, 256^3),
-    // 8^3 (classes of 64) 1.15 -> 3.81
-    int big = 0;
-    for (int cl = 0; cl < 8; ++cl)
-        big = B->cls_n[cl] > big ? B->cls_n[cl] : big;
-    if (off != n || 2 * work > (long long)n * n || big < 16)
+    const ParityTables pt = parity_tables(B->bx, B->by, B->bz, inv);
+    if (!pt.use)
         return BRS_OK;
-    // folded index f -> its cells with signs, and the weight W[f]
-    std::vector<int> fmap((size_t)n * 8, 0), umap((size_t)n * 8, 0);
-    std::vector<double> W(n);
-    std::vector<int> ucount(n, 0);
     for (int cl = 0; cl < 8; ++cl) {
-        const int c3[3] = {cl & 1, (cl >> 1) & 1, (cl >> 2) & 1};
-        const int sz[3] = {c3[0] ? ha[0] : hs[0], c3[1] ? ha[1] : hs[1], c3[2] ? ha[2] : hs[2]};
-        for (int i = 0; i < B->cls_n[cl]; ++i) {
-            const int j[3] = {i % sz[0], (i / sz[0]) % sz[1], i / (sz[0] * sz[1])};
-            const int f = B->cls_off[cl] + i;
-            double w = 1.0;
-            int q = 0;
-            for (int e = 0; e < 8; ++e) {
-                int x[3], sign = 1;
-                bool ok = true;
-                for (int d = 0; d < 3; ++d) {
-                    const bool mir = (e >> d) & 1;
-                    const bool pair = j[d] < ha[d];  // a mirrored pair (not the middle cell)
-                    if (mir && !pair) {
-                        ok = false;
-                        break;
-                    }
-                    x[d] = mir ? b[d] - 1 - j[d] : j[d];
-                    if (mir && c3[d])
-                        sign = -sign;
-                }
-                if (!ok)
-                    continue;
-                const int l = x[0] + b[0] * (x[1] + b[1] * x[2]);
-                fmap[(size_t)(q++) * n + f] = sign * (l + 1);
-                umap[(size_t)(ucount[l]++) * n + l] = sign * (f + 1);
-            }
-            for (int d = 0; d < 3; ++d)
-                if (j[d] < ha[d])
-                    w *= 0.5;
-            W[f] = w;
-        }
+        B->cls_n[cl] = pt.cls_n[cl];
+        B->cls_off[cl] = pt.cls_off[cl];
+        B->pc_off[cl] = pt.pc_off[cl];
     }
-    // class blocks of P: P[f][g] = W[f] W[g] sum over their cells of s s' Ahat[l][l']
-    std::vector<T> pc;
-    for (int cl = 0; cl < 8; ++cl) {
-        const int nc = B->cls_n[cl], o = B->cls_off[cl];
-        B->pc_off[cl] = (long long)pc.size();
-        for (int f = o; f < o + nc; ++f)
-            for (int g = o; g < o + nc; ++g) {
-                double acc = 0.0;
-                for (int q = 0; q < 8 && fmap[(size_t)q * n + f]; ++q) {
-                    const int ef = fmap[(size_t)q * n + f];
-                    const int l = (ef > 0 ? ef : -ef) - 1;
-                    for (int r = 0; r < 8 && fmap[(size_t)r * n + g]; ++r) {
-                        const int eg = fmap[(size_t)r * n + g];
-                        const int l2 = (eg > 0 ? eg : -eg) - 1;
-                        const double v = inv[(size_t)l * n + l2];
-                        acc += ((ef > 0) == (eg > 0)) ? v : -v;
-                    }
-                }
-                pc.push_back((T)(W[f] * W[g] * acc));
-            }
-    }
-    // the separable passes: layouts are (c0, c1, c2) lexicographic with each coordinate a
-    // cell or, once its axis is folded, a folded coordinate (sums first, then differences)
-    auto lex = [&](const int c[3]) { return c[0] + b[0] * (c[1] + b[1] * c[2]); };
-    std::vector<int> perm(n);  // lexicographic folded index -> class-major index
-    for (int cl = 0; cl < 8; ++cl) {
-        const int c3[3] = {cl & 1, (cl >> 1) & 1, (cl >> 2) & 1};
-        const int sz[3] = {c3[0] ? ha[0] : hs[0], c3[1] ? ha[1] : hs[1], c3[2] ? ha[2] : hs[2]};
-        for (int i = 0; i < B->cls_n[cl]; ++i) {
-            const int j[3] = {i % sz[0], (i / sz[0]) % sz[1], i / (sz[0] * sz[1])};
-            const int f[3] = {j[0] + c3[0] * hs[0], j[1] + c3[1] * hs[1], j[2] + c3[2] * hs[2]};
-            perm[lex(f)] = B->cls_off[cl] + i;
-        }
-    }
-    std::vector<int2> ftab((size_t)3 * n), utab((size_t)3 * n);
-    for (int d = 0; d < 3; ++d)
-        for (int o = 0; o < n; ++o) {
-            int c[3] = {o % b[0], (o / b[0]) % b[1], o / (b[0] * b[1])};
-            // fold pass d: output folded coordinate c[d] from the cells along d
-            {
-                int ca[3] = {c[0], c[1], c[2]}, cb[3] = {c[0], c[1], c[2]};
-                const bool anti = c[d] >= hs[d];
-                const int jj = anti ? c[d] - hs[d] : c[d];
-                ca[d] = jj;
-                cb[d] = b[d] - 1 - jj;
-                int2 t;
-                t.x = lex(ca);
-                t.y = jj < ha[d] ? (anti ? -(lex(cb) + 1) : lex(cb) + 1) : 0;  // cb valid for pairs
-                // the last pass (z) writes class order: its table is indexed by the output's
-                // class-major position
-                ftab[(size_t)d * n + (d == 2 ? perm[o] : o)] = t;
-            }
-            // unfold pass (z, y, x): output cell coordinate c[ax] from the folded ones
-            {
-                const int ax = 2 - d;
-                int ca[3] = {c[0], c[1], c[2]}, cb[3] = {c[0], c[1], c[2]};
-                const int x = c[ax], jj = x < b[ax] - 1 - x ? x : b[ax] - 1 - x;
-                ca[ax] = jj;
-                cb[ax] = hs[ax] + jj;
-                int2 t;
-                const bool pair = jj < ha[ax];  // else the middle cell: no difference term
-                t.x = d == 0 ? perm[lex(ca)] : lex(ca);
-                t.y = 0;
-                if (pair) {
-                    const int ib = d == 0 ? perm[lex(cb)] : lex(cb);
-                    t.y = x == jj ? ib + 1 : -(ib + 1);
-                }
-                utab[(size_t)d * n + o] = t;
-            }
-        }
+    const std::vector<T> pc(pt.pc.begin(), pt.pc.end());
+    const std::vector<int>& ftab = pt.ftab;  // [3][n] (x, y) pairs: the layout of int2
+    const std::vector<int>& utab = pt.utab;
     int rc = upload(&B->Pc, pc);
-    if (rc == BRS_OK)
-        rc = upload(reinterpret_cast<void**>(&B->fmap), fmap);
-    if (rc == BRS_OK)
-        rc = upload(reinterpret_cast<void**>(&B->umap), umap);
     if (rc == BRS_OK)
         rc = upload(&B->ftab, ftab);
     if (rc == BRS_OK)
         rc = upload(&B->utab, utab);
     if (rc == BRS_OK)
-        rc = brs_cuda_status(cudaMalloc(&B->Rf, (size_t)B->nblk * n * sizeof(T)));
+        rc = brs_cuda_status(cudaMalloc(&B->Rf, (size_t)B->nblk * B->n * sizeof(T)));
     if (rc == BRS_OK)
         B->fold = 1;
     return rc;
@@ -1015,8 +883,8 @@ void box_teardown(brs_ctx* c)
     BoxState* B = bs(c);
     if (!B)
         return;
-    void* bufs[] = {B->inv, B->inv_lo, B->R, B->R_lo, B->rows, B->off, B->Pc, B->Rf, B->fmap,
-                    B->umap, B->ftab, B->utab};
+    void* bufs[] = {B->inv, B->inv_lo, B->R, B->R_lo, B->rows, B->off, B->Pc, B->Rf, B->ftab,
+                    B->utab};
     for (void* q : bufs)
         if (q)
             cudaFree(q);
