@@ -424,15 +424,25 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
             return gyp ? gyp + (long long)kk * nx : nullptr;
         return nullptr;
     };
-    auto copy_row = [&](int slot, int f, const T* row) {
-        const bool ok = xin && row;
-        const T* p = ok ? row + x0 : ub;
+    // The steps' rows are issued for consecutive planes k0, k0 + 1, ...: their element
+    // offsets advance by one plane (a y face's ghost rows by nx) per step, and whether
+    // each field's row exists is fixed per item.  (The generic selection of row_of on
+    // every copy cost about a fifth of the kernel's instructions.)
+    long long o_next = (long long)k0 * plane + (long long)j * nx + x0;  // row (j, k) at x0
+    const bool ok_b = xin && jin;
+    const bool ok_n = xin && j >= 1 && j <= ny;  // line j - 1 inside the patch
+    const bool ok_s = xin && j + 1 < ny;         // line j + 1
+    // a level's rows outside the patch: u(k+1) of line ny is the y+ ghost row, and the
+    // halo lines at the patch's y faces are the y- / y+ ghost rows
+    long long og_next = (long long)k0 * nx + x0;
+    const bool ok_0 = xin && (jin || (j == ny && gyp));
+    const bool ok_gn = xin && (j > 0 || gym);
+    const bool ok_gs = xin && (j + 1 < ny || (j + 1 == ny && gyp));
+    auto copy_at = [&](int slot, int f, const T* src, long long o, bool ok) {
+        const T* p = ok ? src + o : ub;
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             cp_async16(ring0 + soff(slot, f, c), p + c * (16 / sizeof(T)), ok ? 16u : 0u);
-    };
-    auto copy_line = [&](int slot, int f, const T* src, int jj, int kk) {
-        copy_row(slot, f, row_of(src, jj, kk));
     };
     // x ghosts of the line (level contexts): the lanes holding x = 0 and x = nx - 1
     const bool xlo = LV && xin && jin && x0 == 0;
@@ -459,25 +469,28 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
             // the rows this step can need outside the patch are known per field: u(k+1)
             // crosses the z+ face on the last plane, the halo lines cross the y faces, and
             // line ny (past the patch, in the last y-block) carries the y+ ghost row that
-            // its neighbour ny - 1 takes by shuffle
-            const T* in = ub + (long long)kk * plane + (long long)j * nx;
-            copy_row(slot, 0, kk + 1 < nz ? (jin ? in + plane
-                                                 : (j == ny && gyp ? gyp + (long long)(kk + 1) * nx
-                                                                   : nullptr))
-                                          : gzp);
-            copy_row(slot, 1, jin ? bb + (in - ub) : nullptr);
+            // its neighbour ny - 1 takes by shuffle (og: row kk of a y face, at x0)
+            const long long o = o_next, og = og_next;
+            o_next += plane;
+            og_next += nx;
+            if (kk + 1 < nz)
+                copy_at(slot, 0, jin ? ub : gyp, jin ? o + plane : og + nx, ok_0);
+            else
+                copy_at(slot, 0, gzp, x0, xin && gzp);
+            copy_at(slot, 1, bb, o, ok_b);
             if (g == 0)
-                copy_row(slot, 2, j > 0 ? in - nx : (gym ? gym + (long long)kk * nx : nullptr));
+                copy_at(slot, 2, j > 0 ? ub : gym, j > 0 ? o - nx : og, ok_gn);
             if (g == R - 1)
-                copy_row(slot, 3, j + 1 < ny ? in + nx
-                                             : (j + 1 == ny && gyp ? gyp + (long long)kk * nx : nullptr));
+                copy_at(slot, 3, j + 1 < ny ? ub : gyp, j + 1 < ny ? o + nx : og, ok_gs);
         } else {
-            copy_line(slot, 0, ub, j, kk + 1);
-            copy_line(slot, 1, bb, j, kk);
+            const long long o = o_next;  // row (j, kk): issue runs for kk = k0, k0 + 1, ...
+            o_next += plane;
+            copy_at(slot, 0, ub, o + plane, ok_b && kk + 1 < nz);
+            copy_at(slot, 1, bb, o, ok_b);
             if (g == 0)
-                copy_line(slot, 2, ub, j - 1, kk);
+                copy_at(slot, 2, ub, o - nx, ok_n);
             if (g == R - 1)
-                copy_line(slot, 3, ub, j + 1, kk);
+                copy_at(slot, 3, ub, o + nx, ok_s);
         }
     };
     auto read = [&](int slot, int f, T (&v)[kE]) {
