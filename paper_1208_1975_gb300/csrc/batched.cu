@@ -154,7 +154,7 @@ __device__ __forceinline__ const T* ghost_x(const PatchDesc& d, const T* ghost, 
 template <typename T>
 __device__ __noinline__ void push_item(const PatchDesc* __restrict__ desc,
                                        const long long* __restrict__ push_all, T* gnext,
-                                       const T* uout, int pq, int item, int KC)
+                                       const T* uout, int pq, int item, int KC, bool yz_done)
 {
     __syncwarp();  // the item's stores by every lane of the warp are visible to all lanes
     const PatchDesc d = desc[pq];
@@ -180,6 +180,8 @@ __device__ __noinline__ void push_item(const PatchDesc* __restrict__ desc,
         }
     }
     for (int f = 2; f < 4; ++f) {  // y faces: line 0 or ny - 1, when the item holds it
+        if (yz_done && ny > 1)
+            break;  // written by the step loop
         const int j = f == 2 ? 0 : ny - 1;
         if (j < j0 || j >= j0 + nj)
             continue;
@@ -192,7 +194,7 @@ __device__ __noinline__ void push_item(const PatchDesc* __restrict__ desc,
             gnext[o + (long long)k * nx + i] = uo[k * plane + (long long)j * nx + i];
         }
     }
-    for (int f = 4; f < 6; ++f) {  // z faces: plane 0 or nz - 1, when the item holds it
+    for (int f = 4; f < 6 && !yz_done; ++f) {  // z faces: plane 0 or nz - 1, when held
         const int k = f == 4 ? 0 : nz - 1;
         if (k < k0 || k >= k1)
             continue;
@@ -372,7 +374,8 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
                                                    const T* uin, T* uout,
                                                    const T* __restrict__ b,
                                                    const T* __restrict__ tab, T ax, T ay, T az,
-                                                   T om1, const T* ghost, unsigned char* ring)
+                                                   T om1, const T* ghost, unsigned char* ring,
+                                                   T* gnext, const long long* pp)
 {
     constexpr int R = 32 / G;
     constexpr int CH = (int)(kE * sizeof(T) / 16);  // 16-byte chunks per lane and field
@@ -447,6 +450,16 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
     // x ghosts of the line (level contexts): the lanes holding x = 0 and x = nx - 1
     const bool xlo = LV && xin && jin && x0 == 0;
     const bool xhi = LV && xin && jin && x0 <= nx - 1 && nx - 1 < x0 + kE;
+    // a level step that writes the next step's ghosts (gnext set): the y- and z-face rows
+    // its lines feed are stored as the steps produce them, from registers (row k of a y face
+    // at o + k nx, row j of a z face at o + j nx; pp: the patch's six push offsets).  Lines
+    // 0 and ny - 1 are distinct when ny > 1; a one-line patch leaves its y faces to push_item.
+    long long gy = -1;  // this lane's piece of the y-face row of plane k, or -1
+    if (LV && gnext && xin && ny > 1 && (j == 0 || j == ny - 1)) {
+        const long long o = __ldg(pp + (j == 0 ? 2 : 3));
+        if (o >= 0)
+            gy = o + (long long)k0 * nx + x0;
+    }
     // the item's x ghosts, staged once: xg[face][k - k0][line in the warp], copied
     // asynchronously with the first step's inputs (zero beyond the last line)
     T* xg = reinterpret_cast<T*>(ring + (size_t)D * kFields * 32 * kE * sizeof(T));
@@ -571,6 +584,26 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
             for (int c = 0; c < CH; ++c)
                 reinterpret_cast<float4*>(p)[c] = reinterpret_cast<const float4*>(v)[c];
         }
+        if constexpr (LV) {
+            if (gy >= 0) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    reinterpret_cast<float4*>(gnext + gy)[c] = reinterpret_cast<const float4*>(v)[c];
+                gy += nx;
+            }
+            if (gnext && (k == 0 || k == nz - 1) && xin && jin) {  // k is the same for the warp
+#pragma unroll
+                for (int f = 4; f < 6; ++f) {
+                    const long long o = (f == 4 ? k == 0 : k == nz - 1) ? __ldg(pp + f) : -1;
+                    if (o >= 0) {
+                        T* p = gnext + o + (long long)j * nx + x0;
+#pragma unroll
+                        for (int c = 0; c < CH; ++c)
+                            reinterpret_cast<float4*>(p)[c] = reinterpret_cast<const float4*>(v)[c];
+                    }
+                }
+            }
+        }
 
 #pragma unroll
         for (int q = 0; q < kE; ++q) {
@@ -615,14 +648,15 @@ __global__ void __launch_bounds__(512) batched_async_kernel(const PatchDesc* __r
         const PatchDesc d = desc[pq];
         const int local = item - d.item0;
         const int jb = local % d.njb, kc = local / d.njb;
+        const long long* pp = push ? push + 6 * pq : nullptr;
         switch (d.cls) {
-        case 0: batched_item_async<T, 4, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
-        case 1: batched_item_async<T, 8, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
-        case 2: batched_item_async<T, 16, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
-        default: batched_item_async<T, 32, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring); break;
+        case 0: batched_item_async<T, 4, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring, gnext, pp); break;
+        case 1: batched_item_async<T, 8, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring, gnext, pp); break;
+        case 2: batched_item_async<T, 16, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring, gnext, pp); break;
+        default: batched_item_async<T, 32, GS, D, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost, ring, gnext, pp); break;
         }
         if (LV && gnext)
-            push_item<T>(desc, push, gnext, uout, item_patch[item], item, KC);
+            push_item<T>(desc, push, gnext, uout, item_patch[item], item, KC, true);
     }
 }
 
@@ -716,7 +750,7 @@ __global__ void __launch_bounds__(512) batched_line_kernel(const PatchDesc* __re
         default: batched_item<T, 32, GS, LV>(d, jb, kc, KC, uin, uout, b, tab, (T)ax, (T)ay, (T)az, (T)om1, ghost); break;
         }
         if (LV && gnext)
-            push_item<T>(desc, push, gnext, uout, item_patch[item], item, KC);
+            push_item<T>(desc, push, gnext, uout, item_patch[item], item, KC, false);
     }
 }
 
