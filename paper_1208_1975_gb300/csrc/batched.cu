@@ -148,9 +148,10 @@ __device__ __forceinline__ const T* ghost_x(const PatchDesc& d, const T* ghost, 
 // is written once per step, so the values are final; they are re-read from the output (just
 // written by this warp, L2-resident).  push[f] is the offset of the destination face in that
 // buffer, -1 where face f has no neighbour; destination layouts: z faces [j][i], y faces
-// [k][i], x faces [k][j].  Not inlined and kept small, with nothing of it in the step loop:
-// the loop keeps its registers (changes there cost more than the copy saves); the item is
-// re-read here.
+// [k][i], x faces [k][j].  With yz_done (the cp.async kernel) the step loop has stored the
+// y- and z-face rows itself, from registers, and only the x faces (and the y faces of a
+// one-line patch) are copied here.  Not inlined and kept small: the step loop keeps its
+// registers; the item is re-read here.
 template <typename T>
 __device__ __noinline__ void push_item(const PatchDesc* __restrict__ desc,
                                        const long long* __restrict__ push_all, T* gnext,
