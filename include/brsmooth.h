@@ -321,7 +321,9 @@ int brsmooth_adjoint_sweep(brs_ctx* c, void* lam, const void* u_k, const void* b
  * kernel: `nsweeps` sweeps on device grid `u` (in/out) with right-hand side `b`, the
  * result left in `u`.
  * The first call on each device looks up the arrays' device addresses (with that device
- * current); make that first call before any stream capture.  All calls share the arrays
+ * current); make that first call before any stream capture.  Later calls may be captured
+ * into a CUDA graph: a call enqueues only kernels and a device-to-device copy, and a
+ * replay recomputes the tables from the captured coefficients.  All calls share the arrays
  * and each call rewrites what it uses (tables and second vector are fully overwritten, so
  * nothing carries over); calls whose GPU work overlaps (different streams or threads)
  * race on them.  Errors: BRS_ERR_ARG (dims < 1, null, misaligned or aliased arrays,

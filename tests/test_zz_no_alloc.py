@@ -77,3 +77,53 @@ def test_noalloc_rejections():
                                             0) == brs.BRS_ERR_ARG  # u aliases b
     torch.cuda.synchronize()
     assert torch.count_nonzero(u) == 0  # rejected calls touched nothing
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_noalloc_calls_captured_in_a_cuda_graph(orc, dt):
+    """Two calls (2 and 3 sweeps) captured into one CUDA graph on a side stream: nothing
+    is copied from the host, so the graph replays on its own.  Every replay from the same
+    start equals the same two calls run directly, bit for bit, and the result matches 5
+    sweeps of the context path and of the oracle."""
+    import torch
+
+    import paper_1208_1975_gb300 as brs
+
+    brs.build()
+    nx, ny, nz, a = 64, 12, 10, (1.0, 0.3, 0.1)
+    shape = (nz, ny, nx)
+    u0 = rounded(initial_guess(shape), dt)
+    b = rounded(rhs(shape), dt)
+    call = lambda u, bb, ns, s: brs.brsmooth_line_jacobi_noalloc(
+        nx, ny, nz, a, 0.0, brs.DTYPES[dt], u.data_ptr(), bb.data_ptr(), ns, s)
+    # direct calls (also the first call on the device, which must precede any capture)
+    ud, bd = to_dev(u0, dt), to_dev(b, dt)
+    cur = torch.cuda.current_stream().cuda_stream
+    assert call(ud, bd, 2, cur) == brs.BRS_OK
+    assert call(ud, bd, 3, cur) == brs.BRS_OK
+    torch.cuda.synchronize()
+    direct = to_np(ud)
+    # the same two calls captured
+    ug, bg = to_dev(u0, dt), to_dev(b, dt)
+    start = ug.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        rc1 = call(ug, bg, 2, side.cuda_stream)
+        rc2 = call(ug, bg, 3, side.cuda_stream)
+    assert rc1 == brs.BRS_OK and rc2 == brs.BRS_OK
+    for _ in range(2):
+        ug.copy_(start)
+        graph.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_np(ug), direct)
+    with brs.Context(nx, ny, nz, a, block="line", method="jacobi", dtype=dt) as ctx:
+        ur, br = to_dev(u0, dt), to_dev(b, dt)
+        ctx.sweep(ur, br, 5)
+        ref_ctx = to_np(ur)
+    ref = u0
+    for _ in range(5):
+        ref = orc.sweep(ref, b, a, block="line", method="jacobi", omega=0.8)
+    assert rel_max_err(direct, ref_ctx) <= TOL[dt]
+    assert rel_max_err(direct, ref) <= TOL[dt]
