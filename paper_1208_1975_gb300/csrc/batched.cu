@@ -174,8 +174,10 @@ __device__ __noinline__ void push_item(const PatchDesc* __restrict__ desc,
         if (o < 0)
             continue;
         const int xi = f ? nx - 1 : 0;
+        const int lgR = 3 - d.cls;  // R = 8 >> cls
         for (int t = lane; t < nj * nk; t += 32) {
-            const int kk = t / nj, jl = t - kk * nj;
+            const int kk = nj == R ? t >> lgR : t / nj;
+            const int jl = t - kk * nj;
             const int j = j0 + jl, k = k0 + kk;
             gnext[o + j + (long long)ny * k] = uo[k * plane + (long long)j * nx + xi];
         }
@@ -465,18 +467,20 @@ __device__ __forceinline__ void batched_item_async(const PatchDesc& d, int jb, i
     // asynchronously with the first step's inputs (zero beyond the last line)
     T* xg = reinterpret_cast<T*>(ring + (size_t)D * kFields * 32 * kE * sizeof(T));
     if (LV) {
+        // x faces are [k][j] in the ghost block: element (kk, jl) of the item at
+        // xb + face * xpo + kk * ny + jl (R a power of two: no divisions)
         const long long xpo = round4((long long)ny * nz);
         const int nk = k1 - k0;
         const uint32_t xg0 = (uint32_t)__cvta_generic_to_shared(xg);
-        for (int idx = lanew; idx < 2 * nk * R; idx += 32) {
-            const int face = idx / (nk * R), rem = idx - face * nk * R;
-            const int kk = rem / R, jl = rem - kk * R;
-            const int jj = jb * R + jl;
-            const bool ok = jj < ny;
-            const T* src = ok ? ghost_x(d, ghost, jj, k0 + kk) + (face ? xpo : 0) : ghost;
-            cp_async4(xg0 + (uint32_t)(((face * kMaxKC + kk) * 8 + jl) * sizeof(T)), src,
-                      ok ? 4u : 0u);
-        }
+        const T* xb = ghost_x(d, ghost, jb * R, k0);
+        for (int face = 0; face < 2; ++face)
+            for (int idx = lanew; idx < nk * R; idx += 32) {
+                const int kk = idx / R, jl = idx % R;
+                const bool ok = jb * R + jl < ny;
+                const T* src = ok ? xb + (face ? xpo : 0) + (long long)kk * ny + jl : ghost;
+                cp_async4(xg0 + (uint32_t)(((face * kMaxKC + kk) * 8 + jl) * sizeof(T)), src,
+                          ok ? 4u : 0u);
+            }
     }
     auto issue = [&](int kk, int slot) {
         if constexpr (LV) {
